@@ -1,0 +1,254 @@
+/*
+ * litho.h - C ABI of the GB300 SOCS lithography imaging library (liblitho.so).
+ *
+ * The library evaluates, on one NVIDIA GB300 (sm_103a):
+ *   - partially coherent aerial images in sum-of-coherent-systems (SOCS) form,
+ *     I(x) = D * sum_k lam_k |(phi_k (x) m)(x)|^2, over K TCC eigen-kernels and
+ *     several focus planes (paper Section III.A, Eqs. (1)-(4));
+ *   - the Gaussian-blur + threshold resist (Eq. (5));
+ *   - the ILT mask gradient through the resist and imaging (the adjoint of the
+ *     above; pixel-based ILT is the paper's Section I prior art);
+ *   - a continuous-batching request server over all of it.
+ *
+ * Conventions shared by every entry point:
+ *   - Grids are N x N, row-major, x fastest; pixel size in nm at the wafer.
+ *   - Frequencies f_u = u / (N * pixel), u in [-N/2, N/2).  Kernels live on a
+ *     C x C crop centred on DC, crop index c <-> u = c - C/2 (C a multiple of
+ *     32, C/2 above the band radius (1 + sigma_max) NA / wavelength).
+ *   - The mask spectrum is M(u) = N^-2 * DFT(m)(u): a clear mask (m = 1)
+ *     images to I = dose everywhere with the full-rank kernel set.
+ *   - Device pointers (suffix _dev) are CUDA global memory owned by the caller
+ *     (for example torch tensors); host pointers (suffix _host) are plain CPU
+ *     memory, pinned or pageable.  Handles (litho_kernels, litho_server) and the
+ *     memory they reference are owned by the library.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Device work is enqueued on it and the call returns without
+ *     waiting, unless a host output (loss_host, *_host buffers) is requested.
+ *   - No C++ exception crosses this boundary.  Every call returns a
+ *     litho_status; on failure litho_last_error() gives a message (per thread).
+ *   - Nothing here allocates device memory except litho_make_kernels /
+ *     litho_upload_kernels (the kernel handle) and the server.  Scratch is the
+ *     caller's `workspace`, sized by the *_workspace_size queries.
+ */
+#ifndef LITHO_H
+#define LITHO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LITHO_OK = 0,
+  LITHO_EINVAL = 1,       /* bad argument (size, null pointer, alignment, mismatch) */
+  LITHO_ENOMEM = 2,       /* host or device allocation failed, or workspace too small */
+  LITHO_ECUDA = 3,        /* a CUDA call failed; message in litho_last_error() */
+  LITHO_EBUSY = 4,        /* server queue full */
+  LITHO_ETIMEOUT = 5,     /* poll timed out, or a device-side wait gave up */
+  LITHO_ECANCELED = 6,    /* request cancelled */
+  LITHO_EUNSUPPORTED = 7  /* valid request this build or device does not implement */
+} litho_status;
+
+typedef enum {
+  LITHO_SRC_ANNULAR = 0,     /* sigma_in <= |sigma| <= sigma_out */
+  LITHO_SRC_QUADRUPOLE = 1,  /* four discs, radius pole_radius, centred on the x/y axes at pole_sigma */
+  LITHO_SRC_CUSTOM = 2       /* weights custom_w on the src_grid x src_grid lattice */
+} litho_source_kind;
+
+/* Illumination and projection optics (paper Eq. (2): source S and pupil P).
+ * The source is sampled on the lattice sigma = (i/h, j/h), i, j in [-h, h],
+ * h = (src_grid - 1)/2, in units of NA/wavelength; membership tests are
+ * inclusive.  Weights are equal (annular, quadrupole) or custom_w, and are
+ * normalised to sum 1.  The pupil is scalar and aberration-free with the NA
+ * cut-off and a defocus phase exp(i 2 pi z (sqrt((n/l)^2 - f^2) - n/l)). */
+typedef struct {
+  double wavelength_nm;   /* 193 (ArF immersion) or 13.5 (EUV) */
+  double na;              /* numerical aperture, 0 < NA <= n_medium */
+  double n_medium;        /* immersion index (1.44 ArF immersion, 1 EUV) */
+  int kind;               /* litho_source_kind */
+  int src_grid;           /* odd, >= 3 */
+  double sigma_in, sigma_out;        /* annular */
+  double pole_sigma, pole_radius;    /* quadrupole */
+  const double* custom_w; /* CUSTOM: src_grid*src_grid weights, row j (y) major; copied */
+} litho_optics;
+
+typedef enum {
+  LITHO_PREC_FFT32 = 0,  /* FP32 FFT path (band multiply + two inverse FFT passes) */
+  LITHO_PREC_BF16 = 1,   /* tcgen05 DFT-GEMM, bf16 operands, FP32 accumulation */
+  LITHO_PREC_BF16X3 = 2, /* tcgen05 DFT-GEMM, split bf16 hi/lo, three products */
+  LITHO_PREC_FP16X3 = 3  /* tcgen05 DFT-GEMM, split fp16 hi/lo (scaled), three products */
+} litho_precision;
+
+typedef struct litho_kernels litho_kernels; /* device-resident SOCS kernels for one (optics, N, pixel, focus list, K) */
+typedef struct litho_server litho_server;
+
+/* ---- kernels (paper Eqs. (2)-(3)) ------------------------------------------------------- */
+
+/* Builds the top-k TCC eigen-kernels of every focus plane on the host in FP64
+ * (TCC = A A^H with A[u,s] = sqrt(w_s) P(f_u + sigma_s; z); eigenpairs from the
+ * Gram matrix A^H A) and uploads them.  k larger than the TCC rank gives zero
+ * kernels (lam = 0) for the excess modes; the rank is reported by
+ * litho_kernels_info.  n must be a power of two in [16, 2048].
+ * Errors: EINVAL (bad optics/sizes), ENOMEM, ECUDA. */
+litho_status litho_make_kernels(const litho_optics* optics, int n, double pixel_nm, const double* defocus_nm,
+                                int n_focus, int k, litho_kernels** out);
+
+/* The FP64 host half of litho_make_kernels for one focus plane, with no GPU
+ * involved: call with phi_host = NULL to learn *crop, then again with
+ * lambda_host of k doubles and phi_host of k*crop*crop*2 doubles ([k][v][u],
+ * re/im interleaved).  rank, trace, gap as in litho_kernels_info; any of the
+ * scalar outputs may be NULL. */
+litho_status litho_tcc_kernels_host(const litho_optics* optics, int n, double pixel_nm, double defocus_nm, int k,
+                                    int* crop, double* lambda_host, double* phi_host, int* rank, double* trace,
+                                    double* gap);
+
+/* Wraps caller-supplied kernels: lambda_host[n_focus*k] (>= 0) and
+ * phi_host[n_focus][k][crop][crop][2] (re, im interleaved), crop a multiple of
+ * 32 in [32, n].  Used to image with kernels from another source (for example
+ * a reference implementation) through the same device path.  Copies the data. */
+litho_status litho_upload_kernels(int n, double pixel_nm, int n_focus, int k, int crop, const double* lambda_host,
+                                  const double* phi_host, litho_kernels** out);
+
+/* Describes a kernel set.  Any output pointer may be NULL.  rank_host,
+ * trace_host and gap_host have n_focus entries, lambda_host n_focus*k.
+ * gap = lam_k - lam_{k+1} of the built TCC (0 for uploaded kernels); a gap
+ * below 1e-12 * lam_1 means the cut at k splits a degenerate cluster. */
+litho_status litho_kernels_info(const litho_kernels* h, int* n, int* crop, int* n_focus, int* k, int* rank_host,
+                                double* lambda_host, double* trace_host, double* gap_host);
+
+/* Copies the FP64 kernels phi[n_focus][k][crop][crop][2] back to the host. */
+litho_status litho_kernels_phi(const litho_kernels* h, double* phi_host);
+
+void litho_free_kernels(litho_kernels* h);
+
+/* ---- aerial image (paper Eq. (4)) ------------------------------------------------------------ */
+
+/* Bytes of device scratch litho_aerial needs for a batch of b clips. */
+litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes);
+
+/* I[b][f][y][x] = dose * sum_k lam_fk |E_fk(x,y)|^2 for masks m[b][y][x]
+ * (values in [0,1], any real values accepted).  mask_dev and intensity_dev are
+ * float32 device arrays; workspace_dev must be 256-byte aligned and hold
+ * litho_aerial_workspace_size bytes.  Asynchronous on `stream`.
+ * Errors: EINVAL, ENOMEM (workspace too small), EUNSUPPORTED (precision not
+ * available for this crop), ECUDA. */
+litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, double dose, litho_precision prec,
+                          float* intensity_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* The same computation from host memory, optionally followed by the resist:
+ * copies mask_host[b][n][n] in, images, and copies back whichever of
+ * intensity_host[b][F][n][n] (f32) and printed_host[b][F][n][n] (u8, the
+ * litho_resist threshold of the blurred image with sigma_nm and threshold) is
+ * non-NULL, then waits for the stream.  Device buffers are carved from
+ * workspace_dev (litho_aerial_host_workspace_size bytes).  Pinned host memory
+ * lets the copies run at full link speed. */
+litho_status litho_aerial_host_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes);
+litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, int b, double dose,
+                               litho_precision prec, float* intensity_host, double sigma_nm, double threshold,
+                               uint8_t* printed_host, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* ---- resist (paper Eq. (5)) ------------------------------------------------------------------- */
+
+/* iblur = g (x) I with the periodic separable Gaussian g[j] ~ exp(-(j p)^2 / (2 s^2)),
+ * |j| <= ceil(4 s / p), sum g = 1; printed = (iblur >= threshold) as 0/1 bytes.
+ * `planes` independent n x n planes.  printed_dev may be NULL.  The blur
+ * radius must be below n/2. */
+litho_status litho_resist(const float* intensity_dev, int planes, int n, double pixel_nm, double sigma_nm,
+                          double threshold, float* iblur_dev, uint8_t* printed_dev, void* stream);
+
+/* ---- ILT gradient -------------------------------------------------------------------------------- */
+
+/* Workspace for litho_ilt_grad: `full_bytes` keeps every focus plane's
+ * stage-1 fields for the backward pass; `min_bytes` keeps one focus plane at a
+ * time and recomputes it in the backward pass. */
+litho_status litho_ilt_workspace_size(const litho_kernels* h, int b, size_t* full_bytes, size_t* min_bytes);
+
+/* Loss and gradient of ILT over all focus planes of h, per clip:
+ *   m = sigmoid(mask_steep * theta), I_f = dose * SOCS_f(m), Ib_f = g (x) I_f,
+ *   Z_f = sigmoid(resist_steep * (Ib_f - threshold)),
+ *   loss = sum_f sum_x (Z_f - target)^2,   grad = d loss / d theta.
+ * theta_dev, target_dev, grad_dev: float32 [b][n][n] on the device.
+ * loss_host (may be NULL): b doubles, reduced in FP64 on the device; when
+ * given, the call waits for the stream.  A workspace between min_bytes and
+ * full_bytes selects recomputation of the forward fields; below min_bytes is
+ * ENOMEM.  Only LITHO_PREC_FFT32 is implemented (else EUNSUPPORTED). */
+litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, const float* target_dev, int b,
+                            double dose, double mask_steep, double resist_steep, double threshold, double sigma_nm,
+                            litho_precision prec, float* grad_dev, double* loss_host, void* workspace_dev,
+                            size_t workspace_bytes, void* stream);
+
+/* ---- serving ------------------------------------------------------------------------------------- */
+
+typedef enum { LITHO_REQ_IMAGE = 0, LITHO_REQ_ILT_STEP = 1 } litho_request_kind;
+
+/* One request: a single clip.  All pointers are host memory that must stay
+ * valid until the request completes (poll returns OK/ECANCELED).
+ *   IMAGE:    input = mask[n][n] -> output = I[n][n] at defocus_nm.
+ *   ILT_STEP: input = theta[n][n], target[n][n] -> output = grad[n][n], *loss. */
+typedef struct {
+  int kind;                 /* litho_request_kind */
+  litho_optics optics;
+  int n;
+  double pixel_nm;
+  double defocus_nm;
+  int k;
+  int precision;            /* litho_precision (ILT steps use FFT32) */
+  double dose;
+  double sigma_nm, threshold, mask_steep, resist_steep;   /* ILT step */
+  const float* input_host;
+  const float* target_host;
+  float* output_host;
+  double* loss_host;
+} litho_request;
+
+typedef struct {
+  uint64_t submitted, completed, rejected, cancelled;
+  double p50_ms, p99_ms;          /* submit -> completion latency over completed requests */
+  double mpx_per_s;               /* completed pixels / (last completion - first submit) */
+  size_t hbm_high_water;          /* peak bytes of admitted work */
+  int kernel_sets_cached;
+} litho_serve_stats_t;
+
+/* A server with its own scheduler thread, max_slots concurrent requests (one
+ * CUDA stream each), admission while the summed device footprint of running
+ * requests stays within hbm_budget_bytes, and a queue of max_queue waiting
+ * requests.  Kernel sets are built once per (optics, n, pixel, focus, k) and
+ * stay resident. */
+litho_status litho_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, litho_server** out);
+/* EBUSY if the queue is full; EINVAL if the request's footprint exceeds the
+ * whole budget or its fields are invalid. */
+litho_status litho_serve_submit(litho_server* s, const litho_request* req, uint64_t* ticket);
+/* OK when done (output written), ECANCELED, ETIMEOUT if still pending after
+ * timeout_ms (0 = just check), EINVAL for an unknown ticket, or the request's
+ * own error status.  Never blocks longer than timeout_ms. */
+litho_status litho_serve_poll(litho_server* s, uint64_t ticket, int timeout_ms);
+/* Cancels a request that has not started; EBUSY if it is already running. */
+litho_status litho_serve_cancel(litho_server* s, uint64_t ticket);
+litho_status litho_serve_stats(litho_server* s, litho_serve_stats_t* out);
+/* Waits for running requests, cancels queued ones, frees everything. */
+void litho_serve_destroy(litho_server* s);
+
+/* ---- tracing ------------------------------------------------------------------------------------- */
+
+/* Per-stage device timing.  While enabled, every stage the library enqueues is
+ * bracketed by CUDA events on its stream (stages: mask_spectrum, stage1_fft,
+ * stage2_fft, stage1_gemm_operands, stage2_gemm, resist, ilt_forward,
+ * ilt_backward, ilt_reduce).  litho_profile_read waits for the recorded events
+ * and reports, for up to max_stages stages that ran since the last reset,
+ * the name (32-byte slots in `names`), the summed device milliseconds and the
+ * number of kernel launches; *count receives how many were written. */
+litho_status litho_profile_enable(int on);
+void litho_profile_reset(void);
+litho_status litho_profile_read(int max_stages, char* names, double* total_ms, long long* launches, int* count);
+
+/* ---- misc ----------------------------------------------------------------------------------------- */
+
+const char* litho_last_error(void);
+const char* litho_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LITHO_H */

@@ -1,0 +1,406 @@
+// C ABI entry points: kernel handles, aerial image, resist, error reporting.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "litho_internal.h"
+#include "gemm.h"
+
+namespace litho {
+
+namespace {
+thread_local char g_err[1024] = "";
+
+size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+bool valid_n(int n) {
+  if (n < 32 || n > 2048) return false;
+  return (n & (n - 1)) == 0;
+}
+
+// Bump allocator over the caller's workspace.
+struct Carve {
+  char* base;
+  size_t cap, used = 0;
+  Carve(void* b, size_t c) : base(static_cast<char*>(b)), cap(c) {}
+  template <class T>
+  T* take(size_t count) {
+    const size_t off = align_up(used);
+    used = off + count * sizeof(T);
+    return base ? reinterpret_cast<T*>(base + off) : nullptr;
+  }
+};
+
+litho_status upload(litho_kernels* h) {
+  const int F = h->n_focus, K = h->k, C = h->crop, N = h->n;
+  LITHO_TRY_CUDA(cudaGetDevice(&h->device));
+  std::vector<float> lam(size_t(F) * K);
+  for (size_t i = 0; i < lam.size(); ++i) lam[i] = float(h->lambda[i]);
+  std::vector<float2> phi(size_t(F) * K * C * C);
+  for (size_t i = 0; i < phi.size(); ++i) phi[i] = make_float2(float(h->phi_host[2 * i]), float(h->phi_host[2 * i + 1]));
+  std::vector<float2> tw(N);
+  for (int j = 0; j < N; ++j) {
+    const double a = 2.0 * M_PI * double(j) / double(N);
+    tw[j] = make_float2(float(std::cos(a)), float(-std::sin(a)));
+  }
+  LITHO_TRY_CUDA(cudaMalloc(&h->d_lambda, lam.size() * sizeof(float)));
+  LITHO_TRY_CUDA(cudaMalloc(&h->d_phi, phi.size() * sizeof(float2)));
+  LITHO_TRY_CUDA(cudaMalloc(&h->d_tw, tw.size() * sizeof(float2)));
+  LITHO_TRY_CUDA(cudaMemcpy(h->d_lambda, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice));
+  LITHO_TRY_CUDA(cudaMemcpy(h->d_phi, phi.data(), phi.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  LITHO_TRY_CUDA(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  return LITHO_OK;
+}
+
+}  // namespace
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+}  // namespace litho
+
+using namespace litho;
+
+#define LITHO_REQUIRE(cond, msg)       \
+  do {                                 \
+    if (!(cond)) {                     \
+      set_error("%s", msg);            \
+      return LITHO_EINVAL;             \
+    }                                  \
+  } while (0)
+
+extern "C" {
+
+const char* litho_last_error(void) { return g_err; }
+const char* litho_version(void) { return "litho-gb300 0.1 (sm_103a)"; }
+
+void litho_free_kernels(litho_kernels* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  cudaFree(h->d_lambda);
+  cudaFree(h->d_phi);
+  cudaFree(h->d_tw);
+  gemm_free_operands(h);
+  cudaSetDevice(cur);
+  delete h;
+}
+
+litho_status litho_make_kernels(const litho_optics* optics, int n, double pixel_nm, const double* defocus_nm,
+                                int n_focus, int k, litho_kernels** out) {
+  LITHO_REQUIRE(optics && out && defocus_nm, "null argument");
+  *out = nullptr;
+  LITHO_REQUIRE(valid_n(n), "n must be a power of two in [32, 2048]");
+  LITHO_REQUIRE(pixel_nm > 0 && std::isfinite(pixel_nm), "pixel_nm must be > 0");
+  LITHO_REQUIRE(n_focus >= 1 && n_focus <= 64, "n_focus must be in [1, 64]");
+  LITHO_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+  LITHO_REQUIRE(optics->wavelength_nm > 0 && optics->na > 0 && optics->n_medium >= optics->na,
+                "need wavelength > 0 and 0 < NA <= n_medium");
+  for (int f = 0; f < n_focus; ++f) LITHO_REQUIRE(std::isfinite(defocus_nm[f]), "defocus must be finite");
+  SourcePoints src;
+  std::string why;
+  if (!sample_source(*optics, &src, &why)) {
+    set_error("%s", why.c_str());
+    return LITHO_EINVAL;
+  }
+  const int crop = band_crop(*optics, src, n, pixel_nm);
+  auto* h = new (std::nothrow) litho_kernels();
+  if (!h) {
+    set_error("host allocation failed");
+    return LITHO_ENOMEM;
+  }
+  h->n = n;
+  h->crop = crop;
+  h->n_focus = n_focus;
+  h->k = k;
+  h->pixel_nm = pixel_nm;
+  const size_t cc = size_t(crop) * crop;
+  try {
+    h->lambda.assign(size_t(n_focus) * k, 0.0);
+    h->phi_host.assign(size_t(n_focus) * k * cc * 2, 0.0);
+    for (int f = 0; f < n_focus; ++f) {
+      FocusKernels fk;
+      if (!build_focus_kernels(*optics, src, n, pixel_nm, defocus_nm[f], k, crop, &fk, &why)) {
+        set_error("%s", why.c_str());
+        delete h;
+        return LITHO_EINVAL;
+      }
+      h->rank.push_back(fk.rank);
+      h->trace.push_back(fk.trace);
+      h->gap.push_back(fk.gap);
+      for (int i = 0; i < k; ++i) {
+        h->lambda[size_t(f) * k + i] = fk.lambda[i];
+        for (size_t b = 0; b < cc; ++b) {
+          const cd v = fk.phi[size_t(i) * cc + b];
+          h->phi_host[((size_t(f) * k + i) * cc + b) * 2] = v.real();
+          h->phi_host[((size_t(f) * k + i) * cc + b) * 2 + 1] = v.imag();
+        }
+      }
+    }
+  } catch (const std::bad_alloc&) {
+    delete h;
+    set_error("host allocation failed while building kernels");
+    return LITHO_ENOMEM;
+  }
+  litho_status st = upload(h);
+  if (st != LITHO_OK) {
+    litho_free_kernels(h);
+    return st;
+  }
+  *out = h;
+  return LITHO_OK;
+}
+
+litho_status litho_tcc_kernels_host(const litho_optics* optics, int n, double pixel_nm, double defocus_nm, int k,
+                                    int* crop, double* lambda_host, double* phi_host, int* rank, double* trace,
+                                    double* gap) {
+  LITHO_REQUIRE(optics && crop, "null argument");
+  LITHO_REQUIRE(valid_n(n), "n must be a power of two in [32, 2048]");
+  LITHO_REQUIRE(pixel_nm > 0 && std::isfinite(pixel_nm) && std::isfinite(defocus_nm), "bad pixel or defocus");
+  LITHO_REQUIRE(k >= 1 && k <= 1024, "k must be in [1, 1024]");
+  LITHO_REQUIRE(optics->wavelength_nm > 0 && optics->na > 0 && optics->n_medium >= optics->na,
+                "need wavelength > 0 and 0 < NA <= n_medium");
+  SourcePoints src;
+  std::string why;
+  if (!sample_source(*optics, &src, &why)) {
+    set_error("%s", why.c_str());
+    return LITHO_EINVAL;
+  }
+  *crop = band_crop(*optics, src, n, pixel_nm);
+  if (!phi_host) return LITHO_OK;
+  LITHO_REQUIRE(lambda_host, "lambda_host required with phi_host");
+  FocusKernels fk;
+  try {
+    if (!build_focus_kernels(*optics, src, n, pixel_nm, defocus_nm, k, *crop, &fk, &why)) {
+      set_error("%s", why.c_str());
+      return LITHO_EINVAL;
+    }
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed while building kernels");
+    return LITHO_ENOMEM;
+  }
+  for (int i = 0; i < k; ++i) lambda_host[i] = fk.lambda[i];
+  for (size_t i = 0; i < fk.phi.size(); ++i) {
+    phi_host[2 * i] = fk.phi[i].real();
+    phi_host[2 * i + 1] = fk.phi[i].imag();
+  }
+  if (rank) *rank = fk.rank;
+  if (trace) *trace = fk.trace;
+  if (gap) *gap = fk.gap;
+  return LITHO_OK;
+}
+
+litho_status litho_upload_kernels(int n, double pixel_nm, int n_focus, int k, int crop, const double* lambda_host,
+                                  const double* phi_host, litho_kernels** out) {
+  LITHO_REQUIRE(out && lambda_host && phi_host, "null argument");
+  *out = nullptr;
+  LITHO_REQUIRE(valid_n(n), "n must be a power of two in [32, 2048]");
+  LITHO_REQUIRE(crop >= 32 && crop <= n && crop % 32 == 0, "crop must be a multiple of 32 in [32, n]");
+  LITHO_REQUIRE(n_focus >= 1 && n_focus <= 64 && k >= 1 && k <= 1024, "bad n_focus or k");
+  LITHO_REQUIRE(pixel_nm > 0, "pixel_nm must be > 0");
+  for (long long i = 0; i < (long long)n_focus * k; ++i)
+    LITHO_REQUIRE(lambda_host[i] >= 0.0 && std::isfinite(lambda_host[i]), "lambda must be finite and >= 0");
+  auto* h = new (std::nothrow) litho_kernels();
+  if (!h) return LITHO_ENOMEM;
+  h->n = n;
+  h->crop = crop;
+  h->n_focus = n_focus;
+  h->k = k;
+  h->pixel_nm = pixel_nm;
+  const size_t cc = size_t(crop) * crop;
+  h->lambda.assign(lambda_host, lambda_host + size_t(n_focus) * k);
+  h->phi_host.assign(phi_host, phi_host + size_t(n_focus) * k * cc * 2);
+  for (int f = 0; f < n_focus; ++f) {
+    int r = 0;
+    double tr = 0.0;
+    for (int i = 0; i < k; ++i) {
+      r += h->lambda[size_t(f) * k + i] > 0.0;
+      tr += h->lambda[size_t(f) * k + i];
+    }
+    h->rank.push_back(r);
+    h->trace.push_back(tr);
+    h->gap.push_back(0.0);
+  }
+  litho_status st = upload(h);
+  if (st != LITHO_OK) {
+    litho_free_kernels(h);
+    return st;
+  }
+  *out = h;
+  return LITHO_OK;
+}
+
+litho_status litho_kernels_info(const litho_kernels* h, int* n, int* crop, int* n_focus, int* k, int* rank_host,
+                                double* lambda_host, double* trace_host, double* gap_host) {
+  LITHO_REQUIRE(h, "null handle");
+  if (n) *n = h->n;
+  if (crop) *crop = h->crop;
+  if (n_focus) *n_focus = h->n_focus;
+  if (k) *k = h->k;
+  for (int f = 0; f < h->n_focus; ++f) {
+    if (rank_host) rank_host[f] = h->rank[f];
+    if (trace_host) trace_host[f] = h->trace[f];
+    if (gap_host) gap_host[f] = h->gap[f];
+  }
+  if (lambda_host) std::memcpy(lambda_host, h->lambda.data(), h->lambda.size() * sizeof(double));
+  return LITHO_OK;
+}
+
+litho_status litho_kernels_phi(const litho_kernels* h, double* phi_host) {
+  LITHO_REQUIRE(h && phi_host, "null argument");
+  std::memcpy(phi_host, h->phi_host.data(), h->phi_host.size() * sizeof(double));
+  return LITHO_OK;
+}
+
+// ---- aerial ------------------------------------------------------------------------------------------
+
+static size_t aerial_layout(const litho_kernels* h, int b, litho_precision prec, void* ws, float2** rowbuf,
+                            float2** mhat, float2** t1, void** gemm_ws) {
+  Carve c(ws, 0);
+  const size_t N = h->n, C = h->crop, F = h->n_focus, K = h->k;
+  float2* r = c.take<float2>(size_t(b) * N * C);
+  float2* m = c.take<float2>(size_t(b) * C * C);
+  float2* t = nullptr;
+  void* g = nullptr;
+  if (prec == LITHO_PREC_FFT32) {
+    t = c.take<float2>(F * K * N * C);
+  } else {
+    g = c.take<char>(gemm_workspace_bytes(h, prec));
+  }
+  if (rowbuf) *rowbuf = r;
+  if (mhat) *mhat = m;
+  if (t1) *t1 = t;
+  if (gemm_ws) *gemm_ws = g;
+  return align_up(c.used);
+}
+
+litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes) {
+  LITHO_REQUIRE(h && bytes, "null argument");
+  LITHO_REQUIRE(b >= 1, "b must be >= 1");
+  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16X3, "unknown precision");
+  *bytes = aerial_layout(h, b, prec, nullptr, nullptr, nullptr, nullptr, nullptr);
+  return LITHO_OK;
+}
+
+litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, double dose, litho_precision prec,
+                          float* intensity_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+  LITHO_REQUIRE(h && mask_dev && intensity_dev && workspace_dev, "null argument");
+  LITHO_REQUIRE(b >= 1, "b must be >= 1");
+  LITHO_REQUIRE(std::isfinite(dose), "dose must be finite");
+  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16X3, "unknown precision");
+  LITHO_REQUIRE((reinterpret_cast<uintptr_t>(workspace_dev) & 255) == 0, "workspace must be 256-byte aligned");
+  LITHO_REQUIRE((reinterpret_cast<uintptr_t>(mask_dev) & 15) == 0 && (reinterpret_cast<uintptr_t>(intensity_dev) & 15) == 0,
+                "mask and intensity must be 16-byte aligned");
+  const size_t need = aerial_layout(h, b, prec, nullptr, nullptr, nullptr, nullptr, nullptr);
+  if (workspace_bytes < need) {
+    set_error("workspace too small: %zu bytes given, %zu needed", workspace_bytes, need);
+    return LITHO_ENOMEM;
+  }
+  if (prec != LITHO_PREC_FFT32) {
+    litho_status s = gemm_supported(h, prec);
+    if (s != LITHO_OK) return s;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  float2 *rowbuf, *mhat, *t1;
+  void* gws;
+  aerial_layout(h, b, prec, workspace_dev, &rowbuf, &mhat, &t1, &gws);
+  const int N = h->n, C = h->crop, F = h->n_focus, K = h->k;
+  {
+    ProfScope ps(kStageMaskSpectrum, st, 2);
+    LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev, b, N, C, h->d_tw, rowbuf, mhat, st));
+  }
+  for (int clip = 0; clip < b; ++clip) {
+    const float2* mh = mhat + size_t(clip) * C * C;
+    float* img = intensity_dev + size_t(clip) * F * N * N;
+    if (prec == LITHO_PREC_FFT32) {
+      {
+        ProfScope ps(kStageStage1Fft, st, 1);
+        LITHO_TRY_CUDA(launch_stage1_fft(mh, h->d_phi, F * K, N, C, h->d_tw, t1, st));
+      }
+      {
+        ProfScope ps(kStageStage2Fft, st, 1);
+        LITHO_TRY_CUDA(launch_stage2_fft(t1, h->d_lambda, K, N, C, float(dose), h->d_tw, img, F,
+                                         (long long)K * N * C, (long long)N * N, st));
+      }
+    } else {
+      litho_status s = gemm_aerial_clip(h, mh, float(dose), prec, img, gws, st);
+      if (s != LITHO_OK) return s;
+    }
+  }
+  return LITHO_OK;
+}
+
+litho_status litho_aerial_host_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes) {
+  LITHO_REQUIRE(h && bytes && b >= 1, "bad argument");
+  size_t w = 0;
+  litho_status s = litho_aerial_workspace_size(h, b, prec, &w);
+  if (s != LITHO_OK) return s;
+  const size_t nn = size_t(h->n) * h->n, planes = size_t(b) * h->n_focus;
+  *bytes = align_up(w) + align_up(size_t(b) * nn * sizeof(float)) + 2 * align_up(planes * nn * sizeof(float)) +
+           align_up(planes * nn);
+  return LITHO_OK;
+}
+
+litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, int b, double dose,
+                               litho_precision prec, float* intensity_host, double sigma_nm, double threshold,
+                               uint8_t* printed_host, void* workspace_dev, size_t workspace_bytes, void* stream) {
+  LITHO_REQUIRE(h && mask_host && workspace_dev, "null argument");
+  LITHO_REQUIRE(intensity_host || printed_host, "nothing to return: intensity_host and printed_host are both NULL");
+  size_t need = 0, w = 0;
+  litho_status s = litho_aerial_host_workspace_size(h, b, prec, &need);
+  if (s != LITHO_OK) return s;
+  if (workspace_bytes < need) {
+    set_error("workspace too small: %zu bytes given, %zu needed", workspace_bytes, need);
+    return LITHO_ENOMEM;
+  }
+  litho_aerial_workspace_size(h, b, prec, &w);
+  w = align_up(w);
+  const size_t nn = size_t(h->n) * h->n, planes = size_t(b) * h->n_focus;
+  char* base = static_cast<char*>(workspace_dev);
+  float* dmask = reinterpret_cast<float*>(base + w);
+  float* dimg = reinterpret_cast<float*>(base + w + align_up(size_t(b) * nn * sizeof(float)));
+  float* dblur = reinterpret_cast<float*>(reinterpret_cast<char*>(dimg) + align_up(planes * nn * sizeof(float)));
+  uint8_t* dpr = reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(dblur) + align_up(planes * nn * sizeof(float)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  LITHO_TRY_CUDA(cudaMemcpyAsync(dmask, mask_host, size_t(b) * nn * sizeof(float), cudaMemcpyHostToDevice, st));
+  s = litho_aerial(h, dmask, b, dose, prec, dimg, workspace_dev, w, stream);
+  if (s != LITHO_OK) return s;
+  if (printed_host) {
+    s = litho_resist(dimg, int(planes), h->n, h->pixel_nm, sigma_nm, threshold, dblur, dpr, stream);
+    if (s != LITHO_OK) return s;
+    LITHO_TRY_CUDA(cudaMemcpyAsync(printed_host, dpr, planes * nn, cudaMemcpyDeviceToHost, st));
+  }
+  if (intensity_host)
+    LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host, dimg, planes * nn * sizeof(float), cudaMemcpyDeviceToHost, st));
+  LITHO_TRY_CUDA(cudaStreamSynchronize(st));
+  return LITHO_OK;
+}
+
+// ---- resist ------------------------------------------------------------------------------------------
+
+litho_status litho_resist(const float* intensity_dev, int planes, int n, double pixel_nm, double sigma_nm,
+                          double threshold, float* iblur_dev, uint8_t* printed_dev, void* stream) {
+  LITHO_REQUIRE(intensity_dev && iblur_dev, "null argument");
+  LITHO_REQUIRE(planes >= 1 && n >= 32 && n % 32 == 0, "planes >= 1 and n a multiple of 32 required");
+  LITHO_REQUIRE(std::isfinite(threshold), "threshold must be finite");
+  ResistTaps taps;
+  std::string why;
+  if (!resist_taps(sigma_nm, pixel_nm, &taps, &why)) {
+    set_error("%s", why.c_str());
+    return LITHO_EINVAL;
+  }
+  LITHO_REQUIRE(2 * taps.radius < n, "blur radius must be below n/2");
+  ProfScope ps(kStageResist, static_cast<cudaStream_t>(stream), 1);
+  LITHO_TRY_CUDA(launch_resist(intensity_dev, planes, n, taps, float(threshold), iblur_dev, printed_dev,
+                               static_cast<cudaStream_t>(stream)));
+  return LITHO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,235 @@
+// FFT-based kernels: mask spectrum (crop), stage 1 (band multiply + inverse
+// transform over v), and stage 2 of the FP32 path (inverse transform over u
+// fused with the lam_k |E_k|^2 accumulation over all kernels).
+//
+// Paper Section III.A: the object spectrum O(f) of Eq. (1) (thin-mask reading:
+// the mask's DFT), and the SOCS image of Eq. (4), I = sum_k lam_k |O (x) phi_k|^2,
+// evaluated as E_k = IDFT(M . Phi_k) restricted to the C x C band crop.
+//
+// Data layout (all row-major, x fastest):
+//   mask    [b][N][N] f32
+//   rowbuf  [b][N][C] c64   row DFT of the mask, crop columns only
+//   mhat    [b][C][C] c64   N^-2 DFT(m) on the crop, [v][u]
+//   t1      [j][N][C] c64   stage-1 field T_j[y][u] = sum_v mhat[v][u] Phi_j[v][u] e^{2 pi i v y/N}
+//   img     [plane][N][N] f32
+#include "fft_common.cuh"
+#include "litho_internal.h"
+
+namespace litho {
+
+namespace {
+
+__device__ __forceinline__ int freq_of(int idx, int n) { return idx < n / 2 ? idx : idx - n; }
+
+// ---- mask spectrum, pass 1: two real rows per complex transform ----------------------------
+// z = m[y0] + i m[y1]; Z = DFT(z); X(u) = (Z(u) + conj Z(-u))/2, Y(u) = (Z(u) - conj Z(-u))/(2i).
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT) k_mask_rows(const float* __restrict__ m, int crop,
+                                                            const float2* __restrict__ tw_g,
+                                                            float2* __restrict__ rowbuf) {
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* buf = smem + N;
+  float2* zc = smem + 2 * N;  // Z(u) for u in [-C/2, C/2], index u + C/2 (crop + 1 <= N + 1 entries)
+  load_twiddles<N>(tw, tw_g);
+  __syncthreads();
+  const int b = blockIdx.y, y0 = 2 * blockIdx.x;
+  const float* r0 = m + ((size_t)b * N + y0) * N;
+  const float* r1 = r0 + N;
+  const int t = threadIdx.x, half = crop / 2;
+  auto load = [&](int i) { return make_float2(__ldg(r0 + i), __ldg(r1 + i)); };
+  auto use = [&](int, int, int idx, float2 v) {
+    const int u = freq_of(idx, N);
+    if (u >= -half && u <= half) zc[u + half] = v;
+    if (u == -N / 2 && half == N / 2) zc[crop] = v;  // crop == N: Z(N/2) is Z(-N/2)
+  };
+  fft_load_use<N, -1>(buf, tw, t, load, use);
+  __syncthreads();
+  float2* o0 = rowbuf + ((size_t)b * N + y0) * crop;
+  float2* o1 = o0 + crop;
+  for (int c = t; c < crop; c += blockDim.x) {
+    const float2 zp = zc[c], zm = zc[crop - c];
+    o0[c] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+    o1[c] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+  }
+}
+
+// Columns per CTA for the column kernels: W transforms of NT threads each.
+template <int N> struct ColW { static constexpr int W = (N >= 2048) ? 8 : (N >= 512 ? 16 : 32); };
+
+// ---- mask spectrum, pass 2: column DFTs of the crop columns, crop rows kept ------------------
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const float2* __restrict__ rowbuf, int crop,
+                                                                         const float2* __restrict__ tw_g,
+                                                                         float2* __restrict__ mhat) {
+  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = N + 1;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* buf = smem + N;
+  load_twiddles<N>(tw, tw_g);
+  const int b = blockIdx.y, u0 = blockIdx.x * W, tid = threadIdx.x;
+  const float2* src = rowbuf + (size_t)b * N * crop + u0;
+  for (int i = tid; i < N * W; i += blockDim.x) {
+    const int y = i / W, w = i % W;
+    buf[w * LD + y] = src[(size_t)y * crop + w];
+  }
+  __syncthreads();
+  fft_smem<N, -1>(buf + (tid / NT) * LD, tw, tid % NT);
+  const float scale = 1.0f / (float(N) * float(N));
+  float2* dst = mhat + (size_t)b * crop * crop + u0;
+  const int half = crop / 2;
+  for (int i = tid; i < crop * W; i += blockDim.x) {
+    const int cv = i / W, w = i % W;
+    const int idx = (cv - half + N) % N;
+    const float2 v = buf[w * LD + idx];
+    dst[(size_t)cv * crop + w] = make_float2(v.x * scale, v.y * scale);
+  }
+}
+
+// ---- stage 1: band multiply + inverse transform over v, for every kernel j ----------------------
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_stage1(const float2* __restrict__ mhat,
+                                                                      const float2* __restrict__ phi, int crop,
+                                                                      const float2* __restrict__ tw_g,
+                                                                      float2* __restrict__ t1) {
+  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = N + 1;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* buf = smem + N;
+  load_twiddles<N>(tw, tw_g);
+  const int j = blockIdx.y, u0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
+  for (int i = tid; i < W * LD; i += blockDim.x) buf[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2* ph = phi + (size_t)j * crop * crop + u0;
+  const float2* mh = mhat + u0;
+  for (int i = tid; i < crop * W; i += blockDim.x) {
+    const int cv = i / W, w = i % W;
+    const int idx = (cv - half + N) % N;
+    buf[w * LD + idx] = cmul(__ldg(mh + (size_t)cv * crop + w), __ldg(ph + (size_t)cv * crop + w));
+  }
+  __syncthreads();
+  fft_smem<N, +1>(buf + (tid / NT) * LD, tw, tid % NT);
+  float2* dst = t1 + (size_t)j * N * crop + u0;
+  for (int i = tid; i < N * W; i += blockDim.x) {
+    const int y = i / W, w = i % W;
+    dst[(size_t)y * crop + w] = buf[w * LD + y];
+  }
+}
+
+// ---- stage 2 (FP32 path): one image row per CTA, all kernels of the plane ------------------------
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT) k_stage2(const float2* __restrict__ t1, const float* __restrict__ lam,
+                                                        int nk, int crop, float dose,
+                                                        const float2* __restrict__ tw_g, float* __restrict__ img,
+                                                        long long t1_plane, long long img_plane, int lam_plane) {
+  using PL = Plan<N>;
+  constexpr int NT = PL::NT;
+  constexpr int RL = PL::R[PL::P - 1];
+  constexpr int PERL = PassShape<N, NT, RL>::PER;
+  __shared__ float2 buf[N];
+  __shared__ float2 tw[N];
+  load_twiddles<N>(tw, tw_g);
+  __syncthreads();
+  const int y = blockIdx.x, plane = blockIdx.y, t = threadIdx.x, half = crop / 2;
+  const float2* base = t1 + plane * t1_plane + (size_t)y * crop;
+  const float* lp = lam + plane * lam_plane;
+  float acc[PERL][RL];
+#pragma unroll
+  for (int p = 0; p < PERL; ++p)
+#pragma unroll
+    for (int q = 0; q < RL; ++q) acc[p][q] = 0.f;
+  for (int j = 0; j < nk; ++j) {
+    const float l = __ldg(lp + j);
+    if (l == 0.f) continue;  // uniform across the block
+    const float2* row = base + (size_t)j * N * crop;
+    auto load = [&](int idx) {
+      const int c = freq_of(idx, N) + half;
+      return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
+    };
+    auto use = [&](int p, int q, int, float2 v) { acc[p][q] = fmaf(l, fmaf(v.x, v.x, v.y * v.y), acc[p][q]); };
+    fft_load_use<N, +1>(buf, tw, t, load, use);
+  }
+  float* out = img + plane * img_plane + (size_t)y * N;
+#pragma unroll
+  for (int p = 0; p < PERL; ++p) {
+    const int jj = t + p * NT;
+    if (jj < N / RL) {
+#pragma unroll
+      for (int q = 0; q < RL; ++q) out[jj + q * (N / RL)] = dose * acc[p][q];
+    }
+  }
+}
+
+template <int N>
+size_t col_smem_bytes() {
+  return sizeof(float2) * (N + ColW<N>::W * (N + 1));
+}
+
+template <int N>
+cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, float2* rowbuf, float2* mhat,
+                            cudaStream_t st) {
+  const size_t smr = sizeof(float2) * (3 * N + 1);
+  cudaError_t e = cudaFuncSetAttribute(k_mask_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  if (e != cudaSuccess) return e;
+  k_mask_rows<N><<<dim3(N / 2, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf);
+  const size_t sm = col_smem_bytes<N>();
+  e = cudaFuncSetAttribute(k_mask_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_mask_cols<N><<<dim3(crop / ColW<N>::W, b), Plan<N>::NT * ColW<N>::W, sm, st>>>(rowbuf, crop, tw, mhat);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t stage1_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, float2* t1,
+                     cudaStream_t st) {
+  const size_t sm = col_smem_bytes<N>();
+  cudaError_t e = cudaFuncSetAttribute(k_stage1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_stage1<N><<<dim3(crop / ColW<N>::W, nk), Plan<N>::NT * ColW<N>::W, sm, st>>>(mhat, phi, crop, tw, t1);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t stage2_n(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw, float* img,
+                     int planes, long long t1_plane, long long img_plane, cudaStream_t st) {
+  k_stage2<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(t1, lam, nk, crop, dose, tw, img, t1_plane, img_plane, nk);
+  return cudaGetLastError();
+}
+
+#define LITHO_DISPATCH_N(n, CALL)          \
+  switch (n) {                             \
+    case 32: return CALL(32);              \
+    case 64: return CALL(64);              \
+    case 128: return CALL(128);            \
+    case 256: return CALL(256);            \
+    case 512: return CALL(512);            \
+    case 1024: return CALL(1024);          \
+    case 2048: return CALL(2048);          \
+    default: return cudaErrorInvalidValue; \
+  }
+
+}  // namespace
+
+cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
+                                 float2* mhat, cudaStream_t st) {
+#define CALL(N) mask_spectrum_n<N>(m, b, crop, tw, rowbuf, mhat, st)
+  LITHO_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int n, int crop, const float2* tw,
+                              float2* t1, cudaStream_t st) {
+#define CALL(N) stage1_n<N>(mhat, phi, nk, crop, tw, t1, st)
+  LITHO_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
+                              const float2* tw, float* img, int planes, long long t1_plane_stride,
+                              long long img_plane_stride, cudaStream_t st) {
+#define CALL(N) stage2_n<N>(t1, lam, nk, crop, dose, tw, img, planes, t1_plane_stride, img_plane_stride, st)
+  LITHO_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+}  // namespace litho

@@ -1,0 +1,213 @@
+// Shared-memory Stockham FFT building blocks for sm_103a.
+//
+// A length-N transform (N a power of two, 32..2048) is a sequence of radix-R
+// passes (R in {4, 8, 16}); before pass p, `NS` is the product of the earlier
+// radices.  Butterfly j in [0, N/R) of a pass reads x[j + r N/R] (r < R),
+// multiplies element r by w^(r (j mod NS) N/(NS R)) (w = e^{-2 pi i/N}, or its
+// conjugate for the inverse), takes an R-point DFT in registers and writes
+// element q to y[(j div NS) NS R + (j mod NS) + q NS].  This is Stockham's
+// self-sorting formulation: the output comes out in natural order with no bit
+// reversal, and each pass reads and writes with unit stride across threads.
+//
+// The R-point DFTs are radix-2 decimation-in-frequency networks in registers.
+// Twiddles come from a table w[j] = e^{-2 pi i j/N} rounded from FP64 on the
+// host and staged in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace litho {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+// cos and sin of 2 pi t / 16 (exact mathematical constants rounded to float)
+__device__ __forceinline__ constexpr float cos16(int t) {
+  return t == 0 ? 1.0f : t == 1 ? 0.92387953251128674f : t == 2 ? 0.70710678118654752f
+       : t == 3 ? 0.38268343236508977f : t == 4 ? 0.0f : t == 5 ? -0.38268343236508977f
+       : t == 6 ? -0.70710678118654752f : t == 7 ? -0.92387953251128674f : -1.0f;
+}
+__device__ __forceinline__ constexpr float sin16(int t) {
+  return t == 0 ? 0.0f : t == 1 ? 0.38268343236508977f : t == 2 ? 0.70710678118654752f
+       : t == 3 ? 0.92387953251128674f : t == 4 ? 1.0f : t == 5 ? 0.92387953251128674f
+       : t == 6 ? 0.70710678118654752f : t == 7 ? 0.38268343236508977f : 0.0f;
+}
+
+__host__ __device__ __forceinline__ constexpr int ilog2(int x) {
+  int r = 0;
+  while (x > 1) {
+    x >>= 1;
+    ++r;
+  }
+  return r;
+}
+__host__ __device__ __forceinline__ constexpr int bitrev(int q, int bits) {
+  int r = 0;
+  for (int i = 0; i < bits; ++i) r = (r << 1) | ((q >> i) & 1);
+  return r;
+}
+
+// In-register R-point DFT, v'[q] = sum_r v[r] e^{SIGN 2 pi i r q / R}.
+template <int R, int SIGN>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+  static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
+#pragma unroll
+  for (int span = R / 2; span >= 1; span /= 2) {
+#pragma unroll
+    for (int b = 0; b < R; b += 2 * span) {
+#pragma unroll
+      for (int i = 0; i < span; ++i) {
+        const float2 a = v[b + i], c = v[b + i + span];
+        v[b + i] = cadd(a, c);
+        float2 d = csub(a, c);
+        const int t = i * (16 / (2 * span));  // e^{SIGN 2 pi i i/(2 span)} = e^{SIGN 2 pi i t/16}
+        if (t != 0) {
+          const float wr = cos16(t), wi = SIGN * sin16(t);
+          if (t == 4) {
+            d = make_float2(-wi * d.y, wi * d.x);  // multiply by +-i
+          } else {
+            d = make_float2(fmaf(d.x, wr, -d.y * wi), fmaf(d.x, wi, d.y * wr));
+          }
+        }
+        v[b + i + span] = d;
+      }
+    }
+  }
+  constexpr int LB = ilog2(R);
+  float2 o[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) o[q] = v[bitrev(q, LB)];
+#pragma unroll
+  for (int q = 0; q < R; ++q) v[q] = o[q];
+}
+
+// Radix plans: passes in order, product N.  NT = threads per transform.
+template <int N> struct Plan;
+template <> struct Plan<32>   { static constexpr int NT = 32;  static constexpr int R[2] = {8, 4}; static constexpr int P = 2; };
+template <> struct Plan<64>   { static constexpr int NT = 32;  static constexpr int R[2] = {8, 8}; static constexpr int P = 2; };
+template <> struct Plan<128>  { static constexpr int NT = 32;  static constexpr int R[2] = {16, 8}; static constexpr int P = 2; };
+template <> struct Plan<256>  { static constexpr int NT = 32;  static constexpr int R[2] = {16, 16}; static constexpr int P = 2; };
+template <> struct Plan<512>  { static constexpr int NT = 64;  static constexpr int R[3] = {8, 8, 8}; static constexpr int P = 3; };
+template <> struct Plan<1024> { static constexpr int NT = 64;  static constexpr int R[3] = {16, 8, 8}; static constexpr int P = 3; };
+template <> struct Plan<2048> { static constexpr int NT = 128; static constexpr int R[3] = {16, 16, 8}; static constexpr int P = 3; };
+
+template <int N, int NT, int R>
+struct PassShape {
+  static constexpr int NB = N / R;                  // butterflies
+  static constexpr int PER = (NB + NT - 1) / NT;    // butterflies per thread
+};
+
+// Twiddle + DFT of one butterfly's R values.
+template <int N, int R, int NS, int SIGN>
+__device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2* __restrict__ tw) {
+  if (NS > 1) {
+    const int k = j % NS;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = tw[r * k * (N / (NS * R))];
+      if (SIGN > 0) w.y = -w.y;
+      v[r] = cmul(v[r], w);
+    }
+  }
+  dft_reg<R, SIGN>(v);
+}
+
+// One pass whose inputs come from `load(index)` (or shared memory when
+// FROM_SMEM) and whose outputs go to shared memory.  Ends with a barrier.
+template <int N, int NT, int R, int NS, int SIGN, bool FROM_SMEM, class Load>
+__device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int t, Load& load) {
+  using S = PassShape<N, NT, R>;
+  float2 v[S::PER][R];
+#pragma unroll
+  for (int p = 0; p < S::PER; ++p) {
+    const int j = t + p * NT;
+    if (j < S::NB) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[p][r] = FROM_SMEM ? buf[j + r * S::NB] : load(j + r * S::NB);
+      twiddle_dft<N, R, NS, SIGN>(v[p], j, tw);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < S::PER; ++p) {
+    const int j = t + p * NT;
+    if (j < S::NB) {
+      const int base = (j / NS) * NS * R + (j % NS);
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[base + r * NS] = v[p][r];
+    }
+  }
+  __syncthreads();
+}
+
+// Last pass from shared memory; hands each output element to
+// use(p, q, index, value), index = j + q N/R with j = t + p NT (NS R = N, so
+// the Stockham output position of element q is j + q NS).  p and q are
+// compile-time after unrolling, so `use` can index register arrays with them.
+// No barrier at the end.
+template <int N, int NT, int R, int NS, int SIGN, class Use>
+__device__ __forceinline__ void pass_last(const float2* buf, const float2* tw, int t, Use& use) {
+  using S = PassShape<N, NT, R>;
+  static_assert(NS * R == N, "last pass");
+#pragma unroll
+  for (int p = 0; p < S::PER; ++p) {
+    const int j = t + p * NT;
+    if (j < S::NB) {
+      float2 v[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[r] = buf[j + r * S::NB];
+      twiddle_dft<N, R, NS, SIGN>(v, j, tw);
+#pragma unroll
+      for (int q = 0; q < R; ++q) use(p, q, j + q * S::NB, v[q]);
+    }
+  }
+}
+
+struct SmemLoadUnused {
+  __device__ float2 operator()(int) const { return make_float2(0.f, 0.f); }
+};
+
+// Full transform: first pass from `load`, middle passes in shared memory,
+// last pass into `use`.  Threads t in [0, NT) of the calling group take part;
+// every thread of the block must call it (it contains __syncthreads).
+template <int N, int SIGN, class Load, class Use>
+__device__ __forceinline__ void fft_load_use(float2* buf, const float2* tw, int t, Load& load, Use& use) {
+  using PL = Plan<N>;
+  constexpr int NT = PL::NT;
+  if constexpr (PL::P == 2) {
+    pass_to_smem<N, NT, PL::R[0], 1, SIGN, false>(buf, tw, t, load);
+    pass_last<N, NT, PL::R[1], PL::R[0], SIGN>(buf, tw, t, use);
+  } else {
+    pass_to_smem<N, NT, PL::R[0], 1, SIGN, false>(buf, tw, t, load);
+    SmemLoadUnused none;
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, true>(buf, tw, t, none);
+    pass_last<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN>(buf, tw, t, use);
+  }
+}
+
+// Full transform in place in shared memory (buf holds the input on entry and
+// the output on return, natural order).  Ends with a barrier.
+template <int N, int SIGN>
+__device__ __forceinline__ void fft_smem(float2* buf, const float2* tw, int t) {
+  using PL = Plan<N>;
+  constexpr int NT = PL::NT;
+  SmemLoadUnused none;
+  pass_to_smem<N, NT, PL::R[0], 1, SIGN, true>(buf, tw, t, none);
+  if constexpr (PL::P == 2) {
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, true>(buf, tw, t, none);
+  } else {
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, true>(buf, tw, t, none);
+    pass_to_smem<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, true>(buf, tw, t, none);
+  }
+}
+
+// Stage the twiddle table into shared memory (all threads of the block).
+template <int N>
+__device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* __restrict__ g_tw) {
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s_tw[i] = g_tw[i];
+}
+
+}  // namespace litho

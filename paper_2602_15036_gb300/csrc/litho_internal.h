@@ -1,0 +1,120 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/litho.h"
+
+namespace litho {
+
+// thread-local error message behind litho_last_error()
+void set_error(const char* fmt, ...);
+
+#define LITHO_TRY_CUDA(expr)                                                                   \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      ::litho::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return LITHO_ECUDA;                                                                      \
+    }                                                                                          \
+  } while (0)
+
+using cd = std::complex<double>;
+
+// ---- per-stage device timing (prof.cpp) ------------------------------------------------------
+enum Stage {
+  kStageMaskSpectrum = 0,
+  kStageStage1Fft,
+  kStageStage2Fft,
+  kStageGemmOperands,
+  kStageStage2Gemm,
+  kStageResist,
+  kStageIltForward,
+  kStageIltBackward,
+  kStageIltReduce,
+  kStageCount
+};
+// Records a CUDA event pair around its lifetime on `st` when profiling is on.
+class ProfScope {
+ public:
+  ProfScope(int stage, cudaStream_t st, int launches);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  int stage_;
+  cudaStream_t st_;
+  int launches_;
+  void* a_ = nullptr;
+};
+
+// ---- host optics builder (optics.cpp) -------------------------------------------------------
+struct SourcePoints {
+  std::vector<double> sx, sy, w;  // units of NA/wavelength; sum w = 1
+};
+bool sample_source(const litho_optics& o, SourcePoints* out, std::string* why);
+int band_crop(const litho_optics& o, const SourcePoints& s, int n, double pixel_nm);
+
+struct FocusKernels {
+  std::vector<double> lambda;  // [k], descending, 0 beyond rank
+  std::vector<cd> phi;         // [k][C][C]
+  int rank = 0;
+  double trace = 0.0, gap = 0.0;
+};
+// Eigen-kernels of the TCC of one focus plane (Eqs. (2)-(3)).
+bool build_focus_kernels(const litho_optics& o, const SourcePoints& s, int n, double pixel_nm, double z_nm, int k,
+                         int crop, FocusKernels* out, std::string* why);
+// Cyclic Jacobi for a Hermitian matrix (row-major, n x n, destroyed). Eigenvalues
+// ascending in `ev` are not guaranteed: the caller sorts.  V columns = eigenvectors.
+void hermitian_jacobi(std::vector<cd>& a, int n, std::vector<double>& ev, std::vector<cd>& v);
+
+// ---- device data for the GEMM path --------------------------------------------------------
+struct GemmOperands;  // gemm.cu
+
+}  // namespace litho
+
+struct litho_kernels {
+  int n = 0, crop = 0, n_focus = 0, k = 0;
+  double pixel_nm = 0.0;
+  std::vector<int> rank;
+  std::vector<double> lambda, trace, gap;  // [F*K], [F], [F]
+  std::vector<double> phi_host;            // [F][K][C][C][2]
+  float* d_lambda = nullptr;               // [F*K]
+  float2* d_phi = nullptr;                 // [F][K][C][C]
+  float2* d_tw = nullptr;                  // e^{-2 pi i j/N}, j in [0, N)
+  litho::GemmOperands* gemm = nullptr;     // lazily built per precision
+  int device = 0;
+};
+
+namespace litho {
+
+// ---- launchers (fft.cu) ---------------------------------------------------------------------
+// Mask spectrum: m[b][n][n] -> mhat[b][C][C] = N^-2 DFT(m) on the crop.  rowbuf: [b][n][C].
+cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
+                                 float2* mhat, cudaStream_t st);
+// Stage 1 (band multiply + inverse DFT over v): for kernels phi[nk][C][C],
+// t1[j][y][c] = sum_v mhat[v][c] phi_j[v][c] e^{+2 pi i v y/N}, j in [0, nk).
+cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int n, int crop, const float2* tw,
+                              float2* t1, cudaStream_t st);
+// Stage 2 FFT path: I[y][x] (+)= dose * sum_j lam[j] |sum_c t1[j][y][c] e^{+2 pi i u_c x/N}|^2.
+cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
+                              const float2* tw, float* img, int planes, long long t1_plane_stride,
+                              long long img_plane_stride, cudaStream_t st);
+
+// ---- resist (resist.cu) ---------------------------------------------------------------------
+constexpr int kMaxResistRadius = 64;
+struct ResistTaps {
+  int radius;
+  float g[2 * kMaxResistRadius + 1];
+};
+bool resist_taps(double sigma_nm, double pixel_nm, ResistTaps* t, std::string* why);
+cudaError_t launch_resist(const float* img, int planes, int n, const ResistTaps& taps, float threshold, float* iblur,
+                          uint8_t* printed, cudaStream_t st);
+
+}  // namespace litho

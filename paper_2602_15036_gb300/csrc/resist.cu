@@ -1,0 +1,88 @@
+// Resist model (paper Eq. (5)): I_blur = g (x) I with a periodic, separable,
+// normalised Gaussian g[j] ~ exp(-(j p)^2 / (2 s^2)), |j| <= R = ceil(4 s / p),
+// then printed = [I_blur >= T] (ties print, as the ">=" of Eqs. (16)-(17)).
+//
+// One pass over HBM: each CTA loads a (TY + 2R) x (TX + 2R) tile with a
+// periodic halo into shared memory, blurs rows into a second tile, blurs
+// columns from it and writes I_blur (f32) and printed (u8) once.
+#include <cmath>
+
+#include "litho_internal.h"
+
+namespace litho {
+
+namespace {
+
+constexpr int TX = 32, TY = 32, BY = 8;
+
+__global__ void __launch_bounds__(TX * BY) k_resist(const float* __restrict__ img, int n, ResistTaps taps, float thr,
+                                                    float* __restrict__ iblur, uint8_t* __restrict__ printed) {
+  extern __shared__ float sm[];
+  const int r = taps.radius, hw = TX + 2 * r, hh = TY + 2 * r;
+  float* tile = sm;             // [hh][hw]
+  float* rows = sm + hh * hw;   // [hh][TX]
+  const int plane = blockIdx.z, x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const float* src = img + (size_t)plane * n * n;
+  const int tid = threadIdx.y * TX + threadIdx.x, nth = TX * BY;
+  for (int i = tid; i < hh * hw; i += nth) {
+    const int ty = i / hw, tx = i % hw;
+    const int gy = (y0 + ty - r + n) % n, gx = (x0 + tx - r + n) % n;
+    tile[i] = __ldg(src + (size_t)gy * n + gx);
+  }
+  __syncthreads();
+  // rows: rows[ty][x] = sum_a g[a] tile[ty][x + r - a]
+  for (int i = tid; i < hh * TX; i += nth) {
+    const int ty = i / TX, x = i % TX;
+    const float* t = tile + ty * hw + x + r;
+    float acc = 0.f;
+    for (int a = -r; a <= r; ++a) acc = fmaf(taps.g[a + r], t[-a], acc);
+    rows[i] = acc;
+  }
+  __syncthreads();
+  float* dst = iblur + (size_t)plane * n * n;
+  uint8_t* pr = printed ? printed + (size_t)plane * n * n : nullptr;
+  for (int yy = threadIdx.y; yy < TY; yy += BY) {
+    const int x = threadIdx.x;
+    const float* c = rows + (yy + r) * TX + x;
+    float acc = 0.f;
+    for (int a = -r; a <= r; ++a) acc = fmaf(taps.g[a + r], c[-a * TX], acc);
+    const size_t o = (size_t)(y0 + yy) * n + x0 + x;
+    dst[o] = acc;
+    if (pr) pr[o] = acc >= thr ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+bool resist_taps(double sigma_nm, double pixel_nm, ResistTaps* t, std::string* why) {
+  if (!(sigma_nm > 0.0) || !(pixel_nm > 0.0)) {
+    *why = "sigma_nm and pixel_nm must be > 0";
+    return false;
+  }
+  const int r = int(std::ceil(4.0 * sigma_nm / pixel_nm));
+  if (r > kMaxResistRadius) {
+    *why = "resist blur radius ceil(4 sigma / pixel) above 64 pixels";
+    return false;
+  }
+  double g[2 * kMaxResistRadius + 1], sum = 0.0;
+  for (int j = -r; j <= r; ++j) {
+    g[j + r] = std::exp(-(j * pixel_nm) * (j * pixel_nm) / (2.0 * sigma_nm * sigma_nm));
+    sum += g[j + r];
+  }
+  t->radius = r;
+  for (int j = 0; j < 2 * r + 1; ++j) t->g[j] = float(g[j] / sum);
+  return true;
+}
+
+cudaError_t launch_resist(const float* img, int planes, int n, const ResistTaps& taps, float threshold, float* iblur,
+                          uint8_t* printed, cudaStream_t st) {
+  if (n % TX != 0 || n % TY != 0 || 2 * taps.radius >= n) return cudaErrorInvalidValue;
+  const int r = taps.radius;
+  const size_t sm = sizeof(float) * ((TY + 2 * r) * (TX + 2 * r) + (TY + 2 * r) * TX);
+  cudaError_t e = cudaFuncSetAttribute(k_resist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_resist<<<dim3(n / TX, n / TY, planes), dim3(TX, BY), sm, st>>>(img, n, taps, threshold, iblur, printed);
+  return cudaGetLastError();
+}
+
+}  // namespace litho

@@ -1,0 +1,317 @@
+"""Python binding of liblitho.so (ctypes): the C ABI of include/litho.h, same names.
+
+Argument marshalling only: every step of the imaging, resist and gradient
+path runs in the library's CUDA kernels.  torch tensors supply device memory
+and streams (`tensor.data_ptr()`, `torch.cuda.current_stream().cuda_stream`).
+If the shared library is missing this module raises at import of the
+library, never falls back to another implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_size_t, c_uint8, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblitho.so")
+
+OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ECANCELED, EUNSUPPORTED = range(8)
+STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EBUSY", "ETIMEOUT", "ECANCELED", "EUNSUPPORTED"]
+
+SRC_ANNULAR, SRC_QUADRUPOLE, SRC_CUSTOM = 0, 1, 2
+PREC = {"fft32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3}
+REQ_IMAGE, REQ_ILT_STEP = 0, 1
+
+
+class LithoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class litho_optics(ctypes.Structure):
+    _fields_ = [("wavelength_nm", c_double), ("na", c_double), ("n_medium", c_double), ("kind", c_int),
+                ("src_grid", c_int), ("sigma_in", c_double), ("sigma_out", c_double), ("pole_sigma", c_double),
+                ("pole_radius", c_double), ("custom_w", POINTER(c_double))]
+
+
+class litho_request(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("optics", litho_optics), ("n", c_int), ("pixel_nm", c_double),
+                ("defocus_nm", c_double), ("k", c_int), ("precision", c_int), ("dose", c_double),
+                ("sigma_nm", c_double), ("threshold", c_double), ("mask_steep", c_double),
+                ("resist_steep", c_double), ("input_host", c_void_p), ("target_host", c_void_p),
+                ("output_host", c_void_p), ("loss_host", c_void_p)]
+
+
+class litho_serve_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("rejected", c_uint64), ("cancelled", c_uint64),
+                ("p50_ms", c_double), ("p99_ms", c_double), ("mpx_per_s", c_double), ("hbm_high_water", c_size_t),
+                ("kernel_sets_cached", c_int)]
+
+
+# name -> (restype, argtypes); mirrors include/litho.h
+_SIGS = {
+    "litho_make_kernels": (c_int, [POINTER(litho_optics), c_int, c_double, POINTER(c_double), c_int, c_int,
+                                   POINTER(c_void_p)]),
+    "litho_tcc_kernels_host": (c_int, [POINTER(litho_optics), c_int, c_double, c_double, c_int, POINTER(c_int),
+                                       POINTER(c_double), POINTER(c_double), POINTER(c_int), POINTER(c_double),
+                                       POINTER(c_double)]),
+    "litho_upload_kernels": (c_int, [c_int, c_double, c_int, c_int, c_int, POINTER(c_double), POINTER(c_double),
+                                     POINTER(c_void_p)]),
+    "litho_kernels_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                   POINTER(c_int), POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+    "litho_kernels_phi": (c_int, [c_void_p, POINTER(c_double)]),
+    "litho_free_kernels": (None, [c_void_p]),
+    "litho_aerial_workspace_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
+    "litho_aerial": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "litho_aerial_host_workspace_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
+    "litho_aerial_host": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_double, c_double,
+                                  c_void_p, c_void_p, c_size_t, c_void_p]),
+    "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
+    "litho_ilt_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
+    "litho_ilt_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double, c_double,
+                               c_int, c_void_p, POINTER(c_double), c_void_p, c_size_t, c_void_p]),
+    "litho_serve_create": (c_int, [c_size_t, c_int, c_int, POINTER(c_void_p)]),
+    "litho_serve_submit": (c_int, [c_void_p, POINTER(litho_request), POINTER(c_uint64)]),
+    "litho_serve_poll": (c_int, [c_void_p, c_uint64, c_int]),
+    "litho_serve_cancel": (c_int, [c_void_p, c_uint64]),
+    "litho_serve_stats": (c_int, [c_void_p, POINTER(litho_serve_stats_t)]),
+    "litho_serve_destroy": (None, [c_void_p]),
+    "litho_profile_enable": (c_int, [c_int]),
+    "litho_profile_reset": (None, []),
+    "litho_profile_read": (c_int, [c_int, c_char_p, POINTER(c_double), POINTER(ctypes.c_longlong), POINTER(c_int)]),
+    "litho_last_error": (c_char_p, []),
+    "litho_version": (c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """Loads liblitho.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2602_15036_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != OK:
+        raise LithoError(status, lib().litho_last_error().decode())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def make_optics(wavelength_nm=193.0, na=1.35, n_medium=1.44, kind="annular", src_grid=21, sigma_in=0.6,
+                sigma_out=0.9, pole_sigma=0.8, pole_radius=0.1, custom_w=None):
+    kinds = {"annular": SRC_ANNULAR, "quadrupole": SRC_QUADRUPOLE, "custom": SRC_CUSTOM}
+    o = litho_optics(wavelength_nm, na, n_medium, kinds[kind] if isinstance(kind, str) else int(kind), src_grid,
+                     sigma_in, sigma_out, pole_sigma, pole_radius, None)
+    if custom_w is not None:
+        arr = np.ascontiguousarray(custom_w, dtype=np.float64)
+        o._keep = arr
+        o.custom_w = arr.ctypes.data_as(POINTER(c_double))
+    return o
+
+
+class Kernels:
+    """Owner of a device-resident litho_kernels handle."""
+
+    def __init__(self, handle: int):
+        self.handle = c_void_p(handle)
+        n, c, f, k = c_int(), c_int(), c_int(), c_int()
+        _check(lib().litho_kernels_info(self.handle, byref(n), byref(c), byref(f), byref(k), None, None, None, None))
+        self.n, self.crop, self.n_focus, self.k = n.value, c.value, f.value, k.value
+
+    def info(self):
+        f, k = self.n_focus, self.k
+        rank = (c_int * f)()
+        lam = np.zeros(f * k)
+        tr = np.zeros(f)
+        gap = np.zeros(f)
+        _check(lib().litho_kernels_info(self.handle, None, None, None, None, rank,
+                                        lam.ctypes.data_as(POINTER(c_double)), tr.ctypes.data_as(POINTER(c_double)),
+                                        gap.ctypes.data_as(POINTER(c_double))))
+        return {"rank": list(rank), "lambda": lam.reshape(f, k), "trace": tr, "gap": gap}
+
+    def phi(self):
+        out = np.zeros((self.n_focus, self.k, self.crop, self.crop, 2))
+        _check(lib().litho_kernels_phi(self.handle, out.ctypes.data_as(POINTER(c_double))))
+        return out[..., 0] + 1j * out[..., 1]
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().litho_free_kernels(self.handle)
+            self.handle = c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def litho_make_kernels(optics, n, pixel_nm, defocus_nm, k) -> Kernels:
+    z = np.ascontiguousarray(np.atleast_1d(defocus_nm), dtype=np.float64)
+    h = c_void_p()
+    _check(lib().litho_make_kernels(byref(optics), n, pixel_nm, z.ctypes.data_as(POINTER(c_double)), len(z), k,
+                                    byref(h)))
+    return Kernels(h.value)
+
+
+def litho_tcc_kernels_host(optics, n, pixel_nm, defocus_nm, k):
+    """FP64 host kernel build for one focus plane (no GPU): returns
+    (lam[k], phi[k][C][C] complex128, info dict)."""
+    crop = c_int()
+    _check(lib().litho_tcc_kernels_host(byref(optics), n, pixel_nm, defocus_nm, k, byref(crop), None, None, None,
+                                        None, None))
+    c = crop.value
+    lam = np.zeros(k)
+    phi = np.zeros((k, c, c, 2))
+    rank, tr, gap = c_int(), c_double(), c_double()
+    _check(lib().litho_tcc_kernels_host(byref(optics), n, pixel_nm, defocus_nm, k, byref(crop),
+                                        lam.ctypes.data_as(POINTER(c_double)), phi.ctypes.data_as(POINTER(c_double)),
+                                        byref(rank), byref(tr), byref(gap)))
+    return lam, phi[..., 0] + 1j * phi[..., 1], {"rank": rank.value, "trace": tr.value, "gap": gap.value}
+
+
+def litho_upload_kernels(n, pixel_nm, lam, phi) -> Kernels:
+    """lam [F][K] float64, phi [F][K][C][C] complex."""
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    f, k = lam.shape
+    phi = np.asarray(phi)
+    c = phi.shape[-1]
+    inter = np.ascontiguousarray(np.stack([phi.real, phi.imag], axis=-1), dtype=np.float64)
+    h = c_void_p()
+    _check(lib().litho_upload_kernels(n, pixel_nm, f, k, c, lam.ctypes.data_as(POINTER(c_double)),
+                                      inter.ctypes.data_as(POINTER(c_double)), byref(h)))
+    return Kernels(h.value)
+
+
+def litho_aerial_workspace_size(kern: Kernels, b: int, precision="fft32") -> int:
+    out = c_size_t()
+    _check(lib().litho_aerial_workspace_size(kern.handle, b, PREC[precision], byref(out)))
+    return out.value
+
+
+def litho_aerial(kern: Kernels, mask, dose=1.0, precision="fft32", out=None, workspace=None, stream=None):
+    """mask: torch float32 CUDA tensor [b][n][n] -> intensity [b][F][n][n]."""
+    import torch
+    assert mask.is_cuda and mask.dtype == torch.float32 and mask.is_contiguous()
+    b = mask.shape[0]
+    if out is None:
+        out = torch.empty((b, kern.n_focus, kern.n, kern.n), dtype=torch.float32, device=mask.device)
+    if workspace is None:
+        workspace = torch.empty(litho_aerial_workspace_size(kern, b, precision), dtype=torch.uint8,
+                                device=mask.device)
+    _check(lib().litho_aerial(kern.handle, c_void_p(mask.data_ptr()), b, dose, PREC[precision],
+                              c_void_p(out.data_ptr()), c_void_p(workspace.data_ptr()), workspace.numel(),
+                              _stream_ptr(stream)))
+    return out
+
+
+def litho_aerial_host_workspace_size(kern: Kernels, b: int, precision="fft32") -> int:
+    out = c_size_t()
+    _check(lib().litho_aerial_host_workspace_size(kern.handle, b, PREC[precision], byref(out)))
+    return out.value
+
+
+def litho_aerial_host(kern: Kernels, mask_host, workspace, intensity_host=None, printed_host=None, dose=1.0,
+                      precision="fft32", sigma_nm=10.0, threshold=0.3, stream=None):
+    """mask_host [b][n][n] f32, intensity_host [b][F][n][n] f32 and/or printed_host
+    [b][F][n][n] u8: CPU tensors (pinned for full-speed copies) or numpy arrays.
+    Synchronous."""
+    def ptr(a):
+        if a is None:
+            return None
+        return c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else c_void_p(a.ctypes.data)
+    b = mask_host.shape[0]
+    _check(lib().litho_aerial_host(kern.handle, ptr(mask_host), b, dose, PREC[precision], ptr(intensity_host),
+                                   sigma_nm, threshold, ptr(printed_host), c_void_p(workspace.data_ptr()),
+                                   workspace.numel(), _stream_ptr(stream)))
+    return intensity_host, printed_host
+
+
+def litho_resist(intensity, pixel_nm, sigma_nm=10.0, threshold=0.3, iblur=None, printed=None, want_printed=True,
+                 stream=None):
+    """intensity: CUDA float32 [..., n, n] -> (iblur, printed u8 or None)."""
+    import torch
+    n = intensity.shape[-1]
+    planes = intensity.numel() // (n * n)
+    if iblur is None:
+        iblur = torch.empty_like(intensity)
+    if printed is None and want_printed:
+        printed = torch.empty(intensity.shape, dtype=torch.uint8, device=intensity.device)
+    _check(lib().litho_resist(c_void_p(intensity.data_ptr()), planes, n, pixel_nm, sigma_nm, threshold,
+                              c_void_p(iblur.data_ptr()), c_void_p(printed.data_ptr()) if printed is not None else None,
+                              _stream_ptr(stream)))
+    return iblur, printed
+
+
+def litho_ilt_workspace_size(kern: Kernels, b: int):
+    full, mn = c_size_t(), c_size_t()
+    _check(lib().litho_ilt_workspace_size(kern.handle, b, byref(full), byref(mn)))
+    return full.value, mn.value
+
+
+def litho_ilt_grad(kern: Kernels, theta, target, dose=1.0, mask_steep=4.0, resist_steep=25.0, threshold=0.3,
+                   sigma_nm=10.0, precision="fft32", grad=None, workspace=None, want_loss=True, stream=None):
+    """theta, target: CUDA float32 [b][n][n] -> (grad, loss[b] float64 numpy or None)."""
+    import torch
+    b = theta.shape[0]
+    if grad is None:
+        grad = torch.empty_like(theta)
+    if workspace is None:
+        workspace = torch.empty(litho_ilt_workspace_size(kern, b)[0], dtype=torch.uint8, device=theta.device)
+    loss = np.zeros(b) if want_loss else None
+    _check(lib().litho_ilt_grad(kern.handle, c_void_p(theta.data_ptr()), c_void_p(target.data_ptr()), b, dose,
+                                mask_steep, resist_steep, threshold, sigma_nm, PREC[precision],
+                                c_void_p(grad.data_ptr()),
+                                loss.ctypes.data_as(POINTER(c_double)) if want_loss else None,
+                                c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream)))
+    return grad, loss
+
+
+def litho_profile_enable(on: bool = True):
+    _check(lib().litho_profile_enable(1 if on else 0))
+
+
+def litho_profile_reset():
+    lib().litho_profile_reset()
+
+
+def litho_profile_read() -> dict:
+    """{stage: (total device ms, kernel launches)} since the last reset."""
+    mx = 16
+    names = ctypes.create_string_buffer(32 * mx)
+    ms = (c_double * mx)()
+    launches = (ctypes.c_longlong * mx)()
+    cnt = c_int()
+    _check(lib().litho_profile_read(mx, names, ms, launches, byref(cnt)))
+    out = {}
+    for i in range(cnt.value):
+        nm = names.raw[32 * i:32 * (i + 1)].split(b"\0")[0].decode()
+        out[nm] = (ms[i], launches[i])
+    return out
+
+
+def litho_last_error() -> str:
+    return lib().litho_last_error().decode()
+
+
+def litho_version() -> str:
+    return lib().litho_version().decode()

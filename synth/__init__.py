@@ -87,19 +87,27 @@ def random_rect_mask(n: int, seed: int, count: int = 40, side_lo: int = 5, side_
 def manhattan_mask(n: int, seed: int, density: float = 0.35, side_lo: int = 5, side_hi: int = 15,
                    block: int = 64) -> np.ndarray:
     """Rectangles as in `random_rect_mask`, added in blocks of `block` until the
-    covered fraction reaches `density` (checked after each block)."""
+    covered fraction reaches `density` (checked after each block).
+
+    Draw order per block: `block` (width, height) pairs, then `block` (x0, y0)
+    pairs.  Coverage is counted incrementally (newly covered pixels per rectangle).
+    """
     st = Stream(seed)
     m = np.zeros((n, n), dtype=np.float32)
-    while m.mean() < density:
+    covered = 0
+    target = density * n * n
+    while covered < target:
         wh = st.integers(side_lo, side_hi, 2 * block).reshape(block, 2)
         xy = st.integers(0, n - 1, 2 * block).reshape(block, 2)
         for (w, h), (x0, y0) in zip(wh, xy):
-            xs = np.arange(x0, x0 + w) % n
-            ys = np.arange(y0, y0 + h) % n
             if x0 + w <= n and y0 + h <= n:
-                m[y0:y0 + h, x0:x0 + w] = 1.0
+                view = m[y0:y0 + h, x0:x0 + w]
+                covered += int(view.size - np.count_nonzero(view))
+                view[...] = 1.0
             else:
-                m[np.ix_(ys, xs)] = 1.0
+                ix = np.ix_(np.arange(y0, y0 + h) % n, np.arange(x0, x0 + w) % n)
+                covered += int(w * h - np.count_nonzero(m[ix]))
+                m[ix] = 1.0
     return m
 
 
