@@ -149,6 +149,29 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
                                litho_precision prec, float* intensity_host, double sigma_nm, double threshold,
                                uint8_t* printed_host, void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* The FP32 aerial image (same result as litho_aerial with LITHO_PREC_FFT32)
+ * without any device allocation and without a workspace argument.  The paper
+ * has no counterpart: this exists for callers that cannot allocate device
+ * memory when they call in, such as a host application that owns all device
+ * memory through its own pool, or a latency-critical loop that cannot take
+ * the device-wide stall cudaMalloc/cudaFree may cause.
+ * Scratch lives in one fixed library array of litho_aerial_noalloc_max_bytes()
+ * bytes (32 MiB) that every GPU loading the library reserves until exit.
+ * Clips are imaged one after another; the scratch one clip needs (row and
+ * crop spectra plus n_focus*k stage-1 fields, about 8*N*C*(1 + n_focus*k)
+ * bytes) must fit, else EINVAL with the sizes in the message (for example
+ * N = 256 with 8 kernels fits; N = 2048 with 72 kernel planes does not).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and each call
+ * overwrites what the previous one left: calls that can run at the same time
+ * on the GPU (different streams, or different host threads) race and corrupt
+ * each other's results; serialise them on one stream.  Asynchronous on
+ * `stream`. */
+litho_status litho_aerial_noalloc(const litho_kernels* h, const float* mask_dev, int b, double dose,
+                                  float* intensity_dev, void* stream);
+size_t litho_aerial_noalloc_max_bytes(void);
+
 /* ---- resist (paper Eq. (5)) ------------------------------------------------------------------- */
 
 /* iblur = g (x) I with the periodic separable Gaussian g[j] ~ exp(-(j p)^2 / (2 s^2)),

@@ -69,6 +69,8 @@ _SIGS = {
     "litho_aerial_host_workspace_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
     "litho_aerial_host": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_double, c_double,
                                   c_void_p, c_void_p, c_size_t, c_void_p]),
+    "litho_aerial_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]),
+    "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
     "litho_ilt_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
     "litho_ilt_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double, c_double,
@@ -244,6 +246,21 @@ def litho_aerial_host(kern: Kernels, mask_host, workspace, intensity_host=None, 
                                    sigma_nm, threshold, ptr(printed_host), c_void_p(workspace.data_ptr()),
                                    workspace.numel(), _stream_ptr(stream)))
     return intensity_host, printed_host
+
+
+def litho_aerial_noalloc(kern: Kernels, mask, out, dose=1.0, stream=None):
+    """FP32 aerial image with no device allocation: the library's fixed scratch
+    array stands in for the workspace, so `out` must be preallocated
+    ([b][F][n][n] float32 on the device).  Calls that may overlap on the GPU
+    race on that array; keep them on one stream."""
+    assert mask.is_cuda and out.is_cuda and mask.is_contiguous() and out.is_contiguous()
+    _check(lib().litho_aerial_noalloc(kern.handle, c_void_p(mask.data_ptr()), mask.shape[0], dose,
+                                      c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def litho_aerial_noalloc_max_bytes() -> int:
+    return int(lib().litho_aerial_noalloc_max_bytes())
 
 
 def litho_resist(intensity, pixel_nm, sigma_nm=10.0, threshold=0.3, iblur=None, printed=None, want_printed=True,
