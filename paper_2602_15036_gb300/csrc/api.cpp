@@ -41,9 +41,9 @@ litho_status upload(litho_kernels* h) {
   std::vector<float2> phi(size_t(F) * K * C * C);
   for (size_t i = 0; i < phi.size(); ++i) phi[i] = make_float2(float(h->phi_host[2 * i]), float(h->phi_host[2 * i + 1]));
   std::vector<float2> tw(N);
-  for (int j = 0; j < N; ++j) {
-    const double a = 2.0 * M_PI * double(j) / double(N);
-    tw[j] = make_float2(float(std::cos(a)), float(-std::sin(a)));
+  if (!fft_twiddle_table(N, tw.data())) {
+    set_error("no FFT plan for n = %d", N);
+    return LITHO_EINVAL;
   }
   LITHO_TRY_CUDA(cudaMalloc(&h->d_lambda, lam.size() * sizeof(float)));
   LITHO_TRY_CUDA(cudaMalloc(&h->d_phi, phi.size() * sizeof(float2)));

@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_mask_rows(const float* __restri
   extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* buf = smem + N;
-  float2* zc = smem + 2 * N;  // Z(u) for u in [-C/2, C/2], index u + C/2 (crop + 1 <= N + 1 entries)
+  float2* zc = smem + N + PadLen<N>::value;  // Z(u) for u in [-C/2, C/2], index u + C/2 (crop + 1 <= N + 1 entries)
   load_twiddles<N>(tw, tw_g);
   __syncthreads();
   const int b = blockIdx.y, y0 = 2 * blockIdx.x;
@@ -56,13 +56,16 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_mask_rows(const float* __restri
 
 // Columns per CTA for the column kernels: W transforms of NT threads each.
 template <int N> struct ColW { static constexpr int W = (N >= 2048) ? 8 : (N >= 512 ? 16 : 32); };
+// Column stride in shared memory: the padded length plus one, so that the
+// cooperative loads across columns (w fastest) fall into different banks.
+template <int N> struct ColLD { static constexpr int value = PadLen<N>::value + 1; };
 
 // ---- mask spectrum, pass 2: column DFTs of the crop columns, crop rows kept ------------------
 template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const float2* __restrict__ rowbuf, int crop,
                                                                          const float2* __restrict__ tw_g,
                                                                          float2* __restrict__ mhat) {
-  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = N + 1;
+  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
   extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* buf = smem + N;
@@ -71,7 +74,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const fl
   const float2* src = rowbuf + (size_t)b * N * crop + u0;
   for (int i = tid; i < N * W; i += blockDim.x) {
     const int y = i / W, w = i % W;
-    buf[w * LD + y] = src[(size_t)y * crop + w];
+    buf[w * LD + pad16(y)] = src[(size_t)y * crop + w];
   }
   __syncthreads();
   fft_smem<N, -1>(buf + (tid / NT) * LD, tw, tid % NT);
@@ -81,7 +84,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const fl
   for (int i = tid; i < crop * W; i += blockDim.x) {
     const int cv = i / W, w = i % W;
     const int idx = (cv - half + N) % N;
-    const float2 v = buf[w * LD + idx];
+    const float2 v = buf[w * LD + pad16(idx)];
     dst[(size_t)cv * crop + w] = make_float2(v.x * scale, v.y * scale);
   }
 }
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_stage1(const float
                                                                       const float2* __restrict__ phi, int crop,
                                                                       const float2* __restrict__ tw_g,
                                                                       float2* __restrict__ t1) {
-  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = N + 1;
+  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
   extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* buf = smem + N;
@@ -105,20 +108,20 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_stage1(const float
   for (int i = tid; i < crop * W; i += blockDim.x) {
     const int cv = i / W, w = i % W;
     const int idx = (cv - half + N) % N;
-    buf[w * LD + idx] = cmul(__ldg(mh + (size_t)cv * crop + w), __ldg(ph + (size_t)cv * crop + w));
+    buf[w * LD + pad16(idx)] = cmul(__ldg(mh + (size_t)cv * crop + w), __ldg(ph + (size_t)cv * crop + w));
   }
   __syncthreads();
   fft_smem<N, +1>(buf + (tid / NT) * LD, tw, tid % NT);
   float2* dst = t1 + (size_t)j * N * crop + u0;
   for (int i = tid; i < N * W; i += blockDim.x) {
     const int y = i / W, w = i % W;
-    dst[(size_t)y * crop + w] = buf[w * LD + y];
+    dst[(size_t)y * crop + w] = buf[w * LD + pad16(y)];
   }
 }
 
 // ---- stage 2 (FP32 path): one image row per CTA, all kernels of the plane ------------------------
 template <int N>
-__global__ void __launch_bounds__(Plan<N>::NT) k_stage2(const float2* __restrict__ t1, const float* __restrict__ lam,
+__global__ void __launch_bounds__(Plan<N>::NT, 4) k_stage2(const float2* __restrict__ t1, const float* __restrict__ lam,
                                                         int nk, int crop, float dose,
                                                         const float2* __restrict__ tw_g, float* __restrict__ img,
                                                         long long t1_plane, long long img_plane, int lam_plane) {
@@ -126,7 +129,7 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_stage2(const float2* __restrict
   constexpr int NT = PL::NT;
   constexpr int RL = PL::R[PL::P - 1];
   constexpr int PERL = PassShape<N, NT, RL>::PER;
-  __shared__ float2 buf[N];
+  __shared__ float2 buf[PadLen<N>::value];
   __shared__ float2 tw[N];
   load_twiddles<N>(tw, tw_g);
   __syncthreads();
@@ -162,13 +165,13 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_stage2(const float2* __restrict
 
 template <int N>
 size_t col_smem_bytes() {
-  return sizeof(float2) * (N + ColW<N>::W * (N + 1));
+  return sizeof(float2) * (N + ColW<N>::W * ColLD<N>::value);
 }
 
 template <int N>
 cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, float2* rowbuf, float2* mhat,
                             cudaStream_t st) {
-  const size_t smr = sizeof(float2) * (3 * N + 1);
+  const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
   cudaError_t e = cudaFuncSetAttribute(k_mask_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
   if (e != cudaSuccess) return e;
   k_mask_rows<N><<<dim3(N / 2, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf);
@@ -209,6 +212,19 @@ cudaError_t stage2_n(const float2* t1, const float* lam, int nk, int crop, float
   }
 
 }  // namespace
+
+bool fft_twiddle_table(int n, float2* out) {
+  switch (n) {
+    case 32: fill_twiddle_table<32>(out); return true;
+    case 64: fill_twiddle_table<64>(out); return true;
+    case 128: fill_twiddle_table<128>(out); return true;
+    case 256: fill_twiddle_table<256>(out); return true;
+    case 512: fill_twiddle_table<512>(out); return true;
+    case 1024: fill_twiddle_table<1024>(out); return true;
+    case 2048: fill_twiddle_table<2048>(out); return true;
+    default: return false;
+  }
+}
 
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
                                  float2* mhat, cudaStream_t st) {

@@ -7,14 +7,24 @@
 // conjugate for the inverse), takes an R-point DFT in registers and writes
 // element q to y[(j div NS) NS R + (j mod NS) + q NS].  This is Stockham's
 // self-sorting formulation: the output comes out in natural order with no bit
-// reversal, and each pass reads and writes with unit stride across threads.
+// reversal, and each pass reads with unit stride across threads.
 //
-// The R-point DFTs are radix-2 decimation-in-frequency networks in registers.
-// Twiddles come from a table w[j] = e^{-2 pi i j/N} rounded from FP64 on the
-// host and staged in shared memory.
+// Shared-memory layout: element i of a transform sits at pad16(i) = i + i/16,
+// one spare slot per 16 complex values.  The first pass writes with stride R
+// across threads; without the spare slots a half-warp of 8-byte stores would
+// land in the same two banks.  With them every pass is conflict-free for
+// R = 16 and at most two-way for R = 8 at NS = 8.
+//
+// Twiddles come from a per-pass table built on the host in FP64 and staged in
+// shared memory: for each pass after the first, entries (r-1) NS + k hold
+// w^(r k N/(NS R)) for r in [1, R), k in [0, NS), so consecutive butterflies
+// read consecutive entries.  The R-point DFTs are radix-2
+// decimation-in-frequency networks in registers.
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <cmath>
 
 namespace litho {
 
@@ -23,6 +33,12 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+
+__host__ __device__ __forceinline__ constexpr int pad16(int i) { return i + (i >> 4); }
+template <int N>
+struct PadLen {
+  static constexpr int value = N + N / 16;
+};
 
 // cos and sin of 2 pi t / 16 (exact mathematical constants rounded to float)
 __device__ __forceinline__ constexpr float cos16(int t) {
@@ -100,14 +116,21 @@ struct PassShape {
   static constexpr int PER = (NB + NT - 1) / NT;    // butterflies per thread
 };
 
+// Offsets of the passes' twiddle blocks: pass 1 at 0, pass 2 after it.
+template <int N>
+struct TwOff {
+  static constexpr int p1 = 0;
+  static constexpr int p2 = (Plan<N>::P == 3) ? (Plan<N>::R[1] - 1) * Plan<N>::R[0] : 0;
+};
+
 // Twiddle + DFT of one butterfly's R values.
-template <int N, int R, int NS, int SIGN>
+template <int N, int R, int NS, int SIGN, int OFF>
 __device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2* __restrict__ tw) {
   if (NS > 1) {
     const int k = j % NS;
 #pragma unroll
     for (int r = 1; r < R; ++r) {
-      float2 w = tw[r * k * (N / (NS * R))];
+      float2 w = tw[OFF + (r - 1) * NS + k];
       if (SIGN > 0) w.y = -w.y;
       v[r] = cmul(v[r], w);
     }
@@ -117,7 +140,7 @@ __device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2*
 
 // One pass whose inputs come from `load(index)` (or shared memory when
 // FROM_SMEM) and whose outputs go to shared memory.  Ends with a barrier.
-template <int N, int NT, int R, int NS, int SIGN, bool FROM_SMEM, class Load>
+template <int N, int NT, int R, int NS, int SIGN, int OFF, bool FROM_SMEM, class Load>
 __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int t, Load& load) {
   using S = PassShape<N, NT, R>;
   float2 v[S::PER][R];
@@ -126,8 +149,8 @@ __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int 
     const int j = t + p * NT;
     if (j < S::NB) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[p][r] = FROM_SMEM ? buf[j + r * S::NB] : load(j + r * S::NB);
-      twiddle_dft<N, R, NS, SIGN>(v[p], j, tw);
+      for (int r = 0; r < R; ++r) v[p][r] = FROM_SMEM ? buf[pad16(j + r * S::NB)] : load(j + r * S::NB);
+      twiddle_dft<N, R, NS, SIGN, OFF>(v[p], j, tw);
     }
   }
   __syncthreads();
@@ -137,7 +160,7 @@ __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int 
     if (j < S::NB) {
       const int base = (j / NS) * NS * R + (j % NS);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[base + r * NS] = v[p][r];
+      for (int r = 0; r < R; ++r) buf[pad16(base + r * NS)] = v[p][r];
     }
   }
   __syncthreads();
@@ -148,7 +171,7 @@ __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int 
 // the Stockham output position of element q is j + q NS).  p and q are
 // compile-time after unrolling, so `use` can index register arrays with them.
 // No barrier at the end.
-template <int N, int NT, int R, int NS, int SIGN, class Use>
+template <int N, int NT, int R, int NS, int SIGN, int OFF, class Use>
 __device__ __forceinline__ void pass_last(const float2* buf, const float2* tw, int t, Use& use) {
   using S = PassShape<N, NT, R>;
   static_assert(NS * R == N, "last pass");
@@ -158,8 +181,8 @@ __device__ __forceinline__ void pass_last(const float2* buf, const float2* tw, i
     if (j < S::NB) {
       float2 v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = buf[j + r * S::NB];
-      twiddle_dft<N, R, NS, SIGN>(v, j, tw);
+      for (int r = 0; r < R; ++r) v[r] = buf[pad16(j + r * S::NB)];
+      twiddle_dft<N, R, NS, SIGN, OFF>(v, j, tw);
 #pragma unroll
       for (int q = 0; q < R; ++q) use(p, q, j + q * S::NB, v[q]);
     }
@@ -178,36 +201,56 @@ __device__ __forceinline__ void fft_load_use(float2* buf, const float2* tw, int 
   using PL = Plan<N>;
   constexpr int NT = PL::NT;
   if constexpr (PL::P == 2) {
-    pass_to_smem<N, NT, PL::R[0], 1, SIGN, false>(buf, tw, t, load);
-    pass_last<N, NT, PL::R[1], PL::R[0], SIGN>(buf, tw, t, use);
+    pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false>(buf, tw, t, load);
+    pass_last<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1>(buf, tw, t, use);
   } else {
-    pass_to_smem<N, NT, PL::R[0], 1, SIGN, false>(buf, tw, t, load);
+    pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false>(buf, tw, t, load);
     SmemLoadUnused none;
-    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, true>(buf, tw, t, none);
-    pass_last<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN>(buf, tw, t, use);
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
+    pass_last<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, TwOff<N>::p2>(buf, tw, t, use);
   }
 }
 
-// Full transform in place in shared memory (buf holds the input on entry and
-// the output on return, natural order).  Ends with a barrier.
+// Full transform in place in shared memory (padded layout on entry and on
+// return, natural order).  Ends with a barrier.
 template <int N, int SIGN>
 __device__ __forceinline__ void fft_smem(float2* buf, const float2* tw, int t) {
   using PL = Plan<N>;
   constexpr int NT = PL::NT;
   SmemLoadUnused none;
-  pass_to_smem<N, NT, PL::R[0], 1, SIGN, true>(buf, tw, t, none);
+  pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, true>(buf, tw, t, none);
   if constexpr (PL::P == 2) {
-    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, true>(buf, tw, t, none);
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
   } else {
-    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, true>(buf, tw, t, none);
-    pass_to_smem<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, true>(buf, tw, t, none);
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
+    pass_to_smem<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, TwOff<N>::p2, true>(buf, tw, t, none);
   }
 }
 
-// Stage the twiddle table into shared memory (all threads of the block).
+// Stage the twiddle table (N entries, see above) into shared memory.
 template <int N>
 __device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* __restrict__ g_tw) {
   for (int i = threadIdx.x; i < N; i += blockDim.x) s_tw[i] = g_tw[i];
+}
+
+// Host: fills the N-entry per-pass twiddle table of the plan for N (FP64
+// angles, rounded to float).  Unused tail entries are zero.
+template <int N>
+void fill_twiddle_table(float2* out) {
+  using PL = Plan<N>;
+  for (int i = 0; i < N; ++i) out[i] = make_float2(0.f, 0.f);
+  int off = 0, ns = PL::R[0];
+  for (int p = 1; p < PL::P; ++p) {
+    const int rp = PL::R[p];
+    for (int r = 1; r < rp; ++r)
+      for (int k = 0; k < ns; ++k) {
+        const long long e = (long long)r * k * (N / (ns * rp));
+        const double a = 2.0 * 3.14159265358979323846 * double(e) / double(N);
+        out[off + (r - 1) * ns + k] = make_float2(float(std::cos(a)), float(-std::sin(a)));
+      }
+    off += (rp - 1) * ns;
+    ns *= rp;
+  }
 }
 
 }  // namespace litho

@@ -95,6 +95,8 @@ struct litho_kernels {
 namespace litho {
 
 // ---- launchers (fft.cu) ---------------------------------------------------------------------
+// The N-entry per-pass twiddle table the FFT kernels expect (false if n unsupported).
+bool fft_twiddle_table(int n, float2* out);
 // Mask spectrum: m[b][n][n] -> mhat[b][C][C] = N^-2 DFT(m) on the crop.  rowbuf: [b][n][C].
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
                                  float2* mhat, cudaStream_t st);

@@ -24,10 +24,16 @@ __global__ void __launch_bounds__(TX * BY) k_resist(const float* __restrict__ im
   const int plane = blockIdx.z, x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const float* src = img + (size_t)plane * n * n;
   const int tid = threadIdx.y * TX + threadIdx.x, nth = TX * BY;
-  for (int i = tid; i < hh * hw; i += nth) {
-    const int ty = i / hw, tx = i % hw;
-    const int gy = (y0 + ty - r + n) % n, gx = (x0 + tx - r + n) % n;
-    tile[i] = __ldg(src + (size_t)gy * n + gx);
+  const bool pow2 = (n & (n - 1)) == 0;
+  for (int ty = threadIdx.y; ty < hh; ty += BY) {
+    int gy = y0 + ty - r;
+    gy = pow2 ? (gy & (n - 1)) : (gy + n) % n;
+    const float* srow = src + (size_t)gy * n;
+    for (int tx = threadIdx.x; tx < hw; tx += TX) {
+      int gx = x0 + tx - r;
+      gx = pow2 ? (gx & (n - 1)) : (gx + n) % n;
+      tile[ty * hw + tx] = __ldg(srow + gx);
+    }
   }
   __syncthreads();
   // rows: rows[ty][x] = sum_a g[a] tile[ty][x + r - a]
