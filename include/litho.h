@@ -78,8 +78,12 @@ typedef enum {
   LITHO_PREC_FFT32 = 0,  /* FP32 FFT path (band multiply + two inverse FFT passes) */
   LITHO_PREC_BF16 = 1,   /* tcgen05 DFT-GEMM, bf16 operands, FP32 accumulation */
   LITHO_PREC_BF16X3 = 2, /* tcgen05 DFT-GEMM, split bf16 hi/lo, three products */
-  LITHO_PREC_FP16X3 = 3  /* tcgen05 DFT-GEMM, split fp16 hi/lo (scaled), three products */
+  LITHO_PREC_FP16X3 = 3, /* tcgen05 DFT-GEMM, split fp16 hi/lo (scaled), three products */
+  LITHO_PREC_FP16 = 4    /* tcgen05 DFT-GEMM, fp16 operands (scaled), FP32 accumulation */
 } litho_precision;
+/* Tensor-core modes need n a multiple of 128 and an sm_103 device (else
+ * EUNSUPPORTED); the fp16 modes scale the stage-1 fields per kernel by a power
+ * of two chosen for masks with |m| <= 1. */
 
 typedef struct litho_kernels litho_kernels; /* device-resident SOCS kernels for one (optics, N, pixel, focus list, K) */
 typedef struct litho_server litho_server;
@@ -136,6 +140,13 @@ litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_pr
  * available for this crop), ECUDA. */
 litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, double dose, litho_precision prec,
                           float* intensity_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Waits for `stream` and reports LITHO_ETIMEOUT if, since the last check, a
+ * tensor-core kernel of this kernel set gave up waiting on one of its
+ * pipeline barriers (each such wait is bounded at about two seconds; the
+ * kernel then drains its own copies, frees its tensor memory and returns,
+ * leaving its output incomplete).  Clears the flag.  LITHO_OK otherwise. */
+litho_status litho_check_device(const litho_kernels* h, void* stream);
 
 /* The same computation from host memory, optionally followed by the resist:
  * copies mask_host[b][n][n] in, images, and copies back whichever of

@@ -1,4 +1,5 @@
 // C ABI entry points: kernel handles, aerial image, resist, error reporting.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -272,7 +273,7 @@ static size_t aerial_layout(const litho_kernels* h, int b, litho_precision prec,
   if (prec == LITHO_PREC_FFT32) {
     t = c.take<float2>(F * K * N * C);
   } else {
-    g = c.take<char>(gemm_workspace_bytes(h, prec));
+    g = c.take<char>(gemm_workspace_bytes(h, prec, b));
   }
   if (rowbuf) *rowbuf = r;
   if (mhat) *mhat = m;
@@ -284,7 +285,7 @@ static size_t aerial_layout(const litho_kernels* h, int b, litho_precision prec,
 litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes) {
   LITHO_REQUIRE(h && bytes, "null argument");
   LITHO_REQUIRE(b >= 1, "b must be >= 1");
-  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16X3, "unknown precision");
+  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16, "unknown precision");
   *bytes = aerial_layout(h, b, prec, nullptr, nullptr, nullptr, nullptr, nullptr);
   return LITHO_OK;
 }
@@ -294,7 +295,7 @@ litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, 
   LITHO_REQUIRE(h && mask_dev && intensity_dev && workspace_dev, "null argument");
   LITHO_REQUIRE(b >= 1, "b must be >= 1");
   LITHO_REQUIRE(std::isfinite(dose), "dose must be finite");
-  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16X3, "unknown precision");
+  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16, "unknown precision");
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(workspace_dev) & 255) == 0, "workspace must be 256-byte aligned");
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(mask_dev) & 15) == 0 && (reinterpret_cast<uintptr_t>(intensity_dev) & 15) == 0,
                 "mask and intensity must be 16-byte aligned");
@@ -316,10 +317,19 @@ litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, 
     ProfScope ps(kStageMaskSpectrum, st, 2);
     LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev, b, N, C, h->d_tw, rowbuf, mhat, st));
   }
+  if (prec != LITHO_PREC_FFT32) {
+    const int G = gemm_group_clips();
+    for (int c0 = 0; c0 < b; c0 += G) {
+      litho_status s = gemm_aerial_group(h, mhat + size_t(c0) * C * C, std::min(G, b - c0), float(dose), prec,
+                                         intensity_dev + size_t(c0) * F * N * N, gws, st);
+      if (s != LITHO_OK) return s;
+    }
+    return LITHO_OK;
+  }
   for (int clip = 0; clip < b; ++clip) {
     const float2* mh = mhat + size_t(clip) * C * C;
     float* img = intensity_dev + size_t(clip) * F * N * N;
-    if (prec == LITHO_PREC_FFT32) {
+    {
       {
         ProfScope ps(kStageStage1Fft, st, 1);
         LITHO_TRY_CUDA(launch_stage1_fft(mh, h->d_phi, F * K, N, C, h->d_tw, t1, st));
@@ -329,9 +339,6 @@ litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, 
         LITHO_TRY_CUDA(launch_stage2_fft(t1, h->d_lambda, K, N, C, float(dose), h->d_tw, img, F,
                                          (long long)K * N * C, (long long)N * N, st));
       }
-    } else {
-      litho_status s = gemm_aerial_clip(h, mh, float(dose), prec, img, gws, st);
-      if (s != LITHO_OK) return s;
     }
   }
   return LITHO_OK;
@@ -381,6 +388,11 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
     LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host, dimg, planes * nn * sizeof(float), cudaMemcpyDeviceToHost, st));
   LITHO_TRY_CUDA(cudaStreamSynchronize(st));
   return LITHO_OK;
+}
+
+litho_status litho_check_device(const litho_kernels* h, void* stream) {
+  LITHO_REQUIRE(h, "null handle");
+  return gemm_check_device(h, static_cast<cudaStream_t>(stream));
 }
 
 // ---- resist ------------------------------------------------------------------------------------------

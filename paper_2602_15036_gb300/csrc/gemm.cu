@@ -1,18 +1,688 @@
-// Placeholder until the tcgen05 DFT-GEMM kernels land.
+// Tensor-core (tcgen05) DFT-GEMM path for the SOCS image, paper Eq. (4).
+//
+// For one focus plane, E_k(y, x) = sum_c T_k(y, c) W(c, x) with the stage-1
+// field T_k (rows y, crop columns c) and the inverse-DFT matrix
+// W(c, x) = exp(+2 pi i u_c x / N), u_c = c - C/2.  Written over real
+// operands with Ar = Re T, Ai = Im T, Wr = cos, Wi = sin:
+//   D1 = Ar Wr^T,  D2 = Ai Wi^T,  D3 = Ar Wi^T + Ai Wr^T,
+//   Re E = D1 - D2,  Im E = D3,  I(y, x) += lam_k ((D1 - D2)^2 + D3^2).
+// The three products accumulate in TMEM (3 x 128 fp32 columns) and need no
+// negated operand.  The k loop runs inside the CTA: the epilogue warps fold
+// each kernel's |E|^2 into registers, so I is written once per tile.
+//
+// Operand layout in global memory (16-bit elements, K-major): the contraction
+// index c is cut into chunks of 32 complex values stored as one 64-element
+// (128-byte) row segment [Re 32 | Im 32].  A: [plane * K + k][y][2C],
+// B: [x][2C] (same chunking, cos | sin).  TMA loads 128-row x 64-element boxes
+// with 128-byte swizzling, which is the canonical K-major SWIZZLE_128B layout
+// that tcgen05.mma reads through shared-memory descriptors; the four 16-element
+// K steps of a chunk are Re(0:16), Re(16:32), Im(0:16), Im(16:32) at byte
+// offsets 0, 32, 64, 96.
+//
+// Precision modes: BF16 / FP16 (one product), BF16X3 and FP16X3
+// (operands split into hi + lo, three products hi.hi + hi.lo + lo.hi; FP16
+// stage-1 fields are scaled per kernel by a power of two so that hi and lo
+// stay in the normal range; plain FP16 is scaled the same way).  FP32
+// accumulation throughout.
+//
+// Kernel structure: persistent, one CTA per SM (192 KB shared memory, all 512
+// TMEM columns), warp 0 = TMA producer, warp 1 = MMA issuer (one thread),
+// warps 2..9 = epilogue.  Every mbarrier wait is bounded: past ~2 s it records
+// an error code in a device flag, the CTA drains its own copies and MMAs with
+// bounded waits, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "fft_common.cuh"
 #include "gemm.h"
 
 namespace litho {
 
-size_t gemm_workspace_bytes(const litho_kernels*, litho_precision) { return 0; }
-litho_status gemm_supported(const litho_kernels*, litho_precision) {
-  set_error("tensor-core path not built yet");
-  return LITHO_EUNSUPPORTED;
+namespace {
+
+constexpr int BM = 128;               // rows (y) per tile = UMMA M
+constexpr int XT = 128;               // x per tile = UMMA N
+constexpr int CH = 32;                // complex values per chunk
+constexpr int KE = 2 * CH;            // 16-bit elements per chunk row (128 bytes)
+constexpr int STAGES = 3;
+constexpr int TILE_BYTES = BM * KE * 2;  // 16 KB (A and B boxes are both 128 x 64)
+constexpr int STAGE_BYTES = 4 * TILE_BYTES;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int GROUP_CLIPS = 4;        // clips per GEMM launch
+constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
+
+enum Mode { kBF16 = 0, kBF16X3 = 1, kFP16X3 = 2, kFP16 = 3, kModes = 4 };
+
+int mode_of(litho_precision p) {
+  return p == LITHO_PREC_BF16 ? kBF16 : p == LITHO_PREC_BF16X3 ? kBF16X3 : p == LITHO_PREC_FP16 ? kFP16 : kFP16X3;
 }
-litho_status gemm_aerial_clip(const litho_kernels*, const float2*, float, litho_precision, float*, void*,
-                              cudaStream_t) {
-  set_error("tensor-core path not built yet");
-  return LITHO_EUNSUPPORTED;
+__host__ __device__ constexpr bool is_split(int m) { return m == kBF16X3 || m == kFP16X3; }
+__host__ __device__ constexpr bool is_fp16(int m) { return m == kFP16X3 || m == kFP16; }
+
+// ---- PTX helpers ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-void gemm_free_operands(litho_kernels*) {}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// K-major, 128-byte-swizzled shared-memory matrix descriptor (tcgen05): start
+// address >> 4, leading-dimension offset (unused for this layout) 16 B, stride
+// between 8-row groups 1024 B, descriptor version 1, swizzle mode 2 (128 B).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(16 >> 4) << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, A/B format (0 fp16,
+// 1 bf16), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int fmt, int m, int n) {
+  return (1u << 4) | (uint32_t(fmt) << 7) | (uint32_t(fmt) << 10) | (uint32_t(n >> 3) << 17) |
+         (uint32_t(m >> 4) << 24);
+}
+
+struct GemmParams {
+  int n, nk, n_focus, planes, tiles_y, tiles_x, chunks, split, fmt;
+  const float* lamp;  // [F][K] lambda / scale^2
+  float dose;
+  float* img;         // [planes][n][n]
+  int* err;
+};
+
+// Bounded wait: true when the phase completed; false after the limit or
+// when another role already gave up (abort flag in shared memory).
+__device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                         int code) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_dft_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo, GemmParams p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  // bars: full[STAGES], empty[STAGES], acc_full, acc_empty, drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
+  const uint32_t acc_full = smem_u32(bars + 2 * STAGES), acc_empty = smem_u32(bars + 2 * STAGES + 1);
+  const uint32_t drain = smem_u32(bars + 2 * STAGES + 2);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, EPI_WARPS);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int tiles_per_plane = p.tiles_y * p.tiles_x;
+  const int total = p.planes * tiles_per_plane;
+  const uint32_t tx_bytes = p.split ? STAGE_BYTES : 2 * TILE_BYTES;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int plane = t / tiles_per_plane, rem = t % tiles_per_plane;
+        const int yt = rem / p.tiles_x, xt = rem % p.tiles_x;
+        const float* lam = p.lamp + (plane % p.n_focus) * p.nk;
+        for (int k = 0; k < p.nk && ok; ++k) {
+          if (lam[k] == 0.f) continue;
+          const int arow = (plane * p.nk + k) * p.n + yt * BM;
+          for (int ch = 0; ch < p.chunks; ++ch, ++it) {
+            const int s = it % STAGES;
+            const uint32_t use = it / STAGES;
+            if (!wait_bar(empty0 + 8 * s, (use & 1) ^ 1, abort_flag, p.err, 1)) {
+              ok = false;
+              break;
+            }
+            const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+            mbar_expect_tx(full0 + 8 * s, tx_bytes);
+            tma_load_2d(base, &ta_hi, full0 + 8 * s, ch * KE, arow);
+            tma_load_2d(base + 2 * TILE_BYTES, &tb_hi, full0 + 8 * s, ch * KE, xt * XT);
+            if (p.split) {
+              tma_load_2d(base + TILE_BYTES, &ta_lo, full0 + 8 * s, ch * KE, arow);
+              tma_load_2d(base + 3 * TILE_BYTES, &tb_lo, full0 + 8 * s, ch * KE, xt * XT);
+            }
+          }
+        }
+      }
+      // drain: the last use of every stage must have landed before the CTA exits
+      for (int d = 0; d < STAGES && it > 0; ++d) {
+        const uint32_t j = it - 1 - d;
+        if ((int)j < 0 || j >= it) break;
+        const int s = j % STAGES;
+        const long long t0 = clock64();
+        while (!mbar_try_wait(full0 + 8 * s, (j / STAGES) & 1) && clock64() - t0 < kWaitCycles) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = idesc_f16(p.fmt, BM, XT);
+      const uint32_t d1 = tmem, d2 = tmem + 128, d3 = tmem + 256;
+      uint32_t it = 0, acc_it = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+        const int plane = t / tiles_per_plane;
+        const float* lam = p.lamp + (plane % p.n_focus) * p.nk;
+        for (int k = 0; k < p.nk && ok; ++k) {
+          if (lam[k] == 0.f) continue;
+          if (!wait_bar(acc_empty, (acc_it & 1) ^ 1, abort_flag, p.err, 2)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          for (int ch = 0; ch < p.chunks; ++ch, ++it) {
+            const int s = it % STAGES;
+            if (!wait_bar(full0 + 8 * s, (it / STAGES) & 1, abort_flag, p.err, 3)) {
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+            const uint64_t ahi = sdesc_sw128(base), alo = sdesc_sw128(base + TILE_BYTES);
+            const uint64_t bhi = sdesc_sw128(base + 2 * TILE_BYTES), blo = sdesc_sw128(base + 3 * TILE_BYTES);
+#pragma unroll
+            for (int ks = 0; ks < 2; ++ks) {
+              const uint64_t re = uint64_t(2 * ks), im = uint64_t(4 + 2 * ks);  // byte offsets >> 4
+              const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
+              // D1 += Ar Wr ; D2 += Ai Wi ; D3 += Ar Wi + Ai Wr   (each x3 when split)
+              umma_f16(d1, ahi + re, bhi + re, idesc, first);
+              umma_f16(d2, ahi + im, bhi + im, idesc, first);
+              umma_f16(d3, ahi + re, bhi + im, idesc, first);
+              umma_f16(d3, ahi + im, bhi + re, idesc, 1u);
+              if (p.split) {
+                umma_f16(d1, ahi + re, blo + re, idesc, 1u);
+                umma_f16(d1, alo + re, bhi + re, idesc, 1u);
+                umma_f16(d2, ahi + im, blo + im, idesc, 1u);
+                umma_f16(d2, alo + im, bhi + im, idesc, 1u);
+                umma_f16(d3, ahi + re, blo + im, idesc, 1u);
+                umma_f16(d3, alo + re, bhi + im, idesc, 1u);
+                umma_f16(d3, ahi + im, blo + re, idesc, 1u);
+                umma_f16(d3, alo + im, bhi + re, idesc, 1u);
+              }
+            }
+            umma_commit(empty0 + 8 * s);  // frees the stage once these MMAs complete
+          }
+          if (!ok) break;
+          umma_commit(acc_full);  // accumulator of kernel k complete
+          ++acc_it;
+        }
+      }
+      // drain outstanding MMAs before the CTA can release TMEM
+      umma_commit(drain);
+      const long long t0 = clock64();
+      while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitCycles) {
+      }
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int e = warp - 2, q = warp % 4, half = e / 4;
+    const uint32_t lane_base = tmem + (uint32_t(q * 32) << 16);
+    uint32_t acc_it = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+      const int plane = t / tiles_per_plane, rem = t % tiles_per_plane;
+      const int yt = rem / p.tiles_x, xt = rem % p.tiles_x;
+      const float* lam = p.lamp + (plane % p.n_focus) * p.nk;
+      float acc[64];
+#pragma unroll
+      for (int i = 0; i < 64; ++i) acc[i] = 0.f;
+      for (int k = 0; k < p.nk; ++k) {
+        const float l = lam[k];
+        if (l == 0.f) continue;
+        if (!wait_bar(acc_full, acc_it & 1, abort_flag, p.err, 4)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const uint32_t col = half * 64 + cc * 16;
+          float a[16], b[16], c[16];
+          tmem_ld16(lane_base + col, a);
+          tmem_ld16(lane_base + 128 + col, b);
+          tmem_ld16(lane_base + 256 + col, c);
+          tmem_wait_ld();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            const float re = a[i] - b[i];
+            acc[cc * 16 + i] = fmaf(l, fmaf(re, re, c[i] * c[i]), acc[cc * 16 + i]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+        ++acc_it;
+      }
+      if (!ok) break;
+      const int row = yt * BM + q * 32 + lane;
+      float4* out = reinterpret_cast<float4*>(p.img + ((size_t)plane * p.n + row) * p.n + xt * XT + half * 64);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        out[i] = make_float4(p.dose * acc[4 * i], p.dose * acc[4 * i + 1], p.dose * acc[4 * i + 2],
+                             p.dose * acc[4 * i + 3]);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---- stage 1 for the GEMM path: band multiply + inverse transform over v, written as split 16-bit A ---
+template <int MODE>
+__device__ __forceinline__ void split_store(float x, float scale, void* hi, void* lo, size_t idx) {
+  if (MODE == kFP16X3 || MODE == kFP16) {
+    const float xs = x * scale;
+    const __half h = __float2half_rn(xs);
+    static_cast<__half*>(hi)[idx] = h;
+    if (MODE == kFP16X3) static_cast<__half*>(lo)[idx] = __float2half_rn(xs - __half2float(h));
+  } else {
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    static_cast<__nv_bfloat16*>(hi)[idx] = h;
+    if (MODE == kBF16X3) static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
+template <int N> struct S1W { static constexpr int W = (N >= 2048) ? 8 : (N >= 512 ? 16 : 32); };
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(Plan<N>::NT * S1W<N>::W) k_stage1_split(const float2* __restrict__ mhat,
+                                                                           const float2* __restrict__ phi, int crop,
+                                                                           const float2* __restrict__ tw_g,
+                                                                           const float* __restrict__ scales,
+                                                                           void* a_hi, void* a_lo) {
+  constexpr int W = S1W<N>::W, NT = Plan<N>::NT, LD = PadLen<N>::value + 1;
+  extern __shared__ float2 smem1[];
+  float2* tw = smem1;
+  float2* buf = smem1 + N;
+  load_twiddles<N>(tw, tw_g);
+  const int j = blockIdx.y, u0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
+  for (int i = tid; i < W * LD; i += blockDim.x) buf[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  const float2* ph = phi + (size_t)j * crop * crop + u0;
+  const float2* mh = mhat + u0;
+  for (int i = tid; i < crop * W; i += blockDim.x) {
+    const int cv = i / W, w = i % W;
+    const int idx = (cv - half + N) % N;
+    buf[w * LD + pad16(idx)] = cmul(__ldg(mh + (size_t)cv * crop + w), __ldg(ph + (size_t)cv * crop + w));
+  }
+  __syncthreads();
+  fft_smem<N, +1>(buf + (tid / NT) * LD, tw, tid % NT);
+  const float scale = scales[j];
+  const size_t row0 = (size_t)j * N;
+  for (int i = tid; i < N * W; i += blockDim.x) {
+    const int y = i / W, w = i % W, c = u0 + w;
+    const float2 v = buf[w * LD + pad16(y)];
+    const size_t kr = (size_t)(c / CH) * KE + (c % CH);
+    const size_t o = (row0 + y) * (size_t)(2 * crop) + kr;
+    split_store<MODE>(v.x, scale, a_hi, a_lo, o);
+    split_store<MODE>(v.y, scale, a_hi, a_lo, o + CH);
+  }
+}
+
+template <int N, int MODE>
+cudaError_t stage1_split_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
+                           const float* scales, void* a_hi, void* a_lo, cudaStream_t st) {
+  constexpr int W = S1W<N>::W;
+  const size_t sm = sizeof(float2) * (N + W * (PadLen<N>::value + 1));
+  cudaError_t e = cudaFuncSetAttribute(k_stage1_split<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_stage1_split<N, MODE><<<dim3(crop / W, nk), Plan<N>::NT * W, sm, st>>>(mhat, phi, crop, tw, scales, a_hi, a_lo);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t stage1_split_mode(int n, const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
+                              const float* scales, void* a_hi, void* a_lo, cudaStream_t st) {
+  switch (n) {
+    case 128: return stage1_split_n<128, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
+    case 256: return stage1_split_n<256, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
+    case 512: return stage1_split_n<512, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
+    case 1024: return stage1_split_n<1024, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
+    case 2048: return stage1_split_n<2048, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---- host side ---------------------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// 2-D tensor map over rows x (2C) 16-bit elements, 128 x 64 boxes, 128-byte swizzle.
+bool make_map(CUtensorMap* m, void* base, int fmt, unsigned long long rows, unsigned long long cols) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {KE, BM};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, fmt == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base, dims, strides,
+            box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+struct GemmOperands {
+  std::mutex mu;
+  bool built[kModes] = {};
+  void* b_hi[kModes] = {};
+  void* b_lo[kModes] = {};
+  CUtensorMap map_hi[kModes], map_lo[kModes];
+  float* d_lamp[kModes] = {};   // lambda / scale^2 per (f, k)
+  float* d_scale[kModes] = {};  // stage-1 scale per (f, k)
+  int* d_err = nullptr;
+  int sm_count = 0;
+};
+
+namespace {
+
+size_t per_clip_bytes(const litho_kernels* h, int mode) {
+  const size_t rows = size_t(h->n_focus) * h->k * h->n, cols = size_t(2) * h->crop;
+  return rows * cols * 2 * (is_split(mode) ? 2 : 1);
+}
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Builds the twiddle operand B (cos | sin chunks, split) and the per-kernel
+// scales for one precision mode.  Host FP64, then rounded.
+litho_status build_operands(const litho_kernels* hc, int mode) {
+  litho_kernels* h = const_cast<litho_kernels*>(hc);
+  if (!h->gemm) h->gemm = new GemmOperands();
+  GemmOperands* g = h->gemm;
+  std::lock_guard<std::mutex> lk(g->mu);
+  if (g->built[mode]) return LITHO_OK;
+  const int N = h->n, C = h->crop, F = h->n_focus, K = h->k;
+  const size_t cols = size_t(2) * C, count = size_t(N) * cols;
+  std::vector<uint16_t> hi(count), lo(count);
+  for (int x = 0; x < N; ++x) {
+    for (size_t kk = 0; kk < cols; ++kk) {
+      const int chunk = int(kk / KE), within = int(kk % KE), part = within / CH;
+      const int c = chunk * CH + within % CH;
+      const long long e = ((long long)(c - C / 2) * x % N + N) % N;
+      const double a = 2.0 * M_PI * double(e) / double(N);
+      const double w = part ? std::sin(a) : std::cos(a);
+      if (is_fp16(mode)) {
+        const __half hh = __float2half_rn(float(w));
+        const __half ll = __float2half_rn(float(w - double(__half2float(hh))));
+        hi[size_t(x) * cols + kk] = __half_as_ushort(hh);
+        lo[size_t(x) * cols + kk] = __half_as_ushort(ll);
+      } else {
+        const __nv_bfloat16 hh = __float2bfloat16_rn(float(w));
+        const __nv_bfloat16 ll = __float2bfloat16_rn(float(w - double(__bfloat162float(hh))));
+        hi[size_t(x) * cols + kk] = __bfloat16_as_ushort(hh);
+        lo[size_t(x) * cols + kk] = __bfloat16_as_ushort(ll);
+      }
+    }
+  }
+  // per-kernel scales: |T_k| <= max_u sum_v |Phi_k(v, u)| for masks with |m| <= 1
+  std::vector<float> scale(size_t(F) * K, 1.f), lamp(size_t(F) * K, 0.f);
+  for (int f = 0; f < F; ++f)
+    for (int k = 0; k < K; ++k) {
+      const size_t fk = size_t(f) * K + k;
+      double s = 1.0;
+      if (is_fp16(mode)) {
+        double bound = 0.0;
+        const double* ph = &h->phi_host[fk * size_t(C) * C * 2];
+        for (int u = 0; u < C; ++u) {
+          double col = 0.0;
+          for (int v = 0; v < C; ++v) col += std::hypot(ph[(size_t(v) * C + u) * 2], ph[(size_t(v) * C + u) * 2 + 1]);
+          bound = std::max(bound, col);
+        }
+        if (bound > 0.0) s = std::ldexp(1.0, int(std::floor(std::log2(8192.0 / bound))));
+      }
+      scale[fk] = float(s);
+      lamp[fk] = float(h->lambda[fk] / (s * s));
+    }
+  LITHO_TRY_CUDA(cudaMalloc(&g->b_hi[mode], count * 2));
+  LITHO_TRY_CUDA(cudaMemcpy(g->b_hi[mode], hi.data(), count * 2, cudaMemcpyHostToDevice));
+  if (is_split(mode)) {
+    LITHO_TRY_CUDA(cudaMalloc(&g->b_lo[mode], count * 2));
+    LITHO_TRY_CUDA(cudaMemcpy(g->b_lo[mode], lo.data(), count * 2, cudaMemcpyHostToDevice));
+  }
+  LITHO_TRY_CUDA(cudaMalloc(&g->d_scale[mode], scale.size() * sizeof(float)));
+  LITHO_TRY_CUDA(cudaMemcpy(g->d_scale[mode], scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
+  LITHO_TRY_CUDA(cudaMalloc(&g->d_lamp[mode], lamp.size() * sizeof(float)));
+  LITHO_TRY_CUDA(cudaMemcpy(g->d_lamp[mode], lamp.data(), lamp.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (!g->d_err) {
+    LITHO_TRY_CUDA(cudaMalloc(&g->d_err, sizeof(int)));
+    LITHO_TRY_CUDA(cudaMemset(g->d_err, 0, sizeof(int)));
+  }
+  const int fmt = is_fp16(mode) ? 0 : 1;
+  if (!make_map(&g->map_hi[mode], g->b_hi[mode], fmt, N, cols) ||
+      !make_map(&g->map_lo[mode], is_split(mode) ? g->b_lo[mode] : g->b_hi[mode], fmt, N, cols)) {
+    set_error("cuTensorMapEncodeTiled failed for the twiddle operand");
+    return LITHO_ECUDA;
+  }
+  int dev = 0;
+  LITHO_TRY_CUDA(cudaGetDevice(&dev));
+  LITHO_TRY_CUDA(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev));
+  g->built[mode] = true;
+  return LITHO_OK;
+}
+
+}  // namespace
+
+size_t gemm_workspace_bytes(const litho_kernels* h, litho_precision prec, int b) {
+  const int mode = mode_of(prec);
+  const int g = std::min(b, GROUP_CLIPS);
+  const size_t half = up256(size_t(g) * per_clip_bytes(h, mode) / (is_split(mode) ? 2 : 1));
+  return is_split(mode) ? 2 * half : half;
+}
+
+litho_status gemm_supported(const litho_kernels* h, litho_precision prec) {
+  if (h->n < 128 || h->n % 128 != 0 || h->crop % CH != 0) {
+    set_error("tensor-core path needs n a multiple of 128 (got n = %d, crop = %d)", h->n, h->crop);
+    return LITHO_EUNSUPPORTED;
+  }
+  int dev = 0, major = 0, minor = 0;
+  LITHO_TRY_CUDA(cudaGetDevice(&dev));
+  LITHO_TRY_CUDA(cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev));
+  LITHO_TRY_CUDA(cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev));
+  if (major != 10 || minor != 3) {
+    set_error("tensor-core path is built for sm_103a (this device is sm_%d%d)", major, minor);
+    return LITHO_EUNSUPPORTED;
+  }
+  if (!encode_fn()) {
+    set_error("cuTensorMapEncodeTiled is not available from the driver");
+    return LITHO_EUNSUPPORTED;
+  }
+  return build_operands(h, mode_of(prec));
+}
+
+litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int clips, float dose,
+                               litho_precision prec, float* img, void* ws, cudaStream_t st) {
+  const int mode = mode_of(prec);
+  GemmOperands* g = h->gemm;
+  const int N = h->n, C = h->crop, F = h->n_focus, K = h->k;
+  const size_t half = up256(size_t(std::min(clips, GROUP_CLIPS)) * per_clip_bytes(h, mode) / (is_split(mode) ? 2 : 1));
+  char* a_hi = static_cast<char*>(ws);
+  char* a_lo = is_split(mode) ? a_hi + half : a_hi;
+  const size_t clip_half = per_clip_bytes(h, mode) / (is_split(mode) ? 2 : 1);
+  {
+    ProfScope ps(kStageGemmOperands, st, clips);
+    for (int c = 0; c < clips; ++c) {
+      const float2* mh = mhat + size_t(c) * C * C;
+      cudaError_t e;
+      if (mode == kBF16)
+        e = stage1_split_mode<kBF16>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+                                     nullptr, st);
+      else if (mode == kFP16)
+        e = stage1_split_mode<kFP16>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+                                     nullptr, st);
+      else if (mode == kBF16X3)
+        e = stage1_split_mode<kBF16X3>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+                                       a_lo + c * clip_half, st);
+      else
+        e = stage1_split_mode<kFP16X3>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+                                       a_lo + c * clip_half, st);
+      LITHO_TRY_CUDA(e);
+    }
+  }
+  const int fmt = is_fp16(mode) ? 0 : 1;
+  const unsigned long long rows = (unsigned long long)clips * F * K * N;
+  CUtensorMap ta_hi, ta_lo;
+  if (!make_map(&ta_hi, a_hi, fmt, rows, 2ull * C) || !make_map(&ta_lo, a_lo, fmt, rows, 2ull * C)) {
+    set_error("cuTensorMapEncodeTiled failed for the stage-1 operand");
+    return LITHO_ECUDA;
+  }
+  GemmParams p;
+  p.n = N;
+  p.nk = K;
+  p.n_focus = F;
+  p.planes = clips * F;
+  p.tiles_y = N / BM;
+  p.tiles_x = N / XT;
+  p.chunks = C / CH;
+  p.split = is_split(mode) ? 1 : 0;
+  p.fmt = fmt;
+  p.lamp = g->d_lamp[mode];
+  p.dose = dose;
+  p.img = img;
+  p.err = g->d_err;
+  const int total = p.planes * p.tiles_y * p.tiles_x;
+  const int grid = std::min(total, g->sm_count);
+  LITHO_TRY_CUDA(cudaFuncSetAttribute(k_dft_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+  ProfScope ps(kStageStage2Gemm, st, 1);
+  k_dft_gemm<<<grid, THREADS, SMEM_BYTES, st>>>(ta_hi, ta_lo, g->map_hi[mode], g->map_lo[mode], p);
+  LITHO_TRY_CUDA(cudaGetLastError());
+  return LITHO_OK;
+}
+
+int gemm_group_clips() { return GROUP_CLIPS; }
+
+litho_status gemm_check_device(const litho_kernels* h, cudaStream_t st) {
+  if (!h->gemm || !h->gemm->d_err) return LITHO_OK;
+  int flag = 0;
+  LITHO_TRY_CUDA(cudaMemcpyAsync(&flag, h->gemm->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LITHO_TRY_CUDA(cudaStreamSynchronize(st));
+  if (flag) {
+    LITHO_TRY_CUDA(cudaMemsetAsync(h->gemm->d_err, 0, sizeof(int), st));
+    set_error("a tensor-core kernel gave up waiting on a pipeline barrier (code %d)", flag);
+    return LITHO_ETIMEOUT;
+  }
+  return LITHO_OK;
+}
+
+void gemm_free_operands(litho_kernels* h) {
+  if (!h->gemm) return;
+  for (int m = 0; m < kModes; ++m) {
+    cudaFree(h->gemm->b_hi[m]);
+    cudaFree(h->gemm->b_lo[m]);
+    cudaFree(h->gemm->d_lamp[m]);
+    cudaFree(h->gemm->d_scale[m]);
+  }
+  cudaFree(h->gemm->d_err);
+  delete h->gemm;
+  h->gemm = nullptr;
+}
 
 }  // namespace litho

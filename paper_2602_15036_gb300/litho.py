@@ -21,7 +21,7 @@ OK, EINVAL, ENOMEM, ECUDA, EBUSY, ETIMEOUT, ECANCELED, EUNSUPPORTED = range(8)
 STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EBUSY", "ETIMEOUT", "ECANCELED", "EUNSUPPORTED"]
 
 SRC_ANNULAR, SRC_QUADRUPOLE, SRC_CUSTOM = 0, 1, 2
-PREC = {"fft32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3}
+PREC = {"fft32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3, "fp16": 4}
 REQ_IMAGE, REQ_ILT_STEP = 0, 1
 
 
@@ -69,6 +69,7 @@ _SIGS = {
     "litho_aerial_host_workspace_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
     "litho_aerial_host": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_double, c_double,
                                   c_void_p, c_void_p, c_size_t, c_void_p]),
+    "litho_check_device": (c_int, [c_void_p, c_void_p]),
     "litho_aerial_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]),
     "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
@@ -246,6 +247,11 @@ def litho_aerial_host(kern: Kernels, mask_host, workspace, intensity_host=None, 
                                    sigma_nm, threshold, ptr(printed_host), c_void_p(workspace.data_ptr()),
                                    workspace.numel(), _stream_ptr(stream)))
     return intensity_host, printed_host
+
+
+def litho_check_device(kern: Kernels, stream=None):
+    """Raises LithoError(ETIMEOUT) if a tensor-core kernel gave up on a barrier wait."""
+    _check(lib().litho_check_device(kern.handle, _stream_ptr(stream)))
 
 
 def litho_aerial_noalloc(kern: Kernels, mask, out, dose=1.0, stream=None):

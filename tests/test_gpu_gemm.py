@@ -1,0 +1,91 @@
+"""GPU parity of the tcgen05 DFT-GEMM path against the FP64 oracle.
+
+Tolerances (absolute intensity, clear field = 1): 2e-3 for plain 16-bit
+operands (met by fp16, whose 11-bit significand gives errors of a few 1e-4)
+and 1e-5 for the split fp16 hi/lo path.  bf16 keeps 8 significand bits per
+operand: plain bf16 lands near 2.3e-3 and split bf16 near 2^-16 relative, so
+their bounds (4e-3 and 5e-5) are stated separately and are not the targets.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import imaging as OI
+from oracle import resist as OR
+from tests.gpu_util import DUV_ANNULAR, DUV_QUAD41, oracle_kernel_set
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp16": 2e-3, "fp16x3": 1e-5, "bf16": 4e-3, "bf16x3": 5e-5}
+
+
+def _run(litho_lib, cuda, lam, phi, n, pixel, masks, precision, dose=1.0):
+    import torch
+    kern = litho_lib.litho_upload_kernels(n, pixel, lam, phi)
+    m = torch.from_numpy(np.ascontiguousarray(masks, dtype=np.float32)).to(cuda)
+    out = litho_lib.litho_aerial(kern, m, dose=dose, precision=precision)
+    litho_lib.litho_check_device(kern)
+    return out.cpu().numpy().astype(np.float64), kern
+
+
+CASES = [
+    (DUV_ANNULAR, 256, 8.0, [0.0], 8, 1, 1.0),              # one clip of the 256^2 workload
+    (DUV_QUAD41, 128, 8.0, [-50.0, 0.0, 50.0], 24, 5, 0.9),  # two launch groups (4 + 1 clips)
+    (DUV_QUAD41, 512, 8.0, [50.0], 12, 2, 1.0),
+]
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp16x3", "bf16", "bf16x3"])
+@pytest.mark.parametrize("preset,n,pixel,focus,k,b,dose", CASES)
+def test_gemm_matches_oracle(litho_lib, cuda, precision, preset, n, pixel, focus, k, b, dose):
+    lam, phi = oracle_kernel_set(preset, n, pixel, focus, k)
+    masks = np.stack([synth.random_rect_mask(n, seed=300 + i, count=max(8, n // 6)) for i in range(b)])
+    got, _ = _run(litho_lib, cuda, lam, phi, n, pixel, masks, precision, dose)
+    worst = 0.0
+    for i in range(b):
+        for f in range(len(focus)):
+            ref = OI.socs_image(masks[i].astype(np.float64), lam[f], phi[f], dose)
+            worst = max(worst, np.abs(got[i, f] - ref).max())
+    print(f"{precision} n={n} k={k} max|err|={worst:.3e}")
+    assert worst <= TOL[precision], worst
+
+
+def test_gemm_fp16x3_full_size_rows(litho_lib, cuda):
+    """2048^2, K=24, three focus planes, two clips, sampled full rows."""
+    n, pixel, k, focus = 2048, 8.0, 24, [-50.0, 0.0, 50.0]
+    lam, phi = oracle_kernel_set(DUV_QUAD41, n, pixel, focus, k)
+    masks = np.stack([synth.manhattan_mask(n, seed=1234 + i) for i in range(2)])
+    got, _ = _run(litho_lib, cuda, lam, phi, n, pixel, masks, "fp16x3")
+    rows = sorted(set(synth.Stream(7).integers(0, n - 1, 6).tolist()) | {0, 127, 128, n - 1})
+    c = phi.shape[-1]
+    for i in range(2):
+        mb = OI.band(OI.mask_spectrum(masks[i]), c)
+        for f in range(3):
+            ref = OI.socs_rows(mb, lam[f], phi[f], n, rows)
+            err = np.abs(got[i, f, rows] - ref).max()
+            assert err <= TOL["fp16x3"], (i, f, err)
+
+
+def test_gemm_clear_dark_and_resist_contours(litho_lib, cuda):
+    import torch
+    n, pixel, k = 256, 8.0, 8
+    lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, [0.0], k)
+    c = phi.shape[-1]
+    masks = np.stack([np.ones((n, n)), np.zeros((n, n)), synth.random_rect_mask(n, seed=1234)])
+    got, kern = _run(litho_lib, cuda, lam, phi, n, pixel, masks, "fp16x3")
+    clear = sum(lam[0, j] * abs(phi[0, j, c // 2, c // 2]) ** 2 for j in range(k))
+    assert np.abs(got[0, 0] - clear).max() <= 1e-5
+    assert np.abs(got[1, 0]).max() <= 1e-12
+    ib, _ = litho_lib.litho_resist(torch.from_numpy(got[2:3].astype(np.float32)).to(cuda), pixel, 10.0, 0.3)
+    ref = OR.blur(OI.socs_image(masks[2].astype(np.float64), lam[0], phi[0]), 10.0, pixel)
+    assert OR.edge_placement_difference(ref, ib.cpu().numpy()[0, 0].astype(np.float64), 0.3, pixel) <= 0.1
+
+
+def test_gemm_rejects_small_grids(litho_lib, cuda):
+    import torch
+    L = litho_lib
+    lam, phi = oracle_kernel_set(DUV_ANNULAR, 64, 8.0, [0.0], 4)
+    kern = L.litho_upload_kernels(64, 8.0, lam, phi)
+    with pytest.raises(L.LithoError) as e:
+        L.litho_aerial(kern, torch.zeros((1, 64, 64), device=cuda), precision="fp16x3")
+    assert e.value.status == L.EUNSUPPORTED
