@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_stage1(const float
   for (int i = tid; i < crop * W; i += blockDim.x) {
     const int cv = i / W, w = i % W;
     const int idx = (cv - half + N) % N;
-    buf[w * LD + pad16(idx)] = cmul(__ldg(mh + (size_t)cv * crop + w), __ldg(ph + (size_t)cv * crop + w));
+    const float2 a = __ldg(mh + (size_t)cv * crop + w);
+    buf[w * LD + pad16(idx)] = phi ? cmul(a, __ldg(ph + (size_t)cv * crop + w)) : a;
   }
   __syncthreads();
   fft_smem<N, +1>(buf + (tid / NT) * LD, tw, tid % NT);

@@ -1,0 +1,410 @@
+// ILT loss and its adjoint (mask gradient) on the FP32 FFT path.
+//
+// Objective (pixel-based ILT, the paper's Section I prior art; dI/dM is the
+// input channel of its Eq. (9)):
+//   m = sigmoid(a theta),  I_f = D sum_k lam_fk |E_fk|^2 (Eq. (4)),
+//   Ib_f = g (x) I_f (Eq. (5) blur),  Z_f = sigmoid(b (Ib_f - t)),
+//   L = sum_f sum_x (Z_f - target)^2.
+// Adjoint by the chain rule (g symmetric, so the blur is its own adjoint):
+//   q_f = 2 (Z_f - target) b Z_f (1 - Z_f),  G_f = g (x) q_f          (= dL/dI_f)
+//   H_fk(u) = sum_x G_f(x) E_fk(x) e^{-2 pi i u.x/N}    on the crop
+//   S(u) = sum_f sum_k lam_fk conj(Phi_fk(u)) H_fk(u)
+//   dL/dm(x) = 2 D N^-2 Re sum_u S(u) e^{+2 pi i u.x/N},  dL/dtheta = dL/dm a m (1 - m).
+//
+// Kernels (per clip, for a group of P focus planes at a time):
+//   k_sigmoid        m from theta
+//   (mask spectrum, stage 1, stage 2, resist blur: shared with the forward path)
+//   k_resist_grad    Z, q and per-block FP64 partial sums of (Z - target)^2
+//   k_reduce_loss    fixed-order FP64 sum of the partials (deterministic)
+//   k_adj_rows       per image row: E_fk from the stage-1 field (inverse FFT),
+//                    times G_f, forward FFT, crop columns -> U_fk[y][c]
+//   k_adj_cols       per crop column block: forward FFT over y, crop rows,
+//                    times lam conj(Phi) -> SK_fk[v][c]
+//   k_sum_planes     S = sum over (f, k) of SK in fixed order
+//   k_grad_rows      band-to-full inverse of S along x (after stage 1 along y),
+//                    real part, chain factor -> dL/dtheta
+// The fields E are never stored: each backward row recomputes E_fk from the
+// stage-1 field T_fk (C values per row) that the forward pass kept.
+#include <cmath>
+
+#include "fft_common.cuh"
+#include "litho_internal.h"
+
+namespace litho {
+
+namespace {
+
+constexpr int kPartials = 1024;  // blocks of k_resist_grad, fixed for a deterministic reduction
+
+__device__ __forceinline__ int freq_of_idx(int idx, int n) { return idx < n / 2 ? idx : idx - n; }
+
+__global__ void k_sigmoid(const float* __restrict__ theta, float alpha, float* __restrict__ m, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    m[i] = 1.0f / (1.0f + expf(-alpha * theta[i]));
+}
+
+__global__ void __launch_bounds__(256) k_resist_grad(const float* __restrict__ ib, const float* __restrict__ target,
+                                                     size_t nn, int planes, float beta, float thr,
+                                                     float* __restrict__ q, double* __restrict__ partial) {
+  double acc = 0.0;
+  const size_t total = nn * planes;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const float z = 1.0f / (1.0f + expf(-beta * (ib[i] - thr)));
+    const float d = z - target[i % nn];
+    acc += double(d) * double(d);
+    q[i] = 2.0f * d * beta * z * (1.0f - z);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double ws[8];
+  if (threadIdx.x % 32 == 0) ws[threadIdx.x / 32] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < 8; ++w) s += ws[w];
+    partial[blockIdx.x] = s;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_reduce_loss(const double* __restrict__ partial, int count,
+                                                      double* __restrict__ out, int accumulate) {
+  __shared__ double s[1024];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < count; i += 1024) a += partial[i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int w = 512; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = (accumulate ? *out : 0.0) + s[0];
+}
+
+// Backward rows: for every kernel of the plane, E = inverse FFT of the band row
+// T[y][:], P = G[y][:] E, U[y][c] = forward FFT of P on the crop columns.
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restrict__ t1, const float* __restrict__ lam,
+                                                          int nk, int crop, const float* __restrict__ g,
+                                                          const float2* __restrict__ tw_g, float2* __restrict__ u) {
+  using PL = Plan<N>;
+  constexpr int NT = PL::NT, RL = PL::R[PL::P - 1];
+  constexpr int PERL = PassShape<N, NT, RL>::PER;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* bufa = sm + N;
+  float2* bufb = sm + N + PadLen<N>::value;
+  load_twiddles<N>(tw, tw_g);
+  const int y = blockIdx.x, plane = blockIdx.y, t = threadIdx.x, half = crop / 2;
+  float gv[PERL][RL];
+  const float* grow = g + ((size_t)plane * N + y) * N;
+#pragma unroll
+  for (int p = 0; p < PERL; ++p)
+#pragma unroll
+    for (int q = 0; q < RL; ++q) {
+      const int jj = t + p * NT;
+      gv[p][q] = jj < N / RL ? grow[jj + q * (N / RL)] : 0.f;
+    }
+  __syncthreads();
+  for (int k = 0; k < nk; ++k) {
+    if (lam[plane * nk + k] == 0.f) continue;
+    const size_t rowoff = (((size_t)plane * nk + k) * N + y) * crop;
+    const float2* row = t1 + rowoff;
+    auto load_band = [&](int idx) {
+      const int c = freq_of_idx(idx, N) + half;
+      return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
+    };
+    auto times_g = [&](int p, int q, int idx, float2 v) {
+      bufb[pad16(idx)] = make_float2(v.x * gv[p][q], v.y * gv[p][q]);
+    };
+    fft_load_use<N, +1>(bufa, tw, t, load_band, times_g);
+    __syncthreads();
+    auto load_prod = [&](int idx) { return bufb[pad16(idx)]; };
+    float2* urow = u + rowoff;
+    auto store_crop = [&](int, int, int idx, float2 v) {
+      const int c = freq_of_idx(idx, N) + half;
+      if (c >= 0 && c < crop) urow[c] = v;
+    };
+    fft_load_use<N, -1>(bufa, tw, t, load_prod, store_crop);
+  }
+}
+
+template <int N> struct AdjW { static constexpr int W = (N >= 2048) ? 8 : (N >= 512 ? 16 : 32); };
+
+// Backward columns: forward FFT over y of U_j[:, c], crop rows, times lam_j conj(Phi_j).
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const float2* __restrict__ u,
+                                                                        const float2* __restrict__ phi,
+                                                                        const float* __restrict__ lam, int crop,
+                                                                        const float2* __restrict__ tw_g,
+                                                                        float2* __restrict__ sk) {
+  constexpr int W = AdjW<N>::W, NT = Plan<N>::NT, LD = PadLen<N>::value + 1;
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* buf = sm + N;
+  const int j = blockIdx.y, c0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
+  const float l = lam[j];
+  float2* dst = sk + (size_t)j * crop * crop + c0;
+  if (l == 0.f) {  // uniform across the block
+    for (int i = tid; i < crop * W; i += blockDim.x) dst[(size_t)(i / W) * crop + i % W] = make_float2(0.f, 0.f);
+    return;
+  }
+  load_twiddles<N>(tw, tw_g);
+  const float2* src = u + (size_t)j * N * crop + c0;
+  for (int i = tid; i < N * W; i += blockDim.x) {
+    const int y = i / W, w = i % W;
+    buf[w * LD + pad16(y)] = src[(size_t)y * crop + w];
+  }
+  __syncthreads();
+  fft_smem<N, -1>(buf + (tid / NT) * LD, tw, tid % NT);
+  const float2* ph = phi + (size_t)j * crop * crop + c0;
+  for (int i = tid; i < crop * W; i += blockDim.x) {
+    const int cv = i / W, w = i % W;
+    const float2 h = buf[w * LD + pad16((cv - half + N) % N)];
+    const float2 p = __ldg(ph + (size_t)cv * crop + w);
+    // lam conj(p) h
+    dst[(size_t)cv * crop + w] = make_float2(l * (p.x * h.x + p.y * h.y), l * (p.x * h.y - p.y * h.x));
+  }
+}
+
+__global__ void k_sum_planes(const float2* __restrict__ sk, int planes, size_t cc, float2* __restrict__ s,
+                             int accumulate) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cc; i += (size_t)gridDim.x * blockDim.x) {
+    float2 a = accumulate ? s[i] : make_float2(0.f, 0.f);
+    for (int j = 0; j < planes; ++j) {
+      const float2 v = sk[(size_t)j * cc + i];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    s[i] = a;
+  }
+}
+
+// Final rows: grad[y][x] = scale Re(sum_c Q[y][c] e^{2 pi i u_c x/N}) a m (1 - m).
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT) k_grad_rows(const float2* __restrict__ qf, int crop, float scale,
+                                                           const float* __restrict__ m, float alpha,
+                                                           const float2* __restrict__ tw_g, float* __restrict__ grad) {
+  extern __shared__ float2 sm[];
+  float2* tw = sm;
+  float2* buf = sm + N;
+  load_twiddles<N>(tw, tw_g);
+  __syncthreads();
+  const int y = blockIdx.x, t = threadIdx.x, half = crop / 2;
+  const float2* row = qf + (size_t)y * crop;
+  auto load = [&](int idx) {
+    const int c = freq_of_idx(idx, N) + half;
+    return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
+  };
+  const float* mr = m + (size_t)y * N;
+  float* gr = grad + (size_t)y * N;
+  auto use = [&](int, int, int x, float2 v) {
+    const float mm = mr[x];
+    gr[x] = scale * v.x * alpha * mm * (1.0f - mm);
+  };
+  fft_load_use<N, +1>(buf, tw, t, load, use);
+}
+
+template <int N>
+cudaError_t adj_rows_n(const float2* t1, const float* lam, int nk, int crop, const float* g, const float2* tw,
+                       float2* u, int planes, cudaStream_t st) {
+  const size_t sm = sizeof(float2) * (N + 2 * PadLen<N>::value);
+  cudaError_t e = cudaFuncSetAttribute(k_adj_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_adj_rows<N><<<dim3(N, planes), Plan<N>::NT, sm, st>>>(t1, lam, nk, crop, g, tw, u);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t adj_cols_n(const float2* u, const float2* phi, const float* lam, int crop, const float2* tw, float2* sk,
+                       int planes, cudaStream_t st) {
+  constexpr int W = AdjW<N>::W;
+  const size_t sm = sizeof(float2) * (N + W * (PadLen<N>::value + 1));
+  cudaError_t e = cudaFuncSetAttribute(k_adj_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_adj_cols<N><<<dim3(crop / W, planes), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, sk);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t grad_rows_n(const float2* qf, int crop, float scale, const float* m, float alpha, const float2* tw,
+                        float* grad, cudaStream_t st) {
+  const size_t sm = sizeof(float2) * (N + PadLen<N>::value);
+  cudaError_t e = cudaFuncSetAttribute(k_grad_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_grad_rows<N><<<N, Plan<N>::NT, sm, st>>>(qf, crop, scale, m, alpha, tw, grad);
+  return cudaGetLastError();
+}
+
+#define ILT_DISPATCH(n, CALL)              \
+  switch (n) {                             \
+    case 32: return CALL(32);              \
+    case 64: return CALL(64);              \
+    case 128: return CALL(128);            \
+    case 256: return CALL(256);            \
+    case 512: return CALL(512);            \
+    case 1024: return CALL(1024);          \
+    case 2048: return CALL(2048);          \
+    default: return cudaErrorInvalidValue; \
+  }
+
+cudaError_t launch_adj_rows(int n, const float2* t1, const float* lam, int nk, int crop, const float* g,
+                            const float2* tw, float2* u, int planes, cudaStream_t st) {
+#define CALL(N) adj_rows_n<N>(t1, lam, nk, crop, g, tw, u, planes, st)
+  ILT_DISPATCH(n, CALL)
+#undef CALL
+}
+cudaError_t launch_adj_cols(int n, const float2* u, const float2* phi, const float* lam, int crop, const float2* tw,
+                            float2* sk, int planes, cudaStream_t st) {
+#define CALL(N) adj_cols_n<N>(u, phi, lam, crop, tw, sk, planes, st)
+  ILT_DISPATCH(n, CALL)
+#undef CALL
+}
+cudaError_t launch_grad_rows(int n, const float2* qf, int crop, float scale, const float* m, float alpha,
+                             const float2* tw, float* grad, cudaStream_t st) {
+#define CALL(N) grad_rows_n<N>(qf, crop, scale, m, alpha, tw, grad, st)
+  ILT_DISPATCH(n, CALL)
+#undef CALL
+}
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct IltLayout {
+  float* m;
+  float2 *rowbuf, *mhat, *t1, *u, *sk, *s, *qf;
+  float *img, *blur;
+  double *partial, *loss;
+  size_t bytes;
+};
+
+// Carves the workspace for P focus planes per group (P = n_focus or 1).
+IltLayout ilt_layout(const litho_kernels* h, int b, int P, void* base) {
+  const size_t N = h->n, C = h->crop, K = h->k;
+  IltLayout L{};
+  size_t off = 0;
+  char* p = static_cast<char*>(base);
+  auto take = [&](size_t bytes) -> char* {
+    char* r = p ? p + off : nullptr;
+    off += up256(bytes);
+    return r;
+  };
+  L.m = reinterpret_cast<float*>(take(N * N * 4));
+  L.rowbuf = reinterpret_cast<float2*>(take(N * C * 8));
+  L.mhat = reinterpret_cast<float2*>(take(C * C * 8));
+  L.t1 = reinterpret_cast<float2*>(take(P * K * N * C * 8));
+  L.u = reinterpret_cast<float2*>(take(P * K * N * C * 8));
+  L.sk = reinterpret_cast<float2*>(take(P * K * C * C * 8));
+  L.s = reinterpret_cast<float2*>(take(C * C * 8));
+  L.qf = reinterpret_cast<float2*>(take(N * C * 8));
+  L.img = reinterpret_cast<float*>(take(P * N * N * 4));
+  L.blur = reinterpret_cast<float*>(take(P * N * N * 4));
+  L.partial = reinterpret_cast<double*>(take(kPartials * 8));
+  L.loss = reinterpret_cast<double*>(take(size_t(b) * 8));
+  L.bytes = off;
+  return L;
+}
+
+}  // namespace
+
+}  // namespace litho
+
+using namespace litho;
+
+extern "C" {
+
+litho_status litho_ilt_workspace_size(const litho_kernels* h, int b, size_t* full_bytes, size_t* min_bytes) {
+  if (!h || b < 1) {
+    set_error("null handle or b < 1");
+    return LITHO_EINVAL;
+  }
+  if (full_bytes) *full_bytes = ilt_layout(h, b, h->n_focus, nullptr).bytes;
+  if (min_bytes) *min_bytes = ilt_layout(h, b, 1, nullptr).bytes;
+  return LITHO_OK;
+}
+
+litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, const float* target_dev, int b,
+                            double dose, double mask_steep, double resist_steep, double threshold, double sigma_nm,
+                            litho_precision prec, float* grad_dev, double* loss_host, void* workspace_dev,
+                            size_t workspace_bytes, void* stream) {
+  if (!h || !theta_dev || !target_dev || !grad_dev || !workspace_dev || b < 1) {
+    set_error("null argument or b < 1");
+    return LITHO_EINVAL;
+  }
+  if (prec != LITHO_PREC_FFT32) {
+    set_error("litho_ilt_grad implements the FP32 FFT path only (LITHO_PREC_FFT32)");
+    return LITHO_EUNSUPPORTED;
+  }
+  if (!std::isfinite(dose) || !std::isfinite(mask_steep) || !std::isfinite(resist_steep) ||
+      !std::isfinite(threshold)) {
+    set_error("non-finite parameter");
+    return LITHO_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) != 0) {
+    set_error("workspace must be 256-byte aligned");
+    return LITHO_EINVAL;
+  }
+  ResistTaps taps;
+  std::string why;
+  if (!resist_taps(sigma_nm, h->pixel_nm, &taps, &why)) {
+    set_error("%s", why.c_str());
+    return LITHO_EINVAL;
+  }
+  if (2 * taps.radius >= h->n) {
+    set_error("blur radius must be below n/2");
+    return LITHO_EINVAL;
+  }
+  const int F = h->n_focus, K = h->k, N = h->n, C = h->crop;
+  const size_t full = ilt_layout(h, b, F, nullptr).bytes, mn = ilt_layout(h, b, 1, nullptr).bytes;
+  int P;
+  if (workspace_bytes >= full) {
+    P = F;
+  } else if (workspace_bytes >= mn) {
+    P = 1;  // one focus plane at a time: its stage-1 fields are rebuilt per plane
+  } else {
+    set_error("workspace too small: %zu bytes given, at least %zu needed", workspace_bytes, mn);
+    return LITHO_ENOMEM;
+  }
+  IltLayout L = ilt_layout(h, b, P, workspace_dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nn = size_t(N) * N;
+  const float scale = float(2.0 * dose / (double(N) * double(N)));
+  for (int clip = 0; clip < b; ++clip) {
+    {
+      ProfScope ps(kStageIltForward, st, 3);
+      k_sigmoid<<<256, 256, 0, st>>>(theta_dev + clip * nn, float(mask_steep), L.m, nn);
+      LITHO_TRY_CUDA(cudaGetLastError());
+      LITHO_TRY_CUDA(launch_mask_spectrum(L.m, 1, N, C, h->d_tw, L.rowbuf, L.mhat, st));
+    }
+    for (int f0 = 0; f0 < F; f0 += P) {
+      {
+        ProfScope ps(kStageIltForward, st, 5);
+        LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, P * K, N, C, h->d_tw, L.t1, st));
+        LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda + size_t(f0) * K, K, N, C, float(dose), h->d_tw, L.img,
+                                         P, (long long)K * N * C, (long long)nn, st));
+        LITHO_TRY_CUDA(launch_resist(L.img, P, N, taps, float(threshold), L.blur, nullptr, st));
+        k_resist_grad<<<kPartials, 256, 0, st>>>(L.blur, target_dev + clip * nn, nn, P, float(resist_steep),
+                                                 float(threshold), L.img, L.partial);
+        LITHO_TRY_CUDA(cudaGetLastError());
+        k_reduce_loss<<<1, 1024, 0, st>>>(L.partial, kPartials, L.loss + clip, f0 > 0 ? 1 : 0);
+        LITHO_TRY_CUDA(cudaGetLastError());
+      }
+      {
+        ProfScope ps(kStageIltBackward, st, 4);
+        LITHO_TRY_CUDA(launch_resist(L.img, P, N, taps, float(threshold), L.blur, nullptr, st));
+        LITHO_TRY_CUDA(launch_adj_rows(N, L.t1, h->d_lambda + size_t(f0) * K, K, C, L.blur, h->d_tw, L.u, P, st));
+        LITHO_TRY_CUDA(launch_adj_cols(N, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
+                                       h->d_tw, L.sk, P * K, st));
+        k_sum_planes<<<256, 256, 0, st>>>(L.sk, P * K, size_t(C) * C, L.s, f0 > 0 ? 1 : 0);
+        LITHO_TRY_CUDA(cudaGetLastError());
+      }
+    }
+    ProfScope ps(kStageIltBackward, st, 2);
+    LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, 1, N, C, h->d_tw, L.qf, st));
+    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, L.m, float(mask_steep), h->d_tw, grad_dev + clip * nn, st));
+  }
+  if (loss_host) {
+    LITHO_TRY_CUDA(cudaMemcpyAsync(loss_host, L.loss, size_t(b) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    LITHO_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  return LITHO_OK;
+}
+
+}  // extern "C"

@@ -102,6 +102,7 @@ cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const f
                                  float2* mhat, cudaStream_t st);
 // Stage 1 (band multiply + inverse DFT over v): for kernels phi[nk][C][C],
 // t1[j][y][c] = sum_v mhat[v][c] phi_j[v][c] e^{+2 pi i v y/N}, j in [0, nk).
+// phi == NULL transforms mhat itself (nk = 1).
 cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int n, int crop, const float2* tw,
                               float2* t1, cudaStream_t st);
 // Stage 2 FFT path: I[y][x] (+)= dose * sum_j lam[j] |sum_c t1[j][y][c] e^{+2 pi i u_c x/N}|^2.

@@ -5,17 +5,6 @@ using namespace litho;
 
 extern "C" {
 
-litho_status litho_ilt_workspace_size(const litho_kernels*, int, size_t* a, size_t* b) {
-  if (a) *a = 0;
-  if (b) *b = 0;
-  set_error("not implemented yet");
-  return LITHO_EUNSUPPORTED;
-}
-litho_status litho_ilt_grad(const litho_kernels*, const float*, const float*, int, double, double, double, double,
-                            double, litho_precision, float*, double*, void*, size_t, void*) {
-  set_error("not implemented yet");
-  return LITHO_EUNSUPPORTED;
-}
 litho_status litho_serve_create(size_t, int, int, litho_server** out) {
   if (out) *out = nullptr;
   set_error("not implemented yet");
