@@ -263,6 +263,10 @@ litho_status litho_serve_cancel(litho_server* s, uint64_t ticket);
 litho_status litho_serve_stats(litho_server* s, litho_serve_stats_t* out);
 /* Waits for running requests, cancels queued ones, frees everything. */
 void litho_serve_destroy(litho_server* s);
+/* Host-side fault injection for tests: bit 0 makes the next admitted
+ * request's device allocation fail (the request ends with LITHO_ENOMEM and
+ * the server carries on).  No GPU fault is involved. */
+litho_status litho_serve_inject_fault(litho_server* s, int fault_mask);
 
 /* ---- tracing ------------------------------------------------------------------------------------- */
 

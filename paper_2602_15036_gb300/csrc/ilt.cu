@@ -304,6 +304,11 @@ IltLayout ilt_layout(const litho_kernels* h, int b, int P, void* base) {
 
 }  // namespace
 
+double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes) {
+  const int P = workspace_bytes >= ilt_layout(h, b, h->n_focus, nullptr).bytes ? h->n_focus : 1;
+  return ilt_layout(h, b, P, workspace).loss;
+}
+
 }  // namespace litho
 
 using namespace litho;

@@ -110,6 +110,9 @@ cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
                               long long img_plane_stride, cudaStream_t st);
 
+// Device address of the per-clip FP64 losses inside an ILT workspace (ilt.cu).
+double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes);
+
 // ---- resist (resist.cu) ---------------------------------------------------------------------
 constexpr int kMaxResistRadius = 64;
 struct ResistTaps {

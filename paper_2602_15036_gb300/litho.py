@@ -82,6 +82,7 @@ _SIGS = {
     "litho_serve_cancel": (c_int, [c_void_p, c_uint64]),
     "litho_serve_stats": (c_int, [c_void_p, POINTER(litho_serve_stats_t)]),
     "litho_serve_destroy": (None, [c_void_p]),
+    "litho_serve_inject_fault": (c_int, [c_void_p, c_int]),
     "litho_profile_enable": (c_int, [c_int]),
     "litho_profile_reset": (None, []),
     "litho_profile_read": (c_int, [c_int, c_char_p, POINTER(c_double), POINTER(ctypes.c_longlong), POINTER(c_int)]),
@@ -307,6 +308,69 @@ def litho_ilt_grad(kern: Kernels, theta, target, dose=1.0, mask_steep=4.0, resis
                                 loss.ctypes.data_as(POINTER(c_double)) if want_loss else None,
                                 c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream)))
     return grad, loss
+
+
+class Server:
+    """litho_serve_*: continuous-batching request server (one clip per request).
+
+    submit() copies nothing: the numpy arrays given for input, target and
+    output must stay alive until poll() reports the request finished; the
+    server keeps references to them for that reason.
+    """
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4, max_queue: int = 4096):
+        h = c_void_p()
+        _check(lib().litho_serve_create(hbm_budget_bytes, max_slots, max_queue, byref(h)))
+        self.handle = h
+        self._keep = {}
+
+    def submit(self, kind, optics, n, pixel_nm, defocus_nm, k, input_host, output_host, target_host=None,
+               precision="fft32", dose=1.0, sigma_nm=10.0, threshold=0.3, mask_steep=4.0, resist_steep=25.0):
+        """kind: 'image' or 'ilt'.  Arrays: contiguous float32 numpy [n][n].
+        Returns (ticket, loss_buffer) where loss_buffer[0] receives the ILT loss."""
+        loss = np.zeros(1)
+        r = litho_request()
+        r.kind = REQ_IMAGE if kind == "image" else REQ_ILT_STEP
+        r.optics = optics
+        r.n, r.pixel_nm, r.defocus_nm, r.k = n, pixel_nm, defocus_nm, k
+        r.precision = PREC[precision]
+        r.dose, r.sigma_nm, r.threshold, r.mask_steep, r.resist_steep = dose, sigma_nm, threshold, mask_steep, \
+            resist_steep
+        r.input_host = input_host.ctypes.data
+        r.target_host = target_host.ctypes.data if target_host is not None else None
+        r.output_host = output_host.ctypes.data
+        r.loss_host = loss.ctypes.data
+        t = c_uint64()
+        _check(lib().litho_serve_submit(self.handle, byref(r), byref(t)))
+        self._keep[t.value] = (input_host, output_host, target_host, loss, optics)
+        return t.value, loss
+
+    def poll(self, ticket: int, timeout_ms: int = 0) -> int:
+        """Status code: OK, ETIMEOUT (pending), ECANCELED or the request's error."""
+        return lib().litho_serve_poll(self.handle, ticket, timeout_ms)
+
+    def cancel(self, ticket: int) -> int:
+        return lib().litho_serve_cancel(self.handle, ticket)
+
+    def inject_fault(self, mask: int):
+        _check(lib().litho_serve_inject_fault(self.handle, mask))
+
+    def stats(self) -> dict:
+        s = litho_serve_stats_t()
+        _check(lib().litho_serve_stats(self.handle, byref(s)))
+        return {f: getattr(s, f) for f, _ in litho_serve_stats_t._fields_}
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lib().litho_serve_destroy(self.handle)
+            self.handle = c_void_p(0)
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def litho_profile_enable(on: bool = True):
