@@ -287,7 +287,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fft32", "bf16", "bf16x3", "fp16x3", "fp16"], default="fft32")
+    ap.add_argument("--precision", choices=["fft32", "bf16", "bf16x3", "fp16x3", "fp16", "fft32/coarse", "fp16x3/coarse", "fp16/coarse", "bf16x3/coarse"], default="fft32")
     ap.add_argument("--clips", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

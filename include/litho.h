@@ -81,6 +81,13 @@ typedef enum {
   LITHO_PREC_FP16X3 = 3, /* tcgen05 DFT-GEMM, split fp16 hi/lo (scaled), three products */
   LITHO_PREC_FP16 = 4    /* tcgen05 DFT-GEMM, fp16 operands (scaled), FP32 accumulation */
 } litho_precision;
+/* OR-ed into a precision: evaluate the coherent fields on the coarse grid
+ * nc x nc, nc the smallest power of two >= 2C, and interpolate I to N x N
+ * exactly (I = sum_k lam_k |E_k|^2 has no frequency at or beyond C along
+ * either axis, so nc >= 2C samples determine it; the interpolation is a
+ * forward transform on nc and an inverse transform on N).  Ignored when
+ * nc >= N.  Exact up to rounding; saves about (N/nc)^2 of the stage-2 work. */
+#define LITHO_GRID_COARSE 0x100
 /* Tensor-core modes need n a multiple of 128 and an sm_103 device (else
  * EUNSUPPORTED); the fp16 modes scale the stage-1 fields per kernel by a power
  * of two chosen for masks with |m| <= 1. */

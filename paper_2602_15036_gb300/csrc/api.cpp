@@ -52,6 +52,17 @@ litho_status upload(litho_kernels* h) {
   LITHO_TRY_CUDA(cudaMemcpy(h->d_lambda, lam.data(), lam.size() * sizeof(float), cudaMemcpyHostToDevice));
   LITHO_TRY_CUDA(cudaMemcpy(h->d_phi, phi.data(), phi.size() * sizeof(float2), cudaMemcpyHostToDevice));
   LITHO_TRY_CUDA(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  // coarse grid: I has no frequency at or beyond C along either axis, so
+  // nc >= 2C samples determine it exactly
+  int nc = 32;
+  while (nc < 2 * C) nc *= 2;
+  h->nc = nc < N ? nc : 0;
+  if (h->nc) {
+    std::vector<float2> twc(h->nc);
+    fft_twiddle_table(h->nc, twc.data());
+    LITHO_TRY_CUDA(cudaMalloc(&h->d_twc, twc.size() * sizeof(float2)));
+    LITHO_TRY_CUDA(cudaMemcpy(h->d_twc, twc.data(), twc.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   return LITHO_OK;
 }
 
@@ -89,6 +100,7 @@ void litho_free_kernels(litho_kernels* h) {
   cudaFree(h->d_lambda);
   cudaFree(h->d_phi);
   cudaFree(h->d_tw);
+  cudaFree(h->d_twc);
   gemm_free_operands(h);
   cudaSetDevice(cur);
   delete h;
@@ -262,31 +274,66 @@ litho_status litho_kernels_phi(const litho_kernels* h, double* phi_host) {
 
 // ---- aerial ------------------------------------------------------------------------------------------
 
-static size_t aerial_layout(const litho_kernels* h, int b, litho_precision prec, void* ws, float2** rowbuf,
-                            float2** mhat, float2** t1, void** gemm_ws) {
+// Workspace regions of litho_aerial.  With the coarse grid the fields are
+// evaluated on nc x nc and `ic` holds those images until the upsampling
+// (mask-spectrum kernels on a 2C crop, stage 1 over y, real band rows over x)
+// writes the N x N result.
+struct AerialLayout {
+  float2 *rowbuf = nullptr, *mhat = nullptr, *t1 = nullptr;
+  void* gws = nullptr;
+  float* ic = nullptr;
+  float2 *rowbuf2 = nullptr, *spec = nullptr, *q = nullptr;
+  size_t bytes = 0;
+};
+
+static AerialLayout aerial_layout(const litho_kernels* h, int b, litho_precision prec, bool coarse, void* ws) {
   Carve c(ws, 0);
-  const size_t N = h->n, C = h->crop, F = h->n_focus, K = h->k;
-  float2* r = c.take<float2>(size_t(b) * N * C);
-  float2* m = c.take<float2>(size_t(b) * C * C);
-  float2* t = nullptr;
-  void* g = nullptr;
+  const size_t N = h->n, C = h->crop, F = h->n_focus, K = h->k, NE = coarse ? h->nc : h->n;
+  AerialLayout L;
+  L.rowbuf = c.take<float2>(size_t(b) * N * C);
+  L.mhat = c.take<float2>(size_t(b) * C * C);
+  size_t planes = F;
   if (prec == LITHO_PREC_FFT32) {
-    t = c.take<float2>(F * K * N * C);
+    L.t1 = c.take<float2>(F * K * NE * C);
   } else {
-    g = c.take<char>(gemm_workspace_bytes(h, prec, b));
+    L.gws = c.take<char>(gemm_workspace_bytes(h, prec, b, coarse));
+    planes = size_t(std::min(b, gemm_group_clips())) * F;
   }
-  if (rowbuf) *rowbuf = r;
-  if (mhat) *mhat = m;
-  if (t1) *t1 = t;
-  if (gemm_ws) *gemm_ws = g;
-  return align_up(c.used);
+  if (coarse) {
+    L.ic = c.take<float>(planes * NE * NE);
+    L.rowbuf2 = c.take<float2>(planes * NE * 2 * C);
+    L.spec = c.take<float2>(planes * 4 * C * C);
+    L.q = c.take<float2>(planes * N * 2 * C);
+  }
+  L.bytes = align_up(c.used);
+  return L;
+}
+
+static bool decode_precision(int raw, litho_precision* p, bool* coarse) {
+  if ((raw & ~(0xFF | LITHO_GRID_COARSE)) != 0) return false;
+  const int base = raw & 0xFF;
+  if (base < LITHO_PREC_FFT32 || base > LITHO_PREC_FP16) return false;
+  *p = static_cast<litho_precision>(base);
+  *coarse = (raw & LITHO_GRID_COARSE) != 0;
+  return true;
+}
+
+static litho_status upsample(const litho_kernels* h, const AerialLayout& L, int planes, float* out, cudaStream_t st) {
+  const int N = h->n, NC = h->nc, C2 = 2 * h->crop;
+  ProfScope ps(kStageUpsample, st, 4);
+  LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, h->d_twc, L.rowbuf2, L.spec, st));
+  LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, planes, N, C2, h->d_tw, L.q, st));
+  LITHO_TRY_CUDA(launch_band_rows_real(L.q, planes, N, C2, 1.0f, h->d_tw, out, st));
+  return LITHO_OK;
 }
 
 litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes) {
   LITHO_REQUIRE(h && bytes, "null argument");
   LITHO_REQUIRE(b >= 1, "b must be >= 1");
-  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16, "unknown precision");
-  *bytes = aerial_layout(h, b, prec, nullptr, nullptr, nullptr, nullptr, nullptr);
+  litho_precision p;
+  bool coarse;
+  LITHO_REQUIRE(decode_precision(int(prec), &p, &coarse), "unknown precision");
+  *bytes = aerial_layout(h, b, p, coarse && h->nc > 0, nullptr).bytes;
   return LITHO_OK;
 }
 
@@ -295,50 +342,58 @@ litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, 
   LITHO_REQUIRE(h && mask_dev && intensity_dev && workspace_dev, "null argument");
   LITHO_REQUIRE(b >= 1, "b must be >= 1");
   LITHO_REQUIRE(std::isfinite(dose), "dose must be finite");
-  LITHO_REQUIRE(prec >= LITHO_PREC_FFT32 && prec <= LITHO_PREC_FP16, "unknown precision");
+  litho_precision p;
+  bool coarse;
+  LITHO_REQUIRE(decode_precision(int(prec), &p, &coarse), "unknown precision");
+  coarse = coarse && h->nc > 0;
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(workspace_dev) & 255) == 0, "workspace must be 256-byte aligned");
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(mask_dev) & 15) == 0 && (reinterpret_cast<uintptr_t>(intensity_dev) & 15) == 0,
                 "mask and intensity must be 16-byte aligned");
-  const size_t need = aerial_layout(h, b, prec, nullptr, nullptr, nullptr, nullptr, nullptr);
+  const size_t need = aerial_layout(h, b, p, coarse, nullptr).bytes;
   if (workspace_bytes < need) {
     set_error("workspace too small: %zu bytes given, %zu needed", workspace_bytes, need);
     return LITHO_ENOMEM;
   }
-  if (prec != LITHO_PREC_FFT32) {
-    litho_status s = gemm_supported(h, prec);
+  if (p != LITHO_PREC_FFT32) {
+    litho_status s = gemm_supported(h, p, coarse);
     if (s != LITHO_OK) return s;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  float2 *rowbuf, *mhat, *t1;
-  void* gws;
-  aerial_layout(h, b, prec, workspace_dev, &rowbuf, &mhat, &t1, &gws);
+  const AerialLayout L = aerial_layout(h, b, p, coarse, workspace_dev);
   const int N = h->n, C = h->crop, F = h->n_focus, K = h->k;
   {
     ProfScope ps(kStageMaskSpectrum, st, 2);
-    LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev, b, N, C, h->d_tw, rowbuf, mhat, st));
+    LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev, b, N, C, h->d_tw, L.rowbuf, L.mhat, st));
   }
-  if (prec != LITHO_PREC_FFT32) {
+  if (p != LITHO_PREC_FFT32) {
     const int G = gemm_group_clips();
     for (int c0 = 0; c0 < b; c0 += G) {
-      litho_status s = gemm_aerial_group(h, mhat + size_t(c0) * C * C, std::min(G, b - c0), float(dose), prec,
-                                         intensity_dev + size_t(c0) * F * N * N, gws, st);
+      const int g = std::min(G, b - c0);
+      float* dst = intensity_dev + size_t(c0) * F * N * N;
+      litho_status s =
+          gemm_aerial_group(h, L.mhat + size_t(c0) * C * C, g, float(dose), p, coarse, coarse ? L.ic : dst, L.gws, st);
       if (s != LITHO_OK) return s;
+      if (coarse && (s = upsample(h, L, g * F, dst, st)) != LITHO_OK) return s;
     }
     return LITHO_OK;
   }
+  const int NE = coarse ? h->nc : N;
+  const float2* tw = coarse ? h->d_twc : h->d_tw;
   for (int clip = 0; clip < b; ++clip) {
-    const float2* mh = mhat + size_t(clip) * C * C;
+    const float2* mh = L.mhat + size_t(clip) * C * C;
     float* img = intensity_dev + size_t(clip) * F * N * N;
     {
-      {
-        ProfScope ps(kStageStage1Fft, st, 1);
-        LITHO_TRY_CUDA(launch_stage1_fft(mh, h->d_phi, F * K, N, C, h->d_tw, t1, st));
-      }
-      {
-        ProfScope ps(kStageStage2Fft, st, 1);
-        LITHO_TRY_CUDA(launch_stage2_fft(t1, h->d_lambda, K, N, C, float(dose), h->d_tw, img, F,
-                                         (long long)K * N * C, (long long)N * N, st));
-      }
+      ProfScope ps(kStageStage1Fft, st, 1);
+      LITHO_TRY_CUDA(launch_stage1_fft(mh, h->d_phi, F * K, NE, C, tw, L.t1, st));
+    }
+    {
+      ProfScope ps(kStageStage2Fft, st, 1);
+      LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda, K, NE, C, float(dose), tw, coarse ? L.ic : img, F,
+                                       (long long)K * NE * C, (long long)NE * NE, st));
+    }
+    if (coarse) {
+      litho_status s = upsample(h, L, F, img, st);
+      if (s != LITHO_OK) return s;
     }
   }
   return LITHO_OK;

@@ -103,8 +103,9 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_stage1(const float
   const int j = blockIdx.y, u0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
   for (int i = tid; i < W * LD; i += blockDim.x) buf[i] = make_float2(0.f, 0.f);
   __syncthreads();
+  // with kernels: one spectrum times kernel j; without: spectrum j itself
   const float2* ph = phi + (size_t)j * crop * crop + u0;
-  const float2* mh = mhat + u0;
+  const float2* mh = mhat + (phi ? 0 : (size_t)j * crop * crop) + u0;
   for (int i = tid; i < crop * W; i += blockDim.x) {
     const int cv = i / W, w = i % W;
     const int idx = (cv - half + N) % N;
@@ -162,6 +163,34 @@ __global__ void __launch_bounds__(Plan<N>::NT, 4) k_stage2(const float2* __restr
       for (int q = 0; q < RL; ++q) out[jj + q * (N / RL)] = dose * acc[p][q];
     }
   }
+}
+
+// ---- band rows to real image rows: out[p][y][x] = scale Re(sum_c q[p][y][c] e^{2 pi i u_c x/N}) ----------
+// Second half of the exact Fourier interpolation from the coarse grid.
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_real(const float2* __restrict__ q, int crop, float scale,
+                                                                const float2* __restrict__ tw_g,
+                                                                float* __restrict__ out) {
+  __shared__ float2 buf[PadLen<N>::value];
+  __shared__ float2 tw[N];
+  load_twiddles<N>(tw, tw_g);
+  __syncthreads();
+  const int y = blockIdx.x, p = blockIdx.y, half = crop / 2;
+  const float2* row = q + ((size_t)p * N + y) * crop;
+  auto load = [&](int idx) {
+    const int c = freq_of(idx, N) + half;
+    return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
+  };
+  float* o = out + ((size_t)p * N + y) * N;
+  auto use = [&](int, int, int x, float2 v) { o[x] = scale * v.x; };
+  fft_load_use<N, +1>(buf, tw, threadIdx.x, load, use);
+}
+
+template <int N>
+cudaError_t band_rows_real_n(const float2* q, int planes, int crop, float scale, const float2* tw, float* out,
+                             cudaStream_t st) {
+  k_band_rows_real<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out);
+  return cudaGetLastError();
 }
 
 template <int N>
@@ -230,6 +259,13 @@ bool fft_twiddle_table(int n, float2* out) {
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
                                  float2* mhat, cudaStream_t st) {
 #define CALL(N) mask_spectrum_n<N>(m, b, crop, tw, rowbuf, mhat, st)
+  LITHO_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+cudaError_t launch_band_rows_real(const float2* q, int planes, int n, int crop, float scale, const float2* tw,
+                                  float* out, cudaStream_t st) {
+#define CALL(N) band_rows_real_n<N>(q, planes, crop, scale, tw, out, st)
   LITHO_DISPATCH_N(n, CALL)
 #undef CALL
 }

@@ -471,12 +471,13 @@ bool make_map(CUtensorMap* m, void* base, int fmt, unsigned long long rows, unsi
 
 }  // namespace
 
+// Constant operands per precision mode and grid (0 = full N, 1 = coarse nc).
 struct GemmOperands {
   std::mutex mu;
-  bool built[kModes] = {};
-  void* b_hi[kModes] = {};
-  void* b_lo[kModes] = {};
-  CUtensorMap map_hi[kModes], map_lo[kModes];
+  bool built[kModes][2] = {};
+  void* b_hi[kModes][2] = {};
+  void* b_lo[kModes][2] = {};
+  CUtensorMap map_hi[kModes][2], map_lo[kModes][2];
   float* d_lamp[kModes] = {};   // lambda / scale^2 per (f, k)
   float* d_scale[kModes] = {};  // stage-1 scale per (f, k)
   int* d_err = nullptr;
@@ -485,8 +486,10 @@ struct GemmOperands {
 
 namespace {
 
-size_t per_clip_bytes(const litho_kernels* h, int mode) {
-  const size_t rows = size_t(h->n_focus) * h->k * h->n, cols = size_t(2) * h->crop;
+int eval_n(const litho_kernels* h, bool coarse) { return coarse ? h->nc : h->n; }
+
+size_t per_clip_bytes(const litho_kernels* h, int mode, bool coarse) {
+  const size_t rows = size_t(h->n_focus) * h->k * eval_n(h, coarse), cols = size_t(2) * h->crop;
   return rows * cols * 2 * (is_split(mode) ? 2 : 1);
 }
 
@@ -494,13 +497,18 @@ size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
 // Builds the twiddle operand B (cos | sin chunks, split) and the per-kernel
 // scales for one precision mode.  Host FP64, then rounded.
-litho_status build_operands(const litho_kernels* hc, int mode) {
+litho_status build_operands(const litho_kernels* hc, int mode, bool coarse) {
   litho_kernels* h = const_cast<litho_kernels*>(hc);
-  if (!h->gemm) h->gemm = new GemmOperands();
+  static std::mutex create_mu;
+  {
+    std::lock_guard<std::mutex> lk0(create_mu);
+    if (!h->gemm) h->gemm = new GemmOperands();
+  }
   GemmOperands* g = h->gemm;
   std::lock_guard<std::mutex> lk(g->mu);
-  if (g->built[mode]) return LITHO_OK;
-  const int N = h->n, C = h->crop, F = h->n_focus, K = h->k;
+  const int gi = coarse ? 1 : 0;
+  if (g->built[mode][gi]) return LITHO_OK;
+  const int N = eval_n(h, coarse), C = h->crop, F = h->n_focus, K = h->k;
   const size_t cols = size_t(2) * C, count = size_t(N) * cols;
   std::vector<uint16_t> hi(count), lo(count);
   for (int x = 0; x < N; ++x) {
@@ -542,45 +550,48 @@ litho_status build_operands(const litho_kernels* hc, int mode) {
       scale[fk] = float(s);
       lamp[fk] = float(h->lambda[fk] / (s * s));
     }
-  LITHO_TRY_CUDA(cudaMalloc(&g->b_hi[mode], count * 2));
-  LITHO_TRY_CUDA(cudaMemcpy(g->b_hi[mode], hi.data(), count * 2, cudaMemcpyHostToDevice));
+  LITHO_TRY_CUDA(cudaMalloc(&g->b_hi[mode][gi], count * 2));
+  LITHO_TRY_CUDA(cudaMemcpy(g->b_hi[mode][gi], hi.data(), count * 2, cudaMemcpyHostToDevice));
   if (is_split(mode)) {
-    LITHO_TRY_CUDA(cudaMalloc(&g->b_lo[mode], count * 2));
-    LITHO_TRY_CUDA(cudaMemcpy(g->b_lo[mode], lo.data(), count * 2, cudaMemcpyHostToDevice));
+    LITHO_TRY_CUDA(cudaMalloc(&g->b_lo[mode][gi], count * 2));
+    LITHO_TRY_CUDA(cudaMemcpy(g->b_lo[mode][gi], lo.data(), count * 2, cudaMemcpyHostToDevice));
   }
-  LITHO_TRY_CUDA(cudaMalloc(&g->d_scale[mode], scale.size() * sizeof(float)));
-  LITHO_TRY_CUDA(cudaMemcpy(g->d_scale[mode], scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
-  LITHO_TRY_CUDA(cudaMalloc(&g->d_lamp[mode], lamp.size() * sizeof(float)));
-  LITHO_TRY_CUDA(cudaMemcpy(g->d_lamp[mode], lamp.data(), lamp.size() * sizeof(float), cudaMemcpyHostToDevice));
+  if (!g->d_scale[mode]) {
+    LITHO_TRY_CUDA(cudaMalloc(&g->d_scale[mode], scale.size() * sizeof(float)));
+    LITHO_TRY_CUDA(cudaMemcpy(g->d_scale[mode], scale.data(), scale.size() * sizeof(float), cudaMemcpyHostToDevice));
+    LITHO_TRY_CUDA(cudaMalloc(&g->d_lamp[mode], lamp.size() * sizeof(float)));
+    LITHO_TRY_CUDA(cudaMemcpy(g->d_lamp[mode], lamp.data(), lamp.size() * sizeof(float), cudaMemcpyHostToDevice));
+  }
   if (!g->d_err) {
     LITHO_TRY_CUDA(cudaMalloc(&g->d_err, sizeof(int)));
     LITHO_TRY_CUDA(cudaMemset(g->d_err, 0, sizeof(int)));
   }
   const int fmt = is_fp16(mode) ? 0 : 1;
-  if (!make_map(&g->map_hi[mode], g->b_hi[mode], fmt, N, cols) ||
-      !make_map(&g->map_lo[mode], is_split(mode) ? g->b_lo[mode] : g->b_hi[mode], fmt, N, cols)) {
+  if (!make_map(&g->map_hi[mode][gi], g->b_hi[mode][gi], fmt, N, cols) ||
+      !make_map(&g->map_lo[mode][gi], is_split(mode) ? g->b_lo[mode][gi] : g->b_hi[mode][gi], fmt, N, cols)) {
     set_error("cuTensorMapEncodeTiled failed for the twiddle operand");
     return LITHO_ECUDA;
   }
   int dev = 0;
   LITHO_TRY_CUDA(cudaGetDevice(&dev));
   LITHO_TRY_CUDA(cudaDeviceGetAttribute(&g->sm_count, cudaDevAttrMultiProcessorCount, dev));
-  g->built[mode] = true;
+  g->built[mode][gi] = true;
   return LITHO_OK;
 }
 
 }  // namespace
 
-size_t gemm_workspace_bytes(const litho_kernels* h, litho_precision prec, int b) {
+size_t gemm_workspace_bytes(const litho_kernels* h, litho_precision prec, int b, bool coarse) {
   const int mode = mode_of(prec);
   const int g = std::min(b, GROUP_CLIPS);
-  const size_t half = up256(size_t(g) * per_clip_bytes(h, mode) / (is_split(mode) ? 2 : 1));
+  const size_t half = up256(size_t(g) * per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1));
   return is_split(mode) ? 2 * half : half;
 }
 
-litho_status gemm_supported(const litho_kernels* h, litho_precision prec) {
-  if (h->n < 128 || h->n % 128 != 0 || h->crop % CH != 0) {
-    set_error("tensor-core path needs n a multiple of 128 (got n = %d, crop = %d)", h->n, h->crop);
+litho_status gemm_supported(const litho_kernels* h, litho_precision prec, bool coarse) {
+  const int n = eval_n(h, coarse);
+  if (n < 128 || n % 128 != 0 || h->crop % CH != 0) {
+    set_error("tensor-core path needs an evaluation grid that is a multiple of 128 (got %d, crop = %d)", n, h->crop);
     return LITHO_EUNSUPPORTED;
   }
   int dev = 0, major = 0, minor = 0;
@@ -595,34 +606,36 @@ litho_status gemm_supported(const litho_kernels* h, litho_precision prec) {
     set_error("cuTensorMapEncodeTiled is not available from the driver");
     return LITHO_EUNSUPPORTED;
   }
-  return build_operands(h, mode_of(prec));
+  return build_operands(h, mode_of(prec), coarse);
 }
 
 litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int clips, float dose,
-                               litho_precision prec, float* img, void* ws, cudaStream_t st) {
-  const int mode = mode_of(prec);
+                               litho_precision prec, bool coarse, float* img, void* ws, cudaStream_t st) {
+  const int mode = mode_of(prec), gi = coarse ? 1 : 0;
   GemmOperands* g = h->gemm;
-  const int N = h->n, C = h->crop, F = h->n_focus, K = h->k;
-  const size_t half = up256(size_t(std::min(clips, GROUP_CLIPS)) * per_clip_bytes(h, mode) / (is_split(mode) ? 2 : 1));
+  const int N = eval_n(h, coarse), C = h->crop, F = h->n_focus, K = h->k;
+  const float2* tw = coarse ? h->d_twc : h->d_tw;
+  const size_t half =
+      up256(size_t(std::min(clips, GROUP_CLIPS)) * per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1));
   char* a_hi = static_cast<char*>(ws);
   char* a_lo = is_split(mode) ? a_hi + half : a_hi;
-  const size_t clip_half = per_clip_bytes(h, mode) / (is_split(mode) ? 2 : 1);
+  const size_t clip_half = per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1);
   {
     ProfScope ps(kStageGemmOperands, st, clips);
     for (int c = 0; c < clips; ++c) {
       const float2* mh = mhat + size_t(c) * C * C;
       cudaError_t e;
       if (mode == kBF16)
-        e = stage1_split_mode<kBF16>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+        e = stage1_split_mode<kBF16>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
                                      nullptr, st);
       else if (mode == kFP16)
-        e = stage1_split_mode<kFP16>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+        e = stage1_split_mode<kFP16>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
                                      nullptr, st);
       else if (mode == kBF16X3)
-        e = stage1_split_mode<kBF16X3>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+        e = stage1_split_mode<kBF16X3>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
                                        a_lo + c * clip_half, st);
       else
-        e = stage1_split_mode<kFP16X3>(N, mh, h->d_phi, F * K, C, h->d_tw, g->d_scale[mode], a_hi + c * clip_half,
+        e = stage1_split_mode<kFP16X3>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
                                        a_lo + c * clip_half, st);
       LITHO_TRY_CUDA(e);
     }
@@ -652,7 +665,7 @@ litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int c
   const int grid = std::min(total, g->sm_count);
   LITHO_TRY_CUDA(cudaFuncSetAttribute(k_dft_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   ProfScope ps(kStageStage2Gemm, st, 1);
-  k_dft_gemm<<<grid, THREADS, SMEM_BYTES, st>>>(ta_hi, ta_lo, g->map_hi[mode], g->map_lo[mode], p);
+  k_dft_gemm<<<grid, THREADS, SMEM_BYTES, st>>>(ta_hi, ta_lo, g->map_hi[mode][gi], g->map_lo[mode][gi], p);
   LITHO_TRY_CUDA(cudaGetLastError());
   return LITHO_OK;
 }
@@ -675,8 +688,10 @@ litho_status gemm_check_device(const litho_kernels* h, cudaStream_t st) {
 void gemm_free_operands(litho_kernels* h) {
   if (!h->gemm) return;
   for (int m = 0; m < kModes; ++m) {
-    cudaFree(h->gemm->b_hi[m]);
-    cudaFree(h->gemm->b_lo[m]);
+    for (int gi = 0; gi < 2; ++gi) {
+      cudaFree(h->gemm->b_hi[m][gi]);
+      cudaFree(h->gemm->b_lo[m][gi]);
+    }
     cudaFree(h->gemm->d_lamp[m]);
     cudaFree(h->gemm->d_scale[m]);
   }

@@ -37,6 +37,7 @@ enum Stage {
   kStageIltForward,
   kStageIltBackward,
   kStageIltReduce,
+  kStageUpsample,
   kStageCount
 };
 // Records a CUDA event pair around its lifetime on `st` when profiling is on.
@@ -87,7 +88,9 @@ struct litho_kernels {
   std::vector<double> phi_host;            // [F][K][C][C][2]
   float* d_lambda = nullptr;               // [F*K]
   float2* d_phi = nullptr;                 // [F][K][C][C]
-  float2* d_tw = nullptr;                  // e^{-2 pi i j/N}, j in [0, N)
+  float2* d_tw = nullptr;                  // FFT twiddle table for N
+  int nc = 0;                              // coarse grid: smallest power of two >= 2 crop, 0 if not below N
+  float2* d_twc = nullptr;                 // FFT twiddle table for nc
   litho::GemmOperands* gemm = nullptr;     // lazily built per precision
   int device = 0;
 };
@@ -102,7 +105,7 @@ cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const f
                                  float2* mhat, cudaStream_t st);
 // Stage 1 (band multiply + inverse DFT over v): for kernels phi[nk][C][C],
 // t1[j][y][c] = sum_v mhat[v][c] phi_j[v][c] e^{+2 pi i v y/N}, j in [0, nk).
-// phi == NULL transforms mhat itself (nk = 1).
+// phi == NULL transforms nk spectra mhat[j][C][C] themselves.
 cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int n, int crop, const float2* tw,
                               float2* t1, cudaStream_t st);
 // Stage 2 FFT path: I[y][x] (+)= dose * sum_j lam[j] |sum_c t1[j][y][c] e^{+2 pi i u_c x/N}|^2.
@@ -112,6 +115,10 @@ cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n,
 
 // Device address of the per-clip FP64 losses inside an ILT workspace (ilt.cu).
 double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes);
+
+// out[p][y][x] = scale Re(sum_c q[p][y][c] e^{+2 pi i u_c x/N}) for band rows q[p][N][C].
+cudaError_t launch_band_rows_real(const float2* q, int planes, int n, int crop, float scale, const float2* tw,
+                                  float* out, cudaStream_t st);
 
 // ---- resist (resist.cu) ---------------------------------------------------------------------
 constexpr int kMaxResistRadius = 64;

@@ -369,8 +369,8 @@ litho_status litho_serve_submit(litho_server* s, const litho_request* req, uint6
   const bool pow2 = r.n >= 32 && r.n <= 2048 && (r.n & (r.n - 1)) == 0;
   if (!pow2 || r.k < 1 || r.k > 1024 || !(r.pixel_nm > 0) || !std::isfinite(r.defocus_nm) || !r.input_host ||
       !r.output_host || (r.kind != LITHO_REQ_IMAGE && r.kind != LITHO_REQ_ILT_STEP) ||
-      (r.kind == LITHO_REQ_ILT_STEP && !r.target_host) || r.precision < LITHO_PREC_FFT32 ||
-      r.precision > LITHO_PREC_FP16) {
+      (r.kind == LITHO_REQ_ILT_STEP && !r.target_host) || (r.precision & ~(0xFF | LITHO_GRID_COARSE)) != 0 ||
+      (r.precision & 0xFF) > LITHO_PREC_FP16) {
     set_error("invalid request fields");
     std::lock_guard<std::mutex> lk(s->mu);
     s->rejected++;

@@ -22,6 +22,15 @@ STATUS_NAMES = ["OK", "EINVAL", "ENOMEM", "ECUDA", "EBUSY", "ETIMEOUT", "ECANCEL
 
 SRC_ANNULAR, SRC_QUADRUPOLE, SRC_CUSTOM = 0, 1, 2
 PREC = {"fft32": 0, "bf16": 1, "bf16x3": 2, "fp16x3": 3, "fp16": 4}
+GRID_COARSE = 0x100
+
+
+def prec_code(name: str) -> int:
+    """'fft32', 'fp16x3', ... optionally with '/coarse' (LITHO_GRID_COARSE)."""
+    base, _, grid = name.partition("/")
+    if grid not in ("", "coarse"):
+        raise ValueError(f"unknown grid {grid!r}")
+    return PREC[base] | (GRID_COARSE if grid == "coarse" else 0)
 REQ_IMAGE, REQ_ILT_STEP = 0, 1
 
 
@@ -208,7 +217,7 @@ def litho_upload_kernels(n, pixel_nm, lam, phi) -> Kernels:
 
 def litho_aerial_workspace_size(kern: Kernels, b: int, precision="fft32") -> int:
     out = c_size_t()
-    _check(lib().litho_aerial_workspace_size(kern.handle, b, PREC[precision], byref(out)))
+    _check(lib().litho_aerial_workspace_size(kern.handle, b, prec_code(precision), byref(out)))
     return out.value
 
 
@@ -222,7 +231,7 @@ def litho_aerial(kern: Kernels, mask, dose=1.0, precision="fft32", out=None, wor
     if workspace is None:
         workspace = torch.empty(litho_aerial_workspace_size(kern, b, precision), dtype=torch.uint8,
                                 device=mask.device)
-    _check(lib().litho_aerial(kern.handle, c_void_p(mask.data_ptr()), b, dose, PREC[precision],
+    _check(lib().litho_aerial(kern.handle, c_void_p(mask.data_ptr()), b, dose, prec_code(precision),
                               c_void_p(out.data_ptr()), c_void_p(workspace.data_ptr()), workspace.numel(),
                               _stream_ptr(stream)))
     return out
@@ -230,7 +239,7 @@ def litho_aerial(kern: Kernels, mask, dose=1.0, precision="fft32", out=None, wor
 
 def litho_aerial_host_workspace_size(kern: Kernels, b: int, precision="fft32") -> int:
     out = c_size_t()
-    _check(lib().litho_aerial_host_workspace_size(kern.handle, b, PREC[precision], byref(out)))
+    _check(lib().litho_aerial_host_workspace_size(kern.handle, b, prec_code(precision), byref(out)))
     return out.value
 
 
@@ -244,7 +253,7 @@ def litho_aerial_host(kern: Kernels, mask_host, workspace, intensity_host=None, 
             return None
         return c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else c_void_p(a.ctypes.data)
     b = mask_host.shape[0]
-    _check(lib().litho_aerial_host(kern.handle, ptr(mask_host), b, dose, PREC[precision], ptr(intensity_host),
+    _check(lib().litho_aerial_host(kern.handle, ptr(mask_host), b, dose, prec_code(precision), ptr(intensity_host),
                                    sigma_nm, threshold, ptr(printed_host), c_void_p(workspace.data_ptr()),
                                    workspace.numel(), _stream_ptr(stream)))
     return intensity_host, printed_host
@@ -303,7 +312,7 @@ def litho_ilt_grad(kern: Kernels, theta, target, dose=1.0, mask_steep=4.0, resis
         workspace = torch.empty(litho_ilt_workspace_size(kern, b)[0], dtype=torch.uint8, device=theta.device)
     loss = np.zeros(b) if want_loss else None
     _check(lib().litho_ilt_grad(kern.handle, c_void_p(theta.data_ptr()), c_void_p(target.data_ptr()), b, dose,
-                                mask_steep, resist_steep, threshold, sigma_nm, PREC[precision],
+                                mask_steep, resist_steep, threshold, sigma_nm, prec_code(precision),
                                 c_void_p(grad.data_ptr()),
                                 loss.ctypes.data_as(POINTER(c_double)) if want_loss else None,
                                 c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream)))
@@ -333,7 +342,7 @@ class Server:
         r.kind = REQ_IMAGE if kind == "image" else REQ_ILT_STEP
         r.optics = optics
         r.n, r.pixel_nm, r.defocus_nm, r.k = n, pixel_nm, defocus_nm, k
-        r.precision = PREC[precision]
+        r.precision = prec_code(precision)
         r.dose, r.sigma_nm, r.threshold, r.mask_steep, r.resist_steep = dose, sigma_nm, threshold, mask_steep, \
             resist_steep
         r.input_host = input_host.ctypes.data
