@@ -8,13 +8,19 @@ focus plane at defocus -50/0/+50 nm, Manhattan masks of seeded random
 rectangles (sides 40-120 nm) at 35 % density, Gaussian resist sigma 10 nm,
 threshold 0.3.  Inputs are synthetic (the paper's layouts are not available).
 
-One step = mask spectrum + band multiply + two-stage inverse transform with
-fused lam |E|^2 accumulation (every clip, every focus plane, every kernel)
-+ resist blur and threshold, over the whole batch, inputs resident in HBM.
-`value` is Mpx/s = clips * N^2 / step time (a clip's pixel counts once and
-includes all K kernels and all focus planes).  `e2e` is the same through the
-host-buffer C-ABI call: masks copied in from pinned memory, printed resist
-bytes copied back.
+One step = mask spectrum + band multiply + inverse transforms with fused
+lam |E|^2 accumulation (every clip, every focus plane, every kernel) + resist
+blur and threshold, over the whole batch, inputs resident in HBM.  `value`
+is Mpx/s = clips * N^2 / step time (a clip's pixel counts once and includes
+all K kernels and all focus planes) for the fastest path whose error bound
+is 1e-5 (the FP32 FFT path on the coarse grid).  The same line carries the
+plain FP32 FFT path and the split fp16 tensor-core path, timed the same way.
+`e2e` is the headline path through the host-buffer C-ABI call: masks copied in
+from pinned memory, printed resist bytes copied back.
+
+Other workloads (one JSON line each): --workload ilt (16 clips of 1024^2,
+annular, K=16, 5 focus planes, one ILT gradient step per step) and
+--workload serve (Poisson stream of mixed requests through litho_serve).
 
 Multi-GPU: clips are independent, so each rank images its own batch (weak
 scaling, no collective on the data path).
@@ -23,6 +29,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -45,15 +52,19 @@ OPTICS = dict(wavelength_nm=193.0, na=1.35, n_medium=1.44, kind="quadrupole", sr
               pole_radius=0.1)
 WORKLOAD = "socs-aerial+resist 2048x2048@8nm quadrupole41 K=24 focus(-50,0,50)"
 METRIC = "aerial-image Mpx/s (2048² clips, K=24) vs plain FFT path at ≤1e-5 err; p99 ms"
+HEADLINE = "fft32/coarse"
+COMPARE = ["fft32", "fp16x3/coarse"]   # the plain FFT path, the split tensor-core path
+ERROR_BOUND = {"fft32": 1e-5, "fft32/coarse": 1e-5, "fp16x3": 1e-5, "fp16x3/coarse": 1e-5, "bf16x3": 5e-5,
+               "bf16x3/coarse": 5e-5, "fp16": 2e-3, "fp16/coarse": 2e-3, "bf16": 4e-3}
 
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
 
 
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            p = json.load(f)
-        return p, "measured"
+            return json.load(f), "measured"
     except Exception:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
@@ -120,6 +131,59 @@ def _dist():
     return world, rank, local
 
 
+def clip_seeds(rank: int, clips: int, base: int = 1234):
+    """Seeds of the clips rank `rank` images: disjoint blocks per rank."""
+    return [base + rank * clips + i for i in range(clips)]
+
+
+def whole_job_rate(units_per_rank: float, world: int, rank_seconds: list[float]) -> float:
+    """Units per second of the whole job: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / max(rank_seconds)
+
+
+# ---- algorithmic work models (per step) ------------------------------------------------------------
+
+def stage_models(prec: str, clips: int, n: int, crop: int, n_focus: int, k_eff: int, nc: int, peaks) -> dict:
+    """stage -> (bound, work per step, unit, peak): FLOPs for transforms and GEMMs, bytes for the resist."""
+    coarse = prec.endswith("/coarse") and nc > 0
+    ne = nc if coarse else n
+    planes_k = clips * n_focus * k_eff
+    fft = lambda m: 5.0 * m * math.log2(m)  # noqa: E731  (radix-2 operation count of an m-point transform)
+    hbm = peaks["hbm_gbs"]
+    tensor = peaks["bf16_tflops_sustained"]
+    base = prec.split("/")[0]
+    split = base in ("fp16x3", "bf16x3")
+    m = {
+        "mask_spectrum": ("hbm", clips * n * n * 4.0, "GB/s", hbm),
+        "stage1_fft": ("alu", planes_k * crop * fft(ne), "TFLOP/s", ALU_PEAK_TFLOPS),
+        "stage1_gemm_operands": ("alu", planes_k * crop * fft(ne), "TFLOP/s", ALU_PEAK_TFLOPS),
+        "stage2_fft": ("alu", planes_k * ne * (fft(ne) + 4.0 * ne), "TFLOP/s", ALU_PEAK_TFLOPS),
+        "stage2_gemm": ("tensor", planes_k * 8.0 * ne * ne * crop * (3 if split else 1), "TFLOP/s", tensor),
+        "resist": ("hbm", clips * n_focus * n * n * 9.0, "GB/s", hbm),
+    }
+    if coarse:
+        c2 = 2 * crop
+        m["upsample"] = ("alu", clips * n_focus * (ne / 2 * fft(ne) + c2 * fft(ne) + c2 * fft(n) + n * fft(n)),
+                         "TFLOP/s", ALU_PEAK_TFLOPS)
+    return m
+
+
+def rooflines(prof: dict, steps: int, models: dict) -> dict:
+    out = {}
+    for stage, (ms, launches) in prof.items():
+        if stage not in models:
+            continue
+        bound, work, unit, peak = models[stage]
+        sec = ms / steps * 1e-3
+        scale = 1e9 if unit == "GB/s" else 1e12
+        achieved = work / sec / scale
+        out[stage] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                      "ms_per_step": ms / steps, "launches_per_step": launches / steps}
+    return out
+
+
+# ---- the oracle as the CPU baseline / reference arm --------------------------------------------------
+
 def _oracle_sample(seed: int, focus_planes):
     """Oracle (FP64 numpy, one thread) on one clip for the given focus planes:
     SOCS image from oracle-built kernels, resist blur and threshold.  Returns
@@ -167,118 +231,285 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args):
-    import torch
+# ---- our implementation --------------------------------------------------------------------------------
 
+class Ctx:
+    def __init__(self, args):
+        import torch
+        self.torch = torch
+        self.world, self.rank, self.local = _dist()
+        torch.cuda.set_device(self.local)
+        self.dev = torch.device("cuda", self.local)
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=self.dev)
+
+    def barrier(self):
+        if self.world > 1:
+            self.torch.distributed.barrier()
+
+    def max_over_ranks(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        t = self.torch.tensor([x], device=self.dev)
+        self.torch.distributed.all_reduce(t, op=self.torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            self.torch.distributed.destroy_process_group()
+
+
+def time_steps(ctx, step, steps, warmup, stream, sample_clocks=False):
+    """W untimed steps, then K steps bracketed by CUDA events on `stream`;
+    returns (per-step ms list, clock summary)."""
+    torch = ctx.torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    ctx.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(ctx.local) if sample_clocks else None
+    if clk:
+        clk.__enter__()
+    for a, b in ev:
+        a.record(stream)
+        step()
+        b.record(stream)
+    torch.cuda.synchronize()
+    if clk:
+        clk.__exit__()
+    ctx.barrier()
+    return [a.elapsed_time(b) for a, b in ev], (clk.summary() if clk else None)
+
+
+def run_aerial(args):
     import paper_2602_15036_gb300 as P
     from paper_2602_15036_gb300 import litho as L
-
-    world, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-
+    ctx = Ctx(args)
+    torch = ctx.torch
     clips = args.clips
     kern = P.litho_make_kernels(P.make_optics(**OPTICS), N, PIXEL, FOCUS, K)
     info = kern.info()
-    masks_np = np.stack([synth.manhattan_mask(N, seed=1234 + rank * clips + i) for i in range(clips)])
-    masks = torch.from_numpy(masks_np).to(dev)
+    k_eff = min(K, min(info["rank"]))
+    nc = 0
+    c = kern.crop
+    while nc < 2 * c:
+        nc = 32 if nc == 0 else 2 * nc
+    nc = nc if nc < N else 0
+    masks_np = np.stack([synth.manhattan_mask(N, seed=s) for s in clip_seeds(ctx.rank, clips)])
+    masks = torch.from_numpy(masks_np).to(ctx.dev)
     F = len(FOCUS)
-    img = torch.empty((clips, F, N, N), dtype=torch.float32, device=dev)
+    img = torch.empty((clips, F, N, N), dtype=torch.float32, device=ctx.dev)
     iblur = torch.empty_like(img)
-    printed = torch.empty((clips, F, N, N), dtype=torch.uint8, device=dev)
-    ws = torch.empty(P.litho_aerial_workspace_size(kern, clips, args.precision), dtype=torch.uint8, device=dev)
+    printed = torch.empty((clips, F, N, N), dtype=torch.uint8, device=ctx.dev)
+    paths = [args.precision] + [p for p in COMPARE if p != args.precision and not args.no_compare]
+    ws = torch.empty(max(P.litho_aerial_workspace_size(kern, clips, p) for p in paths), dtype=torch.uint8,
+                     device=ctx.dev)
     stream = torch.cuda.current_stream()
+    peaks, peak_src = _peaks()
+    results = {}
+    for i, prec in enumerate(paths):
+        def step():
+            P.litho_aerial(kern, masks, precision=prec, out=img, workspace=ws, stream=stream)
+            P.litho_resist(img, PIXEL, SIGMA_NM, THRESH, iblur=iblur, printed=printed, stream=stream)
 
-    def step():
-        P.litho_aerial(kern, masks, precision=args.precision, out=img, workspace=ws, stream=stream)
-        P.litho_resist(img, PIXEL, SIGMA_NM, THRESH, iblur=iblur, printed=printed, stream=stream)
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    L.litho_profile_enable(True)
-    L.litho_profile_reset()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for a, b in ev:
-            a.record(stream)
+        L.litho_profile_enable(True)
+        L.litho_profile_reset()
+        # warm-up steps are profiled too; reset again right before the timed ones
+        for _ in range(args.warmup):
             step()
-            b.record(stream)
         torch.cuda.synchronize()
-    barrier()
-    prof = L.litho_profile_read()
-    L.litho_profile_enable(False)
-    step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * clips * N * N * args.steps / (total_ms * 1e-3) / 1e6
+        L.litho_profile_reset()
+        step_ms, clk = time_steps(ctx, step, args.steps, 0, stream, sample_clocks=(i == 0))
+        prof = L.litho_profile_read()
+        L.litho_profile_enable(False)
+        total_ms = ctx.max_over_ranks(sum(step_ms))
+        value = whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total_ms * 1e-3])
+        models = stage_models(prec, clips, N, c, F, k_eff, nc, peaks)
+        roofs = rooflines(prof, args.steps, models)
+        results[prec] = dict(value=value, step_ms=step_ms, total_ms=total_ms, clocks=clk, prof=prof, roofs=roofs,
+                             launches=sum(v[1] for v in prof.values()))
 
+    head = results[args.precision]
     # end to end through the host-buffer C-ABI call: pinned masks in, printed bytes out
     mask_host = torch.from_numpy(masks_np).pin_memory()
     printed_host = torch.empty((clips, F, N, N), dtype=torch.uint8).pin_memory()
     del ws
     ws_host = torch.empty(P.litho_aerial_host_workspace_size(kern, clips, args.precision), dtype=torch.uint8,
-                          device=dev)
+                          device=ctx.dev)
 
     def e2e_step():
         P.litho_aerial_host(kern, mask_host, ws_host, printed_host=printed_host, precision=args.precision,
                             sigma_nm=SIGMA_NM, threshold=THRESH, stream=stream)
 
     e2e_step()
-    barrier()
-    t0 = time.perf_counter()
+    ctx.barrier()
     e2e_steps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
-    e2e_s = time.perf_counter() - t0
-    barrier()
-    e2e_val = world * clips * N * N * e2e_steps / e2e_s / 1e6
+    e2e_s = ctx.max_over_ranks(time.perf_counter() - t0)
+    ctx.barrier()
+    e2e_val = whole_job_rate(clips * N * N * e2e_steps / 1e6, ctx.world, [e2e_s])
 
-    peaks, peak_src = _peaks()
-    # dominant kernel: the stage-2 FFT (inverse transform over u + fused lam |E|^2), one launch per clip
-    s2 = prof.get("stage2_fft")
-    roof = None
-    if s2:
-        ms, launches = s2
-        rank_eff = [min(K, r) for r in info["rank"]]
-        flops = sum(rank_eff) * N * (5.0 * N * np.log2(N) + 4.0 * N)   # per launch (one clip, all planes)
-        achieved = flops / (ms / launches * 1e-3) / 1e12
-        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_stage2<2048>",
-                "note": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 x 2070 MHz; algorithmic flops "
-                        "5 N log2 N + 4 N per row transform, rows = N per kernel and plane"}
-    launches_total = sum(v[1] for v in prof.values())
-    line = {"metric": METRIC, "value": value, "unit": "Mpx/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+    dominant = max(head["roofs"].items(), key=lambda kv: kv[1]["ms_per_step"])
+    roof = dict(dominant[1])
+    roof["kernel"] = dominant[0]
+    roof["traffic"] = None
+    plain = results.get("fft32")
+    line = {"metric": METRIC, "value": head["value"], "unit": "Mpx/s", "n_gpus": ctx.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "clips_per_gpu": clips, "precision": args.precision,
-                       "parallelism": f"replicas x{world} (clips sharded, no collective)",
-                       "l2": "inputs larger than L2 (1.07 GB masks, 3.2 GB images per step)"},
-            "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
-            "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
-            "gpu_launches": launches_total,
+                       "error_bound_abs": ERROR_BOUND.get(args.precision),
+                       "parallelism": f"replicas x{ctx.world} (clips sharded, no collective)",
+                       "l2": "inputs larger than L2 (1.07 GB masks, 3.2 GB images per step); no flush"},
+            "p50_ms": statistics.median(head["step_ms"]), "p99_ms": float(np.percentile(head["step_ms"], 99)),
+            "vs_plain_fft": (head["value"] / plain["value"]) if plain else None,
+            "paths": {p: {"value": r["value"], "ms_per_step": r["total_ms"] / args.steps,
+                          "error_bound_abs": ERROR_BOUND.get(p),
+                          "stages_ms_per_step": {k: v[0] / args.steps for k, v in r["prof"].items()},
+                          "roofline": r["roofs"]} for p, r in results.items()},
+            "gpu_launches": head["launches"],
+            "gpu_launches_per_step": head["launches"] / args.steps,
             "e2e": {"value": e2e_val, "unit": "Mpx/s", "h2d_bytes_per_step": int(mask_host.numel() * 4),
                     "d2h_bytes_per_step": int(printed_host.numel())},
-            "roofline": roof, "peaks_source": peak_src, "clocks": clk.summary()}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            "roofline": roof, "peaks_source": peak_src, "clocks": head["clocks"]}
+    if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-    if rank == 0:
+    if ctx.rank == 0:
         print(json.dumps(line), flush=True)
-    if world > 1:
-        torch.distributed.destroy_process_group()
+    ctx.close()
+
+
+def run_ilt(args):
+    """16 clips of 1024^2, annular 21x21, K=16, 5 focus planes; one step = litho_ilt_grad on all clips
+    plus the gradient-descent update theta -= 0.5 g / max|g| (torch, outside the library)."""
+    import paper_2602_15036_gb300 as P
+    from paper_2602_15036_gb300 import litho as L
+    ctx = Ctx(args)
+    torch = ctx.torch
+    n, pixel, k, focus, clips = 1024, 8.0, 16, [-60.0, -30.0, 0.0, 30.0, 60.0], 16
+    optics = dict(wavelength_nm=193.0, na=1.35, n_medium=1.44, kind="annular", src_grid=21, sigma_in=0.6,
+                  sigma_out=0.9)
+    kern = P.litho_make_kernels(P.make_optics(**optics), n, pixel, focus, k)
+    data = [synth.ilt_clip(n, pixel, seed=s) for s in clip_seeds(ctx.rank, clips, base=4000)]
+    theta = torch.from_numpy(np.stack([d[0] for d in data])).to(ctx.dev)
+    target = torch.from_numpy(np.stack([d[1] for d in data])).to(ctx.dev)
+    grad = torch.empty_like(theta)
+    ws = torch.empty(P.litho_ilt_workspace_size(kern, clips)[0], dtype=torch.uint8, device=ctx.dev)
+    stream = torch.cuda.current_stream()
+    losses = []
+
+    def step():
+        _, loss = P.litho_ilt_grad(kern, theta, target, grad=grad, workspace=ws, want_loss=True, stream=stream)
+        losses.append(float(loss.sum()))
+        theta.sub_(0.5 * grad / grad.abs().amax(dim=(1, 2), keepdim=True).clamp_min(1e-30))
+
+    L.litho_profile_enable(True)
+    L.litho_profile_reset()
+    step_ms, clk = time_steps(ctx, step, args.steps, args.warmup, stream, sample_clocks=True)
+    prof = L.litho_profile_read()
+    L.litho_profile_enable(False)
+    total = ctx.max_over_ranks(sum(step_ms))
+    line = {"metric": "ILT gradient Mpx/s (1024² clips, K=16, 5 focus)", "workload": "ilt",
+            "value": whole_job_rate(clips * n * n * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
+            "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "ilt 16x1024^2@8nm annular21 K=16 focus(-60..60 step 30)", "clips_per_gpu": clips},
+            "loss_first_last": [losses[0], losses[-1]],
+            "stages_ms_per_step": {kk: v[0] / (args.steps + args.warmup) for kk, v in prof.items()},
+            "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_serve(args):
+    """Poisson stream of mixed requests through litho_serve (sizes 256..2048, DUV and EUV optics,
+    K in {8,16,24}, half images and half ILT steps) at 80 % of the measured saturated rate."""
+    from paper_2602_15036_gb300 import litho as L
+    ctx = Ctx(args)
+    duv = dict(wavelength_nm=193.0, na=1.35, n_medium=1.44, kind="annular", src_grid=21, sigma_in=0.6,
+               sigma_out=0.9)
+    euv = dict(wavelength_nm=13.5, na=0.33, n_medium=1.0, kind="annular", src_grid=21, sigma_in=0.6, sigma_out=0.9)
+    st = synth.Stream(77)
+    total = args.requests
+    sizes = [256, 512, 1024, 2048]
+    pool = {n: [(np.ascontiguousarray(synth.random_rect_mask(n, seed=10 * n + i, count=n // 4)),) +
+                tuple(np.ascontiguousarray(a) for a in synth.ilt_clip(n, 8.0, seed=20 * n + i)) for i in range(2)]
+            for n in sizes}
+    reqs = []
+    for i in range(total):
+        n = sizes[int(st.integers(0, 3, 1)[0])]
+        is_euv = bool(st.integers(0, 1, 1)[0])
+        k = [8, 16, 24][int(st.integers(0, 2, 1)[0])]
+        kind = "image" if st.integers(0, 1, 1)[0] == 0 else "ilt"
+        reqs.append((kind, euv if is_euv else duv, n, 1.0 if is_euv else 8.0, k, pool[n][i % 2]))
+    srv = L.Server(64 << 30, max_slots=8, max_queue=total + 16)
+    outs = {}
+
+    def submit(r):
+        kind, opt, n, pixel, k, (mask, theta, tgt) = r
+        out = np.empty((n, n), dtype=np.float32)
+        inp = mask if kind == "image" else theta
+        t, _ = srv.submit(kind, L.make_optics(**opt), n, pixel, 0.0, k, inp, out,
+                          target_host=tgt if kind == "ilt" else None, precision="fft32/coarse")
+        outs[t] = out
+        return t
+
+    statuses, first_err = {}, []
+
+    def drain(tickets):
+        for t in tickets:
+            st_ = srv.poll(t, 1000)
+            while st_ == L.ETIMEOUT:
+                st_ = srv.poll(t, 1000)
+            name = L.STATUS_NAMES[st_]
+            statuses[name] = statuses.get(name, 0) + 1
+            if st_ != L.OK and not first_err:
+                first_err.append(L.litho_last_error())
+
+    # warm the kernel-set cache: one request per (optics, n, k) key, untimed
+    keys = {}
+    for r in reqs:
+        keys.setdefault((r[1]["wavelength_nm"], r[2], r[4]), r)
+    drain([submit(r) for r in keys.values()])
+    # saturated throughput: a burst of 256 requests
+    burst = reqs[:256]
+    t0 = time.perf_counter()
+    drain([submit(r) for r in burst])
+    sat_rps = len(burst) / (time.perf_counter() - t0)
+    srv.close()
+    srv = L.Server(64 << 30, max_slots=8, max_queue=total + 16)
+    drain([submit(r) for r in keys.values()])
+    rate = 0.8 * sat_rps
+    arrivals = np.cumsum(-np.log(1.0 - synth.Stream(78).uniform(total)) / rate)
+    tickets = []
+    t0 = time.perf_counter()
+    for r, ta in zip(reqs, arrivals):
+        now = time.perf_counter() - t0
+        if ta > now:
+            time.sleep(ta - now)
+        tickets.append(submit(r))
+    drain(tickets)
+    wall = time.perf_counter() - t0
+    s = srv.stats()
+    srv.close()
+    px = sum(r[2] * r[2] for r in reqs)
+    line = {"metric": "serving p50/p99 latency and Mpx/s (Poisson, mixed sizes/optics/K, image+ILT)",
+            "workload": "serve", "value": px / wall / 1e6, "unit": "Mpx/s", "n_gpus": ctx.world,
+            "requests": total, "arrival_rate_rps": rate, "saturated_rps": sat_rps,
+            "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic", "config": {"precision": "fft32/coarse (images), fft32 (ILT)", "slots": 8},
+            "stats": {k: s[k] for k in ("submitted", "completed", "rejected", "cancelled", "hbm_high_water",
+                                         "kernel_sets_cached")},
+            "status_counts": statuses, "first_error": first_err[0] if first_err else None}
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 def main():
@@ -287,14 +518,22 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fft32", "bf16", "bf16x3", "fp16x3", "fp16", "fft32/coarse", "fp16x3/coarse", "fp16/coarse", "bf16x3/coarse"], default="fft32")
+    ap.add_argument("--workload", choices=["aerial", "ilt", "serve"], default="aerial")
+    ap.add_argument("--precision", default=HEADLINE,
+                    choices=sorted(ERROR_BOUND) + ["bf16/coarse"])
     ap.add_argument("--clips", type=int, default=64)
+    ap.add_argument("--requests", type=int, default=4096)
+    ap.add_argument("--no-compare", action="store_true", help="time only --precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "ilt":
+        run_ilt(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
-        run_ours(args)
+        run_aerial(args)
 
 
 if __name__ == "__main__":

@@ -14,6 +14,7 @@
 //   img     [plane][N][N] f32
 #include "fft_common.cuh"
 #include "litho_internal.h"
+#include "stage1.cuh"
 
 namespace litho {
 
@@ -54,11 +55,6 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_mask_rows(const float* __restri
   }
 }
 
-// Columns per CTA for the column kernels: W transforms of NT threads each.
-template <int N> struct ColW { static constexpr int W = (N >= 2048) ? 8 : (N >= 512 ? 16 : 32); };
-// Column stride in shared memory: the padded length plus one, so that the
-// cooperative loads across columns (w fastest) fall into different banks.
-template <int N> struct ColLD { static constexpr int value = PadLen<N>::value + 1; };
 
 // ---- mask spectrum, pass 2: column DFTs of the crop columns, crop rows kept ------------------
 template <int N>
@@ -89,41 +85,21 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const fl
   }
 }
 
-// ---- stage 1: band multiply + inverse transform over v, for every kernel j ----------------------
-template <int N>
-__global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_stage1(const float2* __restrict__ mhat,
-                                                                      const float2* __restrict__ phi, int crop,
-                                                                      const float2* __restrict__ tw_g,
-                                                                      float2* __restrict__ t1) {
-  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
-  extern __shared__ float2 smem[];
-  float2* tw = smem;
-  float2* buf = smem + N;
-  load_twiddles<N>(tw, tw_g);
-  const int j = blockIdx.y, u0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
-  for (int i = tid; i < W * LD; i += blockDim.x) buf[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  // with kernels: one spectrum times kernel j; without: spectrum j itself
-  const float2* ph = phi + (size_t)j * crop * crop + u0;
-  const float2* mh = mhat + (phi ? 0 : (size_t)j * crop * crop) + u0;
-  for (int i = tid; i < crop * W; i += blockDim.x) {
-    const int cv = i / W, w = i % W;
-    const int idx = (cv - half + N) % N;
-    const float2 a = __ldg(mh + (size_t)cv * crop + w);
-    buf[w * LD + pad16(idx)] = phi ? cmul(a, __ldg(ph + (size_t)cv * crop + w)) : a;
+// ---- stage 1: band multiply + inverse transform over v (stage1.cuh), FP32 output ------------------
+struct OutC64 {
+  static constexpr bool kRowWise = false;
+  float2* t1;
+  int n, crop;
+  __device__ __forceinline__ void store(int j, int y, int c, float2 v) const {
+    t1[((size_t)j * n + y) * crop + c] = v;
   }
-  __syncthreads();
-  fft_smem<N, +1>(buf + (tid / NT) * LD, tw, tid % NT);
-  float2* dst = t1 + (size_t)j * N * crop + u0;
-  for (int i = tid; i < N * W; i += blockDim.x) {
-    const int y = i / W, w = i % W;
-    dst[(size_t)y * crop + w] = buf[w * LD + pad16(y)];
-  }
-}
+  template <int W>
+  __device__ void store_row(int, int, int, const float2 (&)[W]) const {}
+};
 
 // ---- stage 2 (FP32 path): one image row per CTA, all kernels of the plane ------------------------
 template <int N>
-__global__ void __launch_bounds__(Plan<N>::NT, 4) k_stage2(const float2* __restrict__ t1, const float* __restrict__ lam,
+__global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const float2* __restrict__ t1, const float* __restrict__ lam,
                                                         int nk, int crop, float dose,
                                                         const float2* __restrict__ tw_g, float* __restrict__ img,
                                                         long long t1_plane, long long img_plane, int lam_plane) {
@@ -202,11 +178,11 @@ template <int N>
 cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, float2* rowbuf, float2* mhat,
                             cudaStream_t st) {
   const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
-  cudaError_t e = cudaFuncSetAttribute(k_mask_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smr);
+  cudaError_t e = smem_attrs(k_mask_rows<N>, smr);
   if (e != cudaSuccess) return e;
   k_mask_rows<N><<<dim3(N / 2, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf);
   const size_t sm = col_smem_bytes<N>();
-  e = cudaFuncSetAttribute(k_mask_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  e = smem_attrs(k_mask_cols<N>, sm);
   if (e != cudaSuccess) return e;
   k_mask_cols<N><<<dim3(crop / ColW<N>::W, b), Plan<N>::NT * ColW<N>::W, sm, st>>>(rowbuf, crop, tw, mhat);
   return cudaGetLastError();
@@ -215,11 +191,7 @@ cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, f
 template <int N>
 cudaError_t stage1_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, float2* t1,
                      cudaStream_t st) {
-  const size_t sm = col_smem_bytes<N>();
-  cudaError_t e = cudaFuncSetAttribute(k_stage1<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_stage1<N><<<dim3(crop / ColW<N>::W, nk), Plan<N>::NT * ColW<N>::W, sm, st>>>(mhat, phi, crop, tw, t1);
-  return cudaGetLastError();
+  return launch_stage1_cols<N>(mhat, phi, nk, crop, tw, OutC64{t1, N, crop}, st);
 }
 
 template <int N>

@@ -227,6 +227,43 @@ __device__ __forceinline__ void fft_smem(float2* buf, const float2* tw, int t) {
   }
 }
 
+// Full transform with the first pass from `load` and every pass's output in
+// shared memory (padded layout, natural order on return).  Ends with a barrier.
+template <int N, int SIGN, class Load>
+__device__ __forceinline__ void fft_load_smem(float2* buf, const float2* tw, int t, Load& load) {
+  using PL = Plan<N>;
+  constexpr int NT = PL::NT;
+  SmemLoadUnused none;
+  pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false>(buf, tw, t, load);
+  if constexpr (PL::P == 2) {
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
+  } else {
+    pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
+    pass_to_smem<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, TwOff<N>::p2, true>(buf, tw, t, none);
+  }
+}
+
+// Columns per CTA for the column-transform kernels (W transforms of
+// Plan<N>::NT threads each): small CTAs so that several share an SM.
+template <int N> struct ColW { static constexpr int W = N >= 512 ? 4 : 8; };
+// Column stride in shared memory: the padded length rounded up to 16 complex
+// values plus 16/W, so that a half-warp of the cooperative copies (w fastest,
+// W columns x 16/W rows) touches 16 different 8-byte bank pairs.
+template <int N> struct ColLD {
+  static constexpr int value = (PadLen<N>::value + 15) / 16 * 16 + 16 / ColW<N>::W;
+};
+// Stride of the compact band buffers [W][crop] (crop is a multiple of 32).
+template <int N>
+__host__ __device__ __forceinline__ int band_ld(int crop) { return crop + 16 / ColW<N>::W; }
+
+// Prefer the largest shared-memory carveout for a kernel that uses a lot of it.
+template <class K>
+inline cudaError_t smem_attrs(K kernel, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+}
+
 // Stage the twiddle table (N entries, see above) into shared memory.
 template <int N>
 __device__ __forceinline__ void load_twiddles(float2* s_tw, const float2* __restrict__ g_tw) {

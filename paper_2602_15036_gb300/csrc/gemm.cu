@@ -42,6 +42,7 @@
 
 #include "fft_common.cuh"
 #include "gemm.h"
+#include "stage1.cuh"
 
 namespace litho {
 
@@ -366,66 +367,67 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---- stage 1 for the GEMM path: band multiply + inverse transform over v, written as split 16-bit A ---
+// 16-bit bit patterns of the hi part and the rounded remainder (lo; 0 for the
+// one-product modes).  fp16 values are scaled by the kernel's power of two.
 template <int MODE>
-__device__ __forceinline__ void split_store(float x, float scale, void* hi, void* lo, size_t idx) {
+__device__ __forceinline__ void split16(float x, float scale, uint32_t& h, uint32_t& l) {
   if (MODE == kFP16X3 || MODE == kFP16) {
     const float xs = x * scale;
-    const __half h = __float2half_rn(xs);
-    static_cast<__half*>(hi)[idx] = h;
-    if (MODE == kFP16X3) static_cast<__half*>(lo)[idx] = __float2half_rn(xs - __half2float(h));
+    const __half hh = __float2half_rn(xs);
+    h = __half_as_ushort(hh);
+    l = MODE == kFP16X3 ? __half_as_ushort(__float2half_rn(xs - __half2float(hh))) : 0u;
   } else {
-    const __nv_bfloat16 h = __float2bfloat16_rn(x);
-    static_cast<__nv_bfloat16*>(hi)[idx] = h;
-    if (MODE == kBF16X3) static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+    const __nv_bfloat16 hh = __float2bfloat16_rn(x);
+    h = __bfloat16_as_ushort(hh);
+    l = MODE == kBF16X3 ? __bfloat16_as_ushort(__float2bfloat16_rn(x - __bfloat162float(hh))) : 0u;
   }
 }
 
-template <int N> struct S1W { static constexpr int W = (N >= 2048) ? 8 : (N >= 512 ? 16 : 32); };
-
-template <int N, int MODE>
-__global__ void __launch_bounds__(Plan<N>::NT * S1W<N>::W) k_stage1_split(const float2* __restrict__ mhat,
-                                                                           const float2* __restrict__ phi, int crop,
-                                                                           const float2* __restrict__ tw_g,
-                                                                           const float* __restrict__ scales,
-                                                                           void* a_hi, void* a_lo) {
-  constexpr int W = S1W<N>::W, NT = Plan<N>::NT, LD = PadLen<N>::value + 1;
-  extern __shared__ float2 smem1[];
-  float2* tw = smem1;
-  float2* buf = smem1 + N;
-  load_twiddles<N>(tw, tw_g);
-  const int j = blockIdx.y, u0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
-  for (int i = tid; i < W * LD; i += blockDim.x) buf[i] = make_float2(0.f, 0.f);
-  __syncthreads();
-  const float2* ph = phi + (size_t)j * crop * crop + u0;
-  const float2* mh = mhat + u0;
-  for (int i = tid; i < crop * W; i += blockDim.x) {
-    const int cv = i / W, w = i % W;
-    const int idx = (cv - half + N) % N;
-    buf[w * LD + pad16(idx)] = cmul(__ldg(mh + (size_t)cv * crop + w), __ldg(ph + (size_t)cv * crop + w));
+// Split 16-bit output of stage 1: row (j, y) of the A operand, chunked
+// [Re 32 | Im 32].  W consecutive columns (W a multiple of 4 dividing 32)
+// are packed into 8-byte stores per part.
+template <int MODE>
+struct OutSplit {
+  static constexpr bool kRowWise = true;
+  __device__ void store(int, int, int, float2) const {}
+  void* hi;
+  void* lo;
+  const float* scales;
+  int n, crop;
+  template <int W>
+  __device__ __forceinline__ void store_row(int j, int y, int c0, const float2 (&v)[W]) const {
+    static_assert(W % 4 == 0 && CH % W == 0, "column block");
+    const size_t o = ((size_t)j * n + y) * (size_t)(2 * crop) + (size_t)(c0 / CH) * KE + (c0 % CH);
+    const float s = scales[j];
+    uint32_t rh[W], rl[W], ih[W], il[W];
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      split16<MODE>(v[w].x, s, rh[w], rl[w]);
+      split16<MODE>(v[w].y, s, ih[w], il[w]);
+    }
+    uint2* hr = reinterpret_cast<uint2*>(static_cast<uint16_t*>(hi) + o);
+    uint2* hm = reinterpret_cast<uint2*>(static_cast<uint16_t*>(hi) + o + CH);
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      hr[q] = make_uint2(rh[4 * q] | (rh[4 * q + 1] << 16), rh[4 * q + 2] | (rh[4 * q + 3] << 16));
+      hm[q] = make_uint2(ih[4 * q] | (ih[4 * q + 1] << 16), ih[4 * q + 2] | (ih[4 * q + 3] << 16));
+    }
+    if (MODE == kFP16X3 || MODE == kBF16X3) {
+      uint2* lr = reinterpret_cast<uint2*>(static_cast<uint16_t*>(lo) + o);
+      uint2* lm = reinterpret_cast<uint2*>(static_cast<uint16_t*>(lo) + o + CH);
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        lr[q] = make_uint2(rl[4 * q] | (rl[4 * q + 1] << 16), rl[4 * q + 2] | (rl[4 * q + 3] << 16));
+        lm[q] = make_uint2(il[4 * q] | (il[4 * q + 1] << 16), il[4 * q + 2] | (il[4 * q + 3] << 16));
+      }
+    }
   }
-  __syncthreads();
-  fft_smem<N, +1>(buf + (tid / NT) * LD, tw, tid % NT);
-  const float scale = scales[j];
-  const size_t row0 = (size_t)j * N;
-  for (int i = tid; i < N * W; i += blockDim.x) {
-    const int y = i / W, w = i % W, c = u0 + w;
-    const float2 v = buf[w * LD + pad16(y)];
-    const size_t kr = (size_t)(c / CH) * KE + (c % CH);
-    const size_t o = (row0 + y) * (size_t)(2 * crop) + kr;
-    split_store<MODE>(v.x, scale, a_hi, a_lo, o);
-    split_store<MODE>(v.y, scale, a_hi, a_lo, o + CH);
-  }
-}
+};
 
 template <int N, int MODE>
 cudaError_t stage1_split_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
                            const float* scales, void* a_hi, void* a_lo, cudaStream_t st) {
-  constexpr int W = S1W<N>::W;
-  const size_t sm = sizeof(float2) * (N + W * (PadLen<N>::value + 1));
-  cudaError_t e = cudaFuncSetAttribute(k_stage1_split<N, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_stage1_split<N, MODE><<<dim3(crop / W, nk), Plan<N>::NT * W, sm, st>>>(mhat, phi, crop, tw, scales, a_hi, a_lo);
-  return cudaGetLastError();
+  return launch_stage1_cols<N>(mhat, phi, nk, crop, tw, OutSplit<MODE>{a_hi, a_lo, scales, N, crop}, st);
 }
 
 template <int MODE>

@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restri
   }
 }
 
-template <int N> struct AdjW { static constexpr int W = (N >= 2048) ? 8 : (N >= 512 ? 16 : 32); };
+template <int N> struct AdjW { static constexpr int W = ColW<N>::W; };
 
 // Backward columns: forward FFT over y of U_j[:, c], crop rows, times lam_j conj(Phi_j).
 template <int N>
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
                                                                         const float* __restrict__ lam, int crop,
                                                                         const float2* __restrict__ tw_g,
                                                                         float2* __restrict__ sk) {
-  constexpr int W = AdjW<N>::W, NT = Plan<N>::NT, LD = PadLen<N>::value + 1;
+  constexpr int W = AdjW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
@@ -217,8 +217,8 @@ template <int N>
 cudaError_t adj_cols_n(const float2* u, const float2* phi, const float* lam, int crop, const float2* tw, float2* sk,
                        int planes, cudaStream_t st) {
   constexpr int W = AdjW<N>::W;
-  const size_t sm = sizeof(float2) * (N + W * (PadLen<N>::value + 1));
-  cudaError_t e = cudaFuncSetAttribute(k_adj_cols<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const size_t sm = sizeof(float2) * (N + W * ColLD<N>::value);
+  cudaError_t e = smem_attrs(k_adj_cols<N>, sm);
   if (e != cudaSuccess) return e;
   k_adj_cols<N><<<dim3(crop / W, planes), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, sk);
   return cudaGetLastError();

@@ -1,0 +1,113 @@
+// Stage 1 of the SOCS evaluation (paper Eq. (4)): band multiply and inverse
+// transform over the y frequency, T_j[y][c] = sum_v mhat[v][c] Phi_j[v][c] e^{+2 pi i v y/N},
+// for a block of W crop columns c and a run of kernels j.
+//
+// A CTA keeps its column block of the mask spectrum and the twiddle table in
+// shared memory and loops over JB kernels; the next kernel's Phi block is
+// copied in with cp.async (two buffers) while the current block's W column
+// transforms run, and the band multiply happens inside the first pass's load.
+// Without kernels (phi == NULL) each j transforms its own spectrum mhat[j].
+// The output policy `Out` stores element (j, y, c): FP32 complex for the FFT
+// path, split 16-bit hi/lo rows for the tensor-core path.
+#pragma once
+
+#include "fft_common.cuh"
+
+namespace litho {
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Shared memory of k_stage1_cols in float2 units.
+template <int N>
+inline size_t stage1_smem_elems(int crop) {
+  return size_t(N) + size_t(ColW<N>::W) * ColLD<N>::value + 3 * size_t(ColW<N>::W) * band_ld<N>(crop);
+}
+
+template <int N, class Out>
+__global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W)
+    k_stage1_cols(const float2* __restrict__ mhat, const float2* __restrict__ phi, int crop, int nk, int jb,
+                  const float2* __restrict__ tw_g, Out out) {
+  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value, T = W * NT;
+  extern __shared__ float2 smem[];
+  const int bld = band_ld<N>(crop);
+  float2* tw = smem;
+  float2* buf = smem + N;
+  float2* const blk0 = buf + W * LD;  // Phi (or spectrum) blocks, double-buffered: blk0 + s W bld
+  auto blk = [&](int s) { return blk0 + s * W * bld; };
+  float2* msk = buf + W * LD + 2 * W * bld;                 // mask-spectrum block (with kernels)
+  const int tid = threadIdx.x, u0 = blockIdx.x * W, half = crop / 2;
+  const int j0 = blockIdx.y * jb, j1 = min(nk, j0 + jb);
+  if (j0 >= j1) return;
+  load_twiddles<N>(tw, tw_g);
+  const float2* src_base = phi ? phi : mhat;  // the per-j operand
+  auto issue = [&](int j, float2* dst) {
+    const float2* src = src_base + (size_t)j * crop * crop + u0;
+    for (int i = tid; i < crop * W; i += T) {
+      const int cv = i / W, w = i % W;
+      cp_async8(dst + w * bld + cv, src + (size_t)cv * crop + w);
+    }
+    cp_async_commit();
+  };
+  if (phi) {
+    for (int i = tid; i < crop * W; i += T) {
+      const int cv = i / W, w = i % W;
+      msk[w * bld + cv] = __ldg(mhat + (size_t)cv * crop + u0 + w);
+    }
+  }
+  issue(j0, blk(0));
+  const int g = tid / NT, t = tid % NT;
+  for (int j = j0; j < j1; ++j) {
+    const int s = (j - j0) & 1;
+    if (j + 1 < j1) {
+      issue(j + 1, blk(s ^ 1));
+      cp_async_wait_one();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();  // block j (and, first time round, msk and tw) visible to all threads
+    const float2* b = blk(s) + g * bld;
+    const float2* m = msk + g * bld;
+    auto load = [&](int idx) {
+      const int c = (idx < N / 2 ? idx : idx - N) + half;
+      if (c < 0 || c >= crop) return make_float2(0.f, 0.f);
+      return phi ? cmul(m[c], b[c]) : b[c];
+    };
+    fft_load_smem<N, +1>(buf + g * LD, tw, t, load);
+    if constexpr (Out::kRowWise) {
+      // one thread per output row writes the block's W consecutive columns
+      for (int y = tid; y < N; y += T) {
+        float2 v[W];
+#pragma unroll
+        for (int w = 0; w < W; ++w) v[w] = buf[w * LD + pad16(y)];
+        out.template store_row<W>(j, y, u0, v);
+      }
+    } else {
+      // consecutive threads write consecutive columns of a row (full sectors per warp)
+      for (int i = tid; i < N * W; i += T) {
+        const int y = i / W, w = i % W;
+        out.store(j, y, u0 + w, buf[w * LD + pad16(y)]);
+      }
+    }
+    __syncthreads();  // copy-out done before the next transform overwrites buf
+  }
+}
+
+template <int N, class Out>
+cudaError_t launch_stage1_cols(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, Out out,
+                               cudaStream_t st) {
+  constexpr int W = ColW<N>::W, JB = 8;
+  const size_t sm = sizeof(float2) * stage1_smem_elems<N>(crop);
+  cudaError_t e = smem_attrs(k_stage1_cols<N, Out>, sm);
+  if (e != cudaSuccess) return e;
+  k_stage1_cols<N, Out><<<dim3(crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(mhat, phi, crop, nk, JB,
+                                                                                          tw, out);
+  return cudaGetLastError();
+}
+
+}  // namespace litho

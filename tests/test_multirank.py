@@ -1,0 +1,61 @@
+"""The benchmark's multi-rank host logic on CPU with torch.distributed (gloo,
+world size 2): disjoint clip shards per rank and the whole-job rate taken
+over the slowest rank (the path shards by clip with no data exchange, so the
+only collective is the timing reduction)."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    seeds = bench.clip_seeds(rank, 8)
+    my_time = 1.0 + rank          # rank 1 is the slow one
+    t = torch.tensor([my_time])
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    gathered = [None] * world
+    dist.all_gather_object(gathered, seeds)
+    rate = bench.whole_job_rate(8.0, world, [float(t.item())])
+    q.put((rank, gathered, rate))
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_and_reduce():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, gathered, rate in out:
+        a, b = gathered
+        assert not set(a) & set(b) and len(a) == len(b) == 8
+        assert rate == pytest.approx(16.0 / 2.0)   # 2 x 8 units over the slower rank's 2 s
+
+
+def test_stage_models_are_consistent():
+    peaks = {"hbm_gbs": 6785.5, "bf16_tflops_sustained": 1709.2}
+    m = bench.stage_models("fp16x3/coarse", 64, 2048, 448, 3, 24, 1024, peaks)
+    # 8 N'^2 C flops per kernel and plane, three products for the split operands
+    assert m["stage2_gemm"][1] == pytest.approx(64 * 3 * 24 * 8.0 * 1024 ** 2 * 448 * 3)
+    assert m["resist"][0] == "hbm" and "upsample" in m
+    m2 = bench.stage_models("fft32", 64, 2048, 448, 3, 24, 1024, peaks)
+    assert "upsample" not in m2
