@@ -438,8 +438,17 @@ def run_serve(args):
     st = synth.Stream(77)
     total = args.requests
     sizes = [256, 512, 1024, 2048]
-    pool = {n: [(np.ascontiguousarray(synth.random_rect_mask(n, seed=10 * n + i, count=n // 4)),) +
-                tuple(np.ascontiguousarray(a) for a in synth.ilt_clip(n, 8.0, seed=20 * n + i)) for i in range(2)]
+    import torch
+    keep = []
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+        keep.append(t)
+        return t.numpy()
+
+    # page-locked request buffers: the server DMAs them directly (no staging copy)
+    pool = {n: [(pinned(synth.random_rect_mask(n, seed=10 * n + i, count=n // 4)),) +
+                tuple(pinned(a) for a in synth.ilt_clip(n, 8.0, seed=20 * n + i)) for i in range(2)]
             for n in sizes}
     reqs = []
     for i in range(total):
@@ -451,9 +460,14 @@ def run_serve(args):
     srv = L.Server(64 << 30, max_slots=8, max_queue=total + 16)
     outs = {}
 
-    def submit(r):
+    out_bufs = {}
+
+    def submit(r, idx=None):
         kind, opt, n, pixel, k, (mask, theta, tgt) = r
-        out = np.empty((n, n), dtype=np.float32)
+        key = (idx, n) if idx is not None else ("warm", n)
+        if key not in out_bufs:
+            out_bufs[key] = pinned(np.empty((n, n), dtype=np.float32))
+        out = out_bufs[key]
         inp = mask if kind == "image" else theta
         t, _ = srv.submit(kind, L.make_optics(**opt), n, pixel, 0.0, k, inp, out,
                           target_host=tgt if kind == "ilt" else None, precision="fft32/coarse")
@@ -479,30 +493,38 @@ def run_serve(args):
     drain([submit(r) for r in keys.values()])
     # saturated throughput: a burst of 256 requests
     burst = reqs[:256]
+    for i, r in enumerate(reqs):      # one output buffer per request, allocated before any timing
+        out_bufs.setdefault((i, r[2]), pinned(np.empty((r[2], r[2]), dtype=np.float32)))
     t0 = time.perf_counter()
-    drain([submit(r) for r in burst])
+    drain([submit(r, i) for i, r in enumerate(burst)])
     sat_rps = len(burst) / (time.perf_counter() - t0)
     srv.close()
-    srv = L.Server(64 << 30, max_slots=8, max_queue=total + 16)
-    drain([submit(r) for r in keys.values()])
-    rate = 0.8 * sat_rps
-    arrivals = np.cumsum(-np.log(1.0 - synth.Stream(78).uniform(total)) / rate)
-    tickets = []
-    t0 = time.perf_counter()
-    for r, ta in zip(reqs, arrivals):
-        now = time.perf_counter() - t0
-        if ta > now:
-            time.sleep(ta - now)
-        tickets.append(submit(r))
-    drain(tickets)
-    wall = time.perf_counter() - t0
-    s = srv.stats()
-    srv.close()
     px = sum(r[2] * r[2] for r in reqs)
+    sweep = {}
+    for load in (0.5, 0.8):
+        srv = L.Server(64 << 30, max_slots=8, max_queue=total + 16)
+        drain([submit(r) for r in keys.values()])
+        srv.stats_reset()          # latencies of the timed stream only (not the kernel-set warm-up)
+        rate = load * sat_rps
+        arrivals = np.cumsum(-np.log(1.0 - synth.Stream(78).uniform(total)) / rate)
+        tickets = []
+        t0 = time.perf_counter()
+        for i, (r, ta) in enumerate(zip(reqs, arrivals)):
+            now = time.perf_counter() - t0
+            if ta > now:
+                time.sleep(ta - now)
+            tickets.append(submit(r, i))
+        drain(tickets)
+        wall = time.perf_counter() - t0
+        s = srv.stats()
+        srv.close()
+        sweep[load] = {"arrival_rate_rps": rate, "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
+                       "mpx_per_s": px / wall / 1e6}
     line = {"metric": "serving p50/p99 latency and Mpx/s (Poisson, mixed sizes/optics/K, image+ILT)",
-            "workload": "serve", "value": px / wall / 1e6, "unit": "Mpx/s", "n_gpus": ctx.world,
-            "requests": total, "arrival_rate_rps": rate, "saturated_rps": sat_rps,
-            "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "higher_is_better": True, "dtype": "f32",
+            "workload": "serve", "value": sweep[0.8]["mpx_per_s"], "unit": "Mpx/s", "n_gpus": ctx.world,
+            "requests": total, "arrival_rate_rps": sweep[0.8]["arrival_rate_rps"], "saturated_rps": sat_rps,
+            "p50_ms": sweep[0.8]["p50_ms"], "p99_ms": sweep[0.8]["p99_ms"], "load_sweep": sweep,
+            "higher_is_better": True, "dtype": "f32",
             "data": "synthetic", "config": {"precision": "fft32/coarse (images), fft32 (ILT)", "slots": 8},
             "stats": {k: s[k] for k in ("submitted", "completed", "rejected", "cancelled", "hbm_high_water",
                                          "kernel_sets_cached")},

@@ -155,6 +155,15 @@ litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, 
  * leaving its output incomplete).  Clears the flag.  LITHO_OK otherwise. */
 litho_status litho_check_device(const litho_kernels* h, void* stream);
 
+/* Self-test of that mechanism, for failure-detection tests: launches one
+ * block whose thread waits, with the same bounded wait the tensor-core
+ * pipeline uses, on a barrier that nothing ever signals, limited to limit_ms
+ * (0 < limit_ms <= 2000).  The wait gives up, records the error and the
+ * kernel returns; the call then reports LITHO_ETIMEOUT through
+ * litho_check_device (which also clears the flag).  The device stays usable.
+ * Any other status means the limit did not work. */
+litho_status litho_selftest_wait_limit(const litho_kernels* h, double limit_ms, void* stream);
+
 /* The same computation from host memory, optionally followed by the resist:
  * copies mask_host[b][n][n] in, images, and copies back whichever of
  * intensity_host[b][F][n][n] (f32) and printed_host[b][F][n][n] (u8, the
@@ -268,6 +277,11 @@ litho_status litho_serve_poll(litho_server* s, uint64_t ticket, int timeout_ms);
 /* Cancels a request that has not started; EBUSY if it is already running. */
 litho_status litho_serve_cancel(litho_server* s, uint64_t ticket);
 litho_status litho_serve_stats(litho_server* s, litho_serve_stats_t* out);
+/* Starts a new statistics window (latencies, counters, throughput span,
+ * high-water mark); queued and running requests and the kernel cache are
+ * untouched.  Requests submitted before the reset that complete after it
+ * still count as completed in the new window. */
+litho_status litho_serve_stats_reset(litho_server* s);
 /* Waits for running requests, cancels queued ones, frees everything. */
 void litho_serve_destroy(litho_server* s);
 /* Host-side fault injection for tests: bit 0 makes the next admitted

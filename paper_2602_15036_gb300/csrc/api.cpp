@@ -450,6 +450,12 @@ litho_status litho_check_device(const litho_kernels* h, void* stream) {
   return gemm_check_device(h, static_cast<cudaStream_t>(stream));
 }
 
+litho_status litho_selftest_wait_limit(const litho_kernels* h, double limit_ms, void* stream) {
+  LITHO_REQUIRE(h, "null handle");
+  LITHO_REQUIRE(limit_ms > 0 && limit_ms <= 2000, "limit_ms must be in (0, 2000]");
+  return gemm_wait_selftest(h, limit_ms, static_cast<cudaStream_t>(stream));
+}
+
 // ---- resist ------------------------------------------------------------------------------------------
 
 litho_status litho_resist(const float* intensity_dev, int planes, int n, double pixel_nm, double sigma_nm,

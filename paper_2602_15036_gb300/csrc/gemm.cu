@@ -156,17 +156,31 @@ struct GemmParams {
 // Bounded wait: true when the phase completed; false after the limit or
 // when another role already gave up (abort flag in shared memory).
 __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                         int code) {
+                                         int code, long long limit = kWaitCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > limit) {
       *abort_flag = 1;
       atomicExch(err, code);
       return false;
     }
   }
   return true;
+}
+
+// Self-test of the bounded wait: one barrier that nothing ever arrives on.
+// The wait must give up after `limit` cycles, record `code` and return.
+__global__ void k_wait_selftest(int* err, long long limit, int code) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) wait_bar(smem_u32(&bar), 0, &abort_flag, err, code, limit);
 }
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -427,7 +441,7 @@ struct OutSplit {
 template <int N, int MODE>
 cudaError_t stage1_split_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
                            const float* scales, void* a_hi, void* a_lo, cudaStream_t st) {
-  return launch_stage1_cols<N>(mhat, phi, nk, crop, tw, OutSplit<MODE>{a_hi, a_lo, scales, N, crop}, st);
+  return launch_stage1_cols<N, ColW<N>::W>(mhat, phi, nk, crop, tw, OutSplit<MODE>{a_hi, a_lo, scales, N, crop}, st);
 }
 
 template <int MODE>
@@ -673,6 +687,29 @@ litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int c
 }
 
 int gemm_group_clips() { return GROUP_CLIPS; }
+
+litho_status gemm_wait_selftest(const litho_kernels* hc, double limit_ms, cudaStream_t st) {
+  litho_kernels* h = const_cast<litho_kernels*>(hc);
+  {
+    static std::mutex create_mu;
+    std::lock_guard<std::mutex> lk0(create_mu);
+    if (!h->gemm) h->gemm = new GemmOperands();
+  }
+  {
+    std::lock_guard<std::mutex> lk(h->gemm->mu);
+    if (!h->gemm->d_err) {
+      LITHO_TRY_CUDA(cudaMalloc(&h->gemm->d_err, sizeof(int)));
+      LITHO_TRY_CUDA(cudaMemset(h->gemm->d_err, 0, sizeof(int)));
+    }
+  }
+  int dev = 0, khz = 0;
+  LITHO_TRY_CUDA(cudaGetDevice(&dev));
+  LITHO_TRY_CUDA(cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev));
+  const long long limit = (long long)(limit_ms * double(khz > 0 ? khz : 2000000));
+  k_wait_selftest<<<1, 32, 0, st>>>(h->gemm->d_err, limit, 9);
+  LITHO_TRY_CUDA(cudaGetLastError());
+  return gemm_check_device(h, st);
+}
 
 litho_status gemm_check_device(const litho_kernels* h, cudaStream_t st) {
   if (!h->gemm || !h->gemm->d_err) return LITHO_OK;

@@ -19,6 +19,9 @@ litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int c
                                litho_precision prec, bool coarse, float* img, void* ws, cudaStream_t st);
 // Waits for `st` and reports ETIMEOUT if a device-side pipeline wait gave up.
 litho_status gemm_check_device(const litho_kernels* h, cudaStream_t st);
+// Runs the bounded-wait self-test kernel (a wait nothing completes, limited to
+// limit_ms) and returns what gemm_check_device reports (ETIMEOUT when it works).
+litho_status gemm_wait_selftest(const litho_kernels* h, double limit_ms, cudaStream_t st);
 void gemm_free_operands(litho_kernels* h);
 
 }  // namespace litho

@@ -66,7 +66,19 @@ struct Req {
   double t_submit = 0, t_done = 0;
   int slot = -1;
   litho_server* srv = nullptr;
+  bool in_pinned = false, out_pinned = false;  // caller buffers usable for DMA directly
 };
+
+// True for page-locked (cudaHostAlloc / cudaHostRegister) host memory.
+bool is_pinned(const void* p) {
+  if (!p) return true;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeHost;
+}
 
 struct Slot {
   cudaStream_t stream = nullptr;
@@ -164,7 +176,7 @@ void CUDART_CB on_done(void* arg) {
   Slot& sl = s->slots[q->slot];
   const size_t nn = size_t(q->r.n) * q->r.n;
   const size_t in_bytes = nn * 4 * (q->r.kind == LITHO_REQ_ILT_STEP ? 2 : 1);
-  std::memcpy(q->r.output_host, sl.pinned + up256(in_bytes), nn * 4);
+  if (!q->out_pinned) std::memcpy(q->r.output_host, sl.pinned + up256(in_bytes), nn * 4);
   if (q->r.kind == LITHO_REQ_ILT_STEP && q->r.loss_host)
     std::memcpy(q->r.loss_host, sl.pinned + up256(in_bytes) + up256(nn * 4), sizeof(double));
   std::lock_guard<std::mutex> lk(s->mu);
@@ -189,8 +201,14 @@ litho_status launch(litho_server* s, Req* q, litho_kernels* h, std::string* err)
     }
     sl.pinned_bytes = stage;
   }
-  std::memcpy(sl.pinned, r.input_host, nn * 4);
-  if (ilt) std::memcpy(sl.pinned + nn * 4, r.target_host, nn * 4);
+  // Pinned caller buffers are copied by DMA directly; pageable ones go through
+  // the slot's pinned staging buffer.
+  q->in_pinned = is_pinned(r.input_host) && (!ilt || is_pinned(r.target_host));
+  q->out_pinned = is_pinned(r.output_host);
+  if (!q->in_pinned) {
+    std::memcpy(sl.pinned, r.input_host, nn * 4);
+    if (ilt) std::memcpy(sl.pinned + nn * 4, r.target_host, nn * 4);
+  }
   const size_t dev_bytes = q->footprint;
   void* d = nullptr;
   if (s->fault_mask.load() & 1) {
@@ -215,8 +233,13 @@ litho_status launch(litho_server* s, Req* q, litho_kernels* h, std::string* err)
     cudaFreeAsync(d, sl.stream);
     return code;
   };
-  if (cudaMemcpyAsync(d_in, sl.pinned, in_bytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+  if (q->in_pinned) {
+    if (cudaMemcpyAsync(d_in, r.input_host, nn * 4, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess ||
+        (ilt && cudaMemcpyAsync(d_tg, r.target_host, nn * 4, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess))
+      return fail(LITHO_ECUDA, "host-to-device copy failed");
+  } else if (cudaMemcpyAsync(d_in, sl.pinned, in_bytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
     return fail(LITHO_ECUDA, "host-to-device copy failed");
+  }
   if (ilt) {
     st = litho_ilt_grad(h, d_in, d_tg, 1, r.dose, r.mask_steep, r.resist_steep, r.threshold, r.sigma_nm,
                         LITHO_PREC_FFT32, d_out, nullptr, ws, ws_bytes, sl.stream);
@@ -224,7 +247,8 @@ litho_status launch(litho_server* s, Req* q, litho_kernels* h, std::string* err)
     st = litho_aerial(h, d_in, 1, r.dose, static_cast<litho_precision>(r.precision), d_out, ws, ws_bytes, sl.stream);
   }
   if (st != LITHO_OK) return fail(st, litho_last_error());
-  if (cudaMemcpyAsync(sl.pinned + up256(in_bytes), d_out, nn * 4, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+  if (cudaMemcpyAsync(q->out_pinned ? static_cast<void*>(r.output_host) : sl.pinned + up256(in_bytes), d_out, nn * 4,
+                      cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
     return fail(LITHO_ECUDA, "device-to-host copy failed");
   if (ilt) {
     double* loss_dev = ilt_loss_device(h, 1, ws, ws_bytes);
@@ -354,8 +378,24 @@ litho_status litho_serve_create(size_t hbm_budget_bytes, int max_slots, int max_
   s->max_slots = max_slots;
   s->max_queue = max_queue;
   LITHO_TRY_CUDA(cudaGetDevice(&s->device));
+  // Keep memory freed by cudaFreeAsync in the device pool instead of returning
+  // it to the driver at every synchronisation: re-mapping it costs far more
+  // than a request's kernels.
+  cudaMemPool_t pool;
+  LITHO_TRY_CUDA(cudaDeviceGetDefaultMemPool(&pool, s->device));
+  uint64_t keep = ~0ull;
+  LITHO_TRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
   s->slots.resize(max_slots);
-  for (auto& sl : s->slots) LITHO_TRY_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+  // Pinned staging sized up front for the largest request (2048^2 ILT step:
+  // theta, target, gradient), so no slot ever reallocates it: cudaFreeHost
+  // and cudaMallocHost both wait for the whole device.
+  const size_t nn = size_t(2048) * 2048;
+  const size_t stage = up256(nn * 4 * 2) + up256(nn * 4) + 256;
+  for (auto& sl : s->slots) {
+    LITHO_TRY_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+    LITHO_TRY_CUDA(cudaMallocHost(&sl.pinned, stage));
+    sl.pinned_bytes = stage;
+  }
   litho_server* raw = s.release();
   raw->sched = std::thread(scheduler, raw);
   raw->builder = std::thread(kernel_builder, raw);
@@ -495,6 +535,18 @@ litho_status litho_serve_stats(litho_server* s, litho_serve_stats_t* out) {
   int built = 0;
   for (auto& kv : s->cache) built += kv.second.h != nullptr;
   out->kernel_sets_cached = built;
+  return LITHO_OK;
+}
+
+litho_status litho_serve_stats_reset(litho_server* s) {
+  if (!s) return LITHO_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  s->latencies.clear();
+  s->submitted = s->completed = s->rejected = s->cancelled = 0;
+  s->first_submit = -1.0;
+  s->last_done = 0.0;
+  s->pixels = 0.0;
+  s->high_water = s->in_use + s->cache_bytes;
   return LITHO_OK;
 }
 

@@ -23,19 +23,23 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Shared memory of k_stage1_cols in float2 units.
-template <int N>
-inline size_t stage1_smem_elems(int crop) {
-  return size_t(N) + size_t(ColW<N>::W) * ColLD<N>::value + 3 * size_t(ColW<N>::W) * band_ld<N>(crop);
-}
+// Strides for a block of W columns: each column's padded transform, rounded
+// up to 16 complex values plus 16/W, and the compact band buffers crop + 16/W,
+// so that the cooperative copies (w fastest) hit 16 different bank pairs.
+template <int N, int W>
+struct Stage1Shape {
+  static constexpr int LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
+  static int bld(int crop) { return crop + 16 / W; }
+  static size_t smem_elems(int crop) { return size_t(N) + size_t(W) * LD + 3 * size_t(W) * bld(crop); }
+};
 
-template <int N, class Out>
-__global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W)
+template <int N, int W, class Out>
+__global__ void __launch_bounds__(Plan<N>::NT * W)
     k_stage1_cols(const float2* __restrict__ mhat, const float2* __restrict__ phi, int crop, int nk, int jb,
                   const float2* __restrict__ tw_g, Out out) {
-  constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value, T = W * NT;
+  constexpr int NT = Plan<N>::NT, LD = Stage1Shape<N, W>::LD, T = W * NT;
   extern __shared__ float2 smem[];
-  const int bld = band_ld<N>(crop);
+  const int bld = crop + 16 / W;
   float2* tw = smem;
   float2* buf = smem + N;
   float2* const blk0 = buf + W * LD;  // Phi (or spectrum) blocks, double-buffered: blk0 + s W bld
@@ -98,15 +102,16 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W)
   }
 }
 
-template <int N, class Out>
+// W columns per CTA (a divisor of 32; crop is a multiple of 32).
+template <int N, int W, class Out>
 cudaError_t launch_stage1_cols(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, Out out,
                                cudaStream_t st) {
-  constexpr int W = ColW<N>::W, JB = 8;
-  const size_t sm = sizeof(float2) * stage1_smem_elems<N>(crop);
-  cudaError_t e = smem_attrs(k_stage1_cols<N, Out>, sm);
+  constexpr int JB = 8;
+  const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop);
+  cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out>, sm);
   if (e != cudaSuccess) return e;
-  k_stage1_cols<N, Out><<<dim3(crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(mhat, phi, crop, nk, JB,
-                                                                                          tw, out);
+  k_stage1_cols<N, W, Out><<<dim3(crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(mhat, phi, crop, nk,
+                                                                                             JB, tw, out);
   return cudaGetLastError();
 }
 

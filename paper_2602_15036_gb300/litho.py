@@ -79,6 +79,7 @@ _SIGS = {
     "litho_aerial_host": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_double, c_double,
                                   c_void_p, c_void_p, c_size_t, c_void_p]),
     "litho_check_device": (c_int, [c_void_p, c_void_p]),
+    "litho_selftest_wait_limit": (c_int, [c_void_p, c_double, c_void_p]),
     "litho_aerial_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]),
     "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
@@ -92,6 +93,7 @@ _SIGS = {
     "litho_serve_stats": (c_int, [c_void_p, POINTER(litho_serve_stats_t)]),
     "litho_serve_destroy": (None, [c_void_p]),
     "litho_serve_inject_fault": (c_int, [c_void_p, c_int]),
+    "litho_serve_stats_reset": (c_int, [c_void_p]),
     "litho_profile_enable": (c_int, [c_int]),
     "litho_profile_reset": (None, []),
     "litho_profile_read": (c_int, [c_int, c_char_p, POINTER(c_double), POINTER(ctypes.c_longlong), POINTER(c_int)]),
@@ -264,6 +266,11 @@ def litho_check_device(kern: Kernels, stream=None):
     _check(lib().litho_check_device(kern.handle, _stream_ptr(stream)))
 
 
+def litho_selftest_wait_limit(kern: Kernels, limit_ms: float = 50.0, stream=None) -> int:
+    """Status of the bounded-wait self-test (ETIMEOUT when the limit works)."""
+    return lib().litho_selftest_wait_limit(kern.handle, limit_ms, _stream_ptr(stream))
+
+
 def litho_aerial_noalloc(kern: Kernels, mask, out, dose=1.0, stream=None):
     """FP32 aerial image with no device allocation: the library's fixed scratch
     array stands in for the workspace, so `out` must be preallocated
@@ -363,6 +370,9 @@ class Server:
 
     def inject_fault(self, mask: int):
         _check(lib().litho_serve_inject_fault(self.handle, mask))
+
+    def stats_reset(self):
+        _check(lib().litho_serve_stats_reset(self.handle))
 
     def stats(self) -> dict:
         s = litho_serve_stats_t()
