@@ -169,8 +169,11 @@ litho_status litho_selftest_wait_limit(const litho_kernels* h, double limit_ms, 
  * intensity_host[b][F][n][n] (f32) and printed_host[b][F][n][n] (u8, the
  * litho_resist threshold of the blurred image with sigma_nm and threshold) is
  * non-NULL, then waits for the stream.  Device buffers are carved from
- * workspace_dev (litho_aerial_host_workspace_size bytes).  Pinned host memory
- * lets the copies run at full link speed. */
+ * workspace_dev (litho_aerial_host_workspace_size bytes).  Batches of 4 or more
+ * clips run in chunks alternating between two library streams (ordered after
+ * `stream`), so that one chunk's copies overlap another chunk's kernels;
+ * pinned host memory lets the copies run asynchronously at full link speed.
+ * Calls on the same kernel set are serialised. */
 litho_status litho_aerial_host_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes);
 litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, int b, double dose,
                                litho_precision prec, float* intensity_host, double sigma_nm, double threshold,

@@ -101,6 +101,10 @@ void litho_free_kernels(litho_kernels* h) {
   cudaFree(h->d_phi);
   cudaFree(h->d_tw);
   cudaFree(h->d_twc);
+  for (auto& s : h->host_streams)
+    if (s) cudaStreamDestroy(s);
+  for (auto& e : h->host_events)
+    if (e) cudaEventDestroy(e);
   gemm_free_operands(h);
   cudaSetDevice(cur);
   delete h;
@@ -399,14 +403,26 @@ litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, 
   return LITHO_OK;
 }
 
+// The host-buffer path images the batch in chunks of clips that alternate
+// between two streams, so that one chunk's copies overlap another chunk's
+// kernels.  Each stream owns one region of the workspace.
+static int host_chunk_clips(int b) { return b >= 4 ? std::min(8, (b + 3) / 4) : b; }
+
+static size_t host_region_bytes(const litho_kernels* h, int cb, litho_precision prec) {
+  size_t w = 0;
+  if (litho_aerial_workspace_size(h, cb, prec, &w) != LITHO_OK) return 0;
+  const size_t nn = size_t(h->n) * h->n, planes = size_t(cb) * h->n_focus;
+  return align_up(w) + align_up(size_t(cb) * nn * sizeof(float)) + 2 * align_up(planes * nn * sizeof(float)) +
+         align_up(planes * nn);
+}
+
 litho_status litho_aerial_host_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes) {
   LITHO_REQUIRE(h && bytes && b >= 1, "bad argument");
   size_t w = 0;
-  litho_status s = litho_aerial_workspace_size(h, b, prec, &w);
+  litho_status s = litho_aerial_workspace_size(h, b, prec, &w);  // validates prec
   if (s != LITHO_OK) return s;
-  const size_t nn = size_t(h->n) * h->n, planes = size_t(b) * h->n_focus;
-  *bytes = align_up(w) + align_up(size_t(b) * nn * sizeof(float)) + 2 * align_up(planes * nn * sizeof(float)) +
-           align_up(planes * nn);
+  const int cb = host_chunk_clips(b);
+  *bytes = (cb < b ? 2 : 1) * host_region_bytes(h, cb, prec);
   return LITHO_OK;
 }
 
@@ -415,33 +431,65 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
                                uint8_t* printed_host, void* workspace_dev, size_t workspace_bytes, void* stream) {
   LITHO_REQUIRE(h && mask_host && workspace_dev, "null argument");
   LITHO_REQUIRE(intensity_host || printed_host, "nothing to return: intensity_host and printed_host are both NULL");
-  size_t need = 0, w = 0;
+  size_t need = 0;
   litho_status s = litho_aerial_host_workspace_size(h, b, prec, &need);
   if (s != LITHO_OK) return s;
   if (workspace_bytes < need) {
     set_error("workspace too small: %zu bytes given, %zu needed", workspace_bytes, need);
     return LITHO_ENOMEM;
   }
-  litho_aerial_workspace_size(h, b, prec, &w);
+  const int cb = host_chunk_clips(b), F = h->n_focus;
+  const size_t region = host_region_bytes(h, cb, prec);
+  size_t w = 0;
+  litho_aerial_workspace_size(h, cb, prec, &w);
   w = align_up(w);
-  const size_t nn = size_t(h->n) * h->n, planes = size_t(b) * h->n_focus;
-  char* base = static_cast<char*>(workspace_dev);
-  float* dmask = reinterpret_cast<float*>(base + w);
-  float* dimg = reinterpret_cast<float*>(base + w + align_up(size_t(b) * nn * sizeof(float)));
-  float* dblur = reinterpret_cast<float*>(reinterpret_cast<char*>(dimg) + align_up(planes * nn * sizeof(float)));
-  uint8_t* dpr = reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(dblur) + align_up(planes * nn * sizeof(float)));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  LITHO_TRY_CUDA(cudaMemcpyAsync(dmask, mask_host, size_t(b) * nn * sizeof(float), cudaMemcpyHostToDevice, st));
-  s = litho_aerial(h, dmask, b, dose, prec, dimg, workspace_dev, w, stream);
-  if (s != LITHO_OK) return s;
-  if (printed_host) {
-    s = litho_resist(dimg, int(planes), h->n, h->pixel_nm, sigma_nm, threshold, dblur, dpr, stream);
-    if (s != LITHO_OK) return s;
-    LITHO_TRY_CUDA(cudaMemcpyAsync(printed_host, dpr, planes * nn, cudaMemcpyDeviceToHost, st));
+  const size_t nn = size_t(h->n) * h->n;
+  cudaStream_t caller = static_cast<cudaStream_t>(stream);
+  cudaStream_t lanes[2] = {caller, caller};
+  litho_kernels* hm = const_cast<litho_kernels*>(h);
+  // concurrent host-path calls on one kernel set share its two streams: one at a time
+  std::lock_guard<std::mutex> lk(hm->host_mu);
+  if (cb < b) {
+    for (int i = 0; i < 2; ++i)
+      if (!hm->host_streams[i]) LITHO_TRY_CUDA(cudaStreamCreateWithFlags(&hm->host_streams[i], cudaStreamNonBlocking));
+    if (!hm->host_events[0])
+      for (int i = 0; i < 3; ++i) LITHO_TRY_CUDA(cudaEventCreateWithFlags(&hm->host_events[i], cudaEventDisableTiming));
+    lanes[0] = hm->host_streams[0];
+    lanes[1] = hm->host_streams[1];
+    LITHO_TRY_CUDA(cudaEventRecord(hm->host_events[0], caller));
+    for (int i = 0; i < 2; ++i) LITHO_TRY_CUDA(cudaStreamWaitEvent(lanes[i], hm->host_events[0], 0));
   }
-  if (intensity_host)
-    LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host, dimg, planes * nn * sizeof(float), cudaMemcpyDeviceToHost, st));
-  LITHO_TRY_CUDA(cudaStreamSynchronize(st));
+  for (int c0 = 0, ci = 0; c0 < b; c0 += cb, ++ci) {
+    const int nb = std::min(cb, b - c0);
+    const size_t planes = size_t(nb) * F;
+    cudaStream_t st = lanes[ci & 1];
+    char* base = static_cast<char*>(workspace_dev) + (ci & 1) * (cb < b ? region : 0);
+    float* dmask = reinterpret_cast<float*>(base + w);
+    float* dimg = reinterpret_cast<float*>(base + w + align_up(size_t(cb) * nn * sizeof(float)));
+    float* dblur =
+        reinterpret_cast<float*>(reinterpret_cast<char*>(dimg) + align_up(size_t(cb) * F * nn * sizeof(float)));
+    uint8_t* dpr =
+        reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(dblur) + align_up(size_t(cb) * F * nn * sizeof(float)));
+    LITHO_TRY_CUDA(cudaMemcpyAsync(dmask, mask_host + size_t(c0) * nn, size_t(nb) * nn * sizeof(float),
+                                   cudaMemcpyHostToDevice, st));
+    s = litho_aerial(h, dmask, nb, dose, prec, dimg, base, w, st);
+    if (s != LITHO_OK) return s;
+    if (printed_host) {
+      s = litho_resist(dimg, int(planes), h->n, h->pixel_nm, sigma_nm, threshold, dblur, dpr, st);
+      if (s != LITHO_OK) return s;
+      LITHO_TRY_CUDA(cudaMemcpyAsync(printed_host + size_t(c0) * F * nn, dpr, planes * nn, cudaMemcpyDeviceToHost, st));
+    }
+    if (intensity_host)
+      LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host + size_t(c0) * F * nn, dimg, planes * nn * sizeof(float),
+                                     cudaMemcpyDeviceToHost, st));
+  }
+  if (cb < b) {
+    for (int i = 0; i < 2; ++i) {
+      LITHO_TRY_CUDA(cudaEventRecord(hm->host_events[1 + i], lanes[i]));
+      LITHO_TRY_CUDA(cudaStreamWaitEvent(caller, hm->host_events[1 + i], 0));
+    }
+  }
+  LITHO_TRY_CUDA(cudaStreamSynchronize(caller));
   return LITHO_OK;
 }
 

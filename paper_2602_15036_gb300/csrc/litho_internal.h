@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <complex>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -93,6 +94,10 @@ struct litho_kernels {
   float2* d_twc = nullptr;                 // FFT twiddle table for nc
   litho::GemmOperands* gemm = nullptr;     // lazily built per precision
   int device = 0;
+  // streams and events of the pipelined host-buffer path (created on first use)
+  std::mutex host_mu;
+  cudaStream_t host_streams[2] = {nullptr, nullptr};
+  cudaEvent_t host_events[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace litho {
