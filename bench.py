@@ -143,42 +143,117 @@ def whole_job_rate(units_per_rank: float, world: int, rank_seconds: list[float])
 
 # ---- algorithmic work models (per step) ------------------------------------------------------------
 
-def stage_models(prec: str, clips: int, n: int, crop: int, n_focus: int, k_eff: int, nc: int, peaks) -> dict:
-    """stage -> (bound, work per step, unit, peak): FLOPs for transforms and GEMMs, bytes for the resist."""
+def fft_group(clips: int, n_focus: int, k: int, ne: int, crop: int) -> int:
+    """Clips per FP32 stage launch: the library's rule (stage-1 fields of a group within
+    2 GiB, at most 64 clips, groups of equal size)."""
+    per_clip = n_focus * k * ne * crop * 8
+    cap = max(1, min(64, (2 << 30) // per_clip))
+    groups = -(-clips // cap)
+    return -(-clips // groups)
+
+
+def stage_models(prec: str, clips: int, n: int, crop: int, n_focus: int, k_eff: int, nc: int, peaks,
+                 resist_taps: int = 11, k_alloc: int = K) -> dict:
+    """stage -> (flops per step, algorithmic DRAM bytes per step).
+
+    Bytes count what the stage must move at least: its inputs read once and its
+    outputs written once (intermediates of the library's own making that a stage
+    writes and reads back, such as the row spectra of a 2D transform, are not
+    counted); the kernels Phi count once per launch, since a launch's clips share
+    them.  Flops count 5 m log2 m per m-point complex transform and 6 per complex
+    multiply-add of the band multiply."""
     coarse = prec.endswith("/coarse") and nc > 0
     ne = nc if coarse else n
-    planes_k = clips * n_focus * k_eff
+    fk = n_focus * k_eff
     fft = lambda m: 5.0 * m * math.log2(m)  # noqa: E731  (radix-2 operation count of an m-point transform)
-    hbm = peaks["hbm_gbs"]
-    tensor = peaks["bf16_tflops_sustained"]
     base = prec.split("/")[0]
     split = base in ("fp16x3", "bf16x3")
+    planes = clips * n_focus
+    group = fft_group(clips, n_focus, k_alloc, ne, crop) if base == "fft32" else min(clips, 4)
+    launches = -(-clips // group)
+    phi_bytes = n_focus * k_alloc * crop * crop * 8.0
+    t1_bytes = clips * fk * ne * crop * 8.0
     m = {
-        "mask_spectrum": ("hbm", clips * n * n * 4.0, "GB/s", hbm),
-        "stage1_fft": ("alu", planes_k * crop * fft(ne), "TFLOP/s", ALU_PEAK_TFLOPS),
-        "stage1_gemm_operands": ("alu", planes_k * crop * fft(ne), "TFLOP/s", ALU_PEAK_TFLOPS),
-        "stage2_fft": ("alu", planes_k * ne * (fft(ne) + 4.0 * ne), "TFLOP/s", ALU_PEAK_TFLOPS),
-        "stage2_gemm": ("tensor", planes_k * 8.0 * ne * ne * crop * (3 if split else 1), "TFLOP/s", tensor),
-        "resist": ("hbm", clips * n_focus * n * n * 9.0, "GB/s", hbm),
+        "mask_spectrum": (clips * (n / 2 * fft(n) + crop * fft(n)), clips * (n * n * 4.0 + crop * crop * 8.0)),
+        "stage1_fft": (clips * fk * (crop * fft(ne) + 6.0 * crop * crop),
+                       launches * phi_bytes + clips * crop * crop * 8.0 + t1_bytes),
+        "stage2_fft": (clips * fk * ne * (fft(ne) + 4.0 * ne), t1_bytes + planes * ne * ne * 4.0),
+        "stage1_gemm_operands": (clips * fk * (crop * fft(ne) + 6.0 * crop * crop),
+                                 launches * phi_bytes + clips * crop * crop * 8.0 +
+                                 clips * fk * ne * crop * (8.0 if split else 4.0)),
+        "stage2_gemm": (clips * fk * 8.0 * ne * ne * crop * (3 if split else 1),
+                        clips * fk * ne * crop * (8.0 if split else 4.0) + planes * ne * ne * 4.0),
+        "resist": (planes * n * n * 4.0 * resist_taps, planes * n * n * 9.0),
     }
     if coarse:
         c2 = 2 * crop
-        m["upsample"] = ("alu", clips * n_focus * (ne / 2 * fft(ne) + c2 * fft(ne) + c2 * fft(n) + n * fft(n)),
-                         "TFLOP/s", ALU_PEAK_TFLOPS)
+        up = planes * (ne / 2 * fft(ne) + c2 * fft(ne) + c2 * fft(n) + n * fft(n))
+        m["upsample"] = (up, planes * (ne * ne * 4.0 + n * n * 4.0))
+        m["upsample_resist"] = (up + planes * c2 * c2 * 6.0, planes * (ne * ne * 4.0 + n * n * 9.0))
     return m
 
 
-def rooflines(prof: dict, steps: int, models: dict) -> dict:
+# Sources whose kernels each stage runs: a DRAM-traffic figure taken with ncu
+# holds only while they are unchanged.
+STAGE_SOURCES = {
+    "stage1_fft": ["stage1.cuh", "fft.cu", "fft_common.cuh"],
+    "stage2_fft": ["fft.cu", "fft_common.cuh"],
+    "upsample_resist": ["stage1.cuh", "fft.cu", "fft_common.cuh"],
+}
+
+
+def sources_digest(stage: str):
+    import hashlib
+    files = STAGE_SOURCES.get(stage)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2602_15036_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(stage: str, prec: str, clips: int, launches_per_step: float):
+    """DRAM bytes per launch of `stage` from the committed ncu summary
+    (profiles/dram_traffic.json), if it was taken on the same sources with the
+    same clips per launch; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            entries = json.load(f)
+    except Exception:
+        return None, None
+    per_launch = clips / launches_per_step if launches_per_step else None
+    for e in entries:
+        if (e.get("stage") == stage and e.get("precision") == prec and e.get("sources") == sources_digest(stage)
+                and per_launch and abs(e.get("clips_per_launch", -1) - per_launch) < 1e-9):
+            return e["bytes_per_launch"], e.get("summary")
+    return None, None
+
+
+def rooflines(prof: dict, steps: int, models: dict, peaks) -> dict:
+    """Per stage: the binding resource (the larger of flops / ALU peak and bytes / HBM
+    peak) with achieved = work per step / measured time per step, plus the other one."""
     out = {}
+    hbm = peaks["hbm_gbs"]
     for stage, (ms, launches) in prof.items():
         if stage not in models:
             continue
-        bound, work, unit, peak = models[stage]
+        flops, nbytes = models[stage]
         sec = ms / steps * 1e-3
-        scale = 1e9 if unit == "GB/s" else 1e12
-        achieved = work / sec / scale
-        out[stage] = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                      "ms_per_step": ms / steps, "launches_per_step": launches / steps}
+        tensor = stage == "stage2_gemm"
+        fpeak = peaks["bf16_tflops_sustained"] if tensor else ALU_PEAK_TFLOPS
+        alu = {"bound": "tensor" if tensor else "alu", "achieved": flops / sec / 1e12, "peak": fpeak,
+               "unit": "TFLOP/s"}
+        mem = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": hbm, "unit": "GB/s"}
+        for d in (alu, mem):
+            d["frac"] = d["achieved"] / d["peak"]
+        t_alu, t_mem = flops / (fpeak * 1e12), nbytes / (hbm * 1e9)
+        main, other = (mem, alu) if t_mem >= t_alu else (alu, mem)
+        lps = launches / steps
+        out[stage] = dict(main, other=other, algorithmic_work_per_step={"flops": flops, "bytes": nbytes},
+                          algorithmic_bytes_per_launch=nbytes / lps if lps else None,
+                          ms_per_step=ms / steps, launches_per_step=lps)
     return out
 
 
@@ -312,8 +387,8 @@ def run_aerial(args):
     results = {}
     for i, prec in enumerate(paths):
         def step():
-            P.litho_aerial(kern, masks, precision=prec, out=img, workspace=ws, stream=stream)
-            P.litho_resist(img, PIXEL, SIGMA_NM, THRESH, iblur=iblur, printed=printed, stream=stream)
+            P.litho_aerial_resist(kern, masks, precision=prec, sigma_nm=SIGMA_NM, threshold=THRESH, out=img,
+                                  iblur=iblur, printed=printed, workspace=ws, stream=stream)
 
         L.litho_profile_enable(True)
         L.litho_profile_reset()
@@ -328,7 +403,7 @@ def run_aerial(args):
         total_ms = ctx.max_over_ranks(sum(step_ms))
         value = whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total_ms * 1e-3])
         models = stage_models(prec, clips, N, c, F, k_eff, nc, peaks)
-        roofs = rooflines(prof, args.steps, models)
+        roofs = rooflines(prof, args.steps, models, peaks)
         results[prec] = dict(value=value, step_ms=step_ms, total_ms=total_ms, clocks=clk, prof=prof, roofs=roofs,
                              launches=sum(v[1] for v in prof.values()))
 
@@ -357,7 +432,10 @@ def run_aerial(args):
     dominant = max(head["roofs"].items(), key=lambda kv: kv[1]["ms_per_step"])
     roof = dict(dominant[1])
     roof["kernel"] = dominant[0]
-    roof["traffic"] = None
+    roof["traffic"], roof["traffic_source"] = measured_traffic(dominant[0], args.precision, clips,
+                                                               roof["launches_per_step"])
+    roof["peak_source"] = (f"{peak_src} HBM copy bandwidth" if roof["bound"] == "hbm" else
+                           "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")
     plain = results.get("fft32")
     line = {"metric": METRIC, "value": head["value"], "unit": "Mpx/s", "n_gpus": ctx.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,

@@ -148,6 +148,23 @@ litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_pr
 litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, double dose, litho_precision prec,
                           float* intensity_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
 
+/* litho_aerial followed by litho_resist (paper Eqs. (4)-(5)) in one call:
+ * intensity_dev as litho_aerial, iblur_dev[b][F][n][n] (f32) the periodic
+ * Gaussian blur of every plane with sigma_nm (the kernel set's pixel size),
+ * printed_dev (u8, may be NULL) = [iblur >= threshold].  Same workspace as
+ * litho_aerial (litho_aerial_workspace_size).  With LITHO_GRID_COARSE (when it
+ * applies) the blur is applied in the frequency domain during the exact
+ * interpolation to n x n: the image spectrum is band-limited, so multiplying
+ * it by the transfer function of the truncated taps, sum_a g[a]
+ * e^{-2 pi i f a/n} in each axis, is the periodic convolution exactly (up to
+ * rounding), and the image and its blur come out of one complex inverse
+ * transform as its real and imaginary parts.  Otherwise the litho_resist
+ * kernel runs after the image.  Errors: as litho_aerial and litho_resist. */
+litho_status litho_aerial_resist(const litho_kernels* h, const float* mask_dev, int b, double dose,
+                                 litho_precision prec, float* intensity_dev, double sigma_nm, double threshold,
+                                 float* iblur_dev, uint8_t* printed_dev, void* workspace_dev, size_t workspace_bytes,
+                                 void* stream);
+
 /* Waits for `stream` and reports LITHO_ETIMEOUT if, since the last check, a
  * tensor-core kernel of this kernel set gave up waiting on one of its
  * pipeline barriers (each such wait is bounded at about two seconds; the

@@ -5,6 +5,6 @@ of include/litho.h); this package is its Python binding (`litho`) and the
 in-tree build step (`build`).
 """
 from . import litho  # noqa: F401
-from .litho import (Kernels, LithoError, litho_aerial, litho_aerial_host,  # noqa: F401
+from .litho import (Kernels, LithoError, litho_aerial, litho_aerial_host, litho_aerial_resist,  # noqa: F401
                     litho_aerial_host_workspace_size, litho_aerial_workspace_size, litho_ilt_grad,
                     litho_ilt_workspace_size, litho_make_kernels, litho_tcc_kernels_host, litho_resist, litho_upload_kernels, make_optics)

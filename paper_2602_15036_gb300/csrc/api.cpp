@@ -278,17 +278,33 @@ litho_status litho_kernels_phi(const litho_kernels* h, double* phi_host) {
 
 // ---- aerial ------------------------------------------------------------------------------------------
 
-// Workspace regions of litho_aerial.  With the coarse grid the fields are
-// evaluated on nc x nc and `ic` holds those images until the upsampling
-// (mask-spectrum kernels on a 2C crop, stage 1 over y, real band rows over x)
-// writes the N x N result.
+// Workspace regions of litho_aerial.  The FP32 FFT path images `group`
+// clips per launch (their stage-1 fields side by side in t1); the GEMM path
+// images groups of gemm_group_clips().  With the coarse grid the fields are
+// evaluated on nc x nc and `ic` holds a group's images until the
+// interpolation (mask-spectrum kernels on a 2C crop, stage 1 over y, band
+// rows over x) writes the N x N result; `gain` holds the blur's transfer
+// function when the resist is fused into that interpolation.
 struct AerialLayout {
   float2 *rowbuf = nullptr, *mhat = nullptr, *t1 = nullptr;
   void* gws = nullptr;
   float* ic = nullptr;
   float2 *rowbuf2 = nullptr, *spec = nullptr, *q = nullptr;
+  float* gain = nullptr;
+  int group = 1;
   size_t bytes = 0;
 };
+
+// Clips per FP32 stage launch: enough CTAs that the last wave is a small
+// share of the launch, with the group's stage-1 fields within 2 GiB, and
+// groups of equal size.
+static int fft_group_clips(const litho_kernels* h, int b, bool coarse) {
+  const size_t NE = coarse ? h->nc : h->n;
+  const size_t per_clip = size_t(h->n_focus) * h->k * NE * h->crop * sizeof(float2);
+  const size_t cap = std::max<size_t>(1, std::min<size_t>(64, (size_t(2) << 30) / per_clip));
+  const size_t groups = (size_t(b) + cap - 1) / cap;
+  return int((size_t(b) + groups - 1) / groups);
+}
 
 static AerialLayout aerial_layout(const litho_kernels* h, int b, litho_precision prec, bool coarse, void* ws) {
   Carve c(ws, 0);
@@ -296,18 +312,20 @@ static AerialLayout aerial_layout(const litho_kernels* h, int b, litho_precision
   AerialLayout L;
   L.rowbuf = c.take<float2>(size_t(b) * N * C);
   L.mhat = c.take<float2>(size_t(b) * C * C);
-  size_t planes = F;
   if (prec == LITHO_PREC_FFT32) {
-    L.t1 = c.take<float2>(F * K * NE * C);
+    L.group = fft_group_clips(h, b, coarse);
+    L.t1 = c.take<float2>(size_t(L.group) * F * K * NE * C);
   } else {
     L.gws = c.take<char>(gemm_workspace_bytes(h, prec, b, coarse));
-    planes = size_t(std::min(b, gemm_group_clips())) * F;
+    L.group = std::min(b, gemm_group_clips());
   }
+  const size_t planes = size_t(L.group) * F;
   if (coarse) {
     L.ic = c.take<float>(planes * NE * NE);
     L.rowbuf2 = c.take<float2>(planes * NE * 2 * C);
     L.spec = c.take<float2>(planes * 4 * C * C);
     L.q = c.take<float2>(planes * N * 2 * C);
+    L.gain = c.take<float>(2 * C);
   }
   L.bytes = align_up(c.used);
   return L;
@@ -322,12 +340,32 @@ static bool decode_precision(int raw, litho_precision* p, bool* coarse) {
   return true;
 }
 
-static litho_status upsample(const litho_kernels* h, const AerialLayout& L, int planes, float* out, cudaStream_t st) {
+// Resist fused into the coarse-grid interpolation: outputs of plane p of the
+// call at iblur + p N^2 and printed + p N^2 (printed may be NULL).
+struct FusedResist {
+  float threshold;
+  float* iblur;
+  uint8_t* printed;
+};
+
+// `planes` coarse images in L.ic -> N x N planes at `out` (plane offset `p0`
+// of the call for the fused resist outputs).
+static litho_status upsample(const litho_kernels* h, const AerialLayout& L, int planes, float* out,
+                             const FusedResist* fr, size_t p0, cudaStream_t st) {
   const int N = h->n, NC = h->nc, C2 = 2 * h->crop;
-  ProfScope ps(kStageUpsample, st, 4);
-  LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, h->d_twc, L.rowbuf2, L.spec, st));
+  if (!fr) {
+    ProfScope ps(kStageUpsample, st, 4);
+    LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, h->d_twc, L.rowbuf2, L.spec, st));
+    LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, planes, N, C2, h->d_tw, L.q, st));
+    LITHO_TRY_CUDA(launch_band_rows_real(L.q, planes, N, C2, 1.0f, h->d_tw, out, st));
+    return LITHO_OK;
+  }
+  const size_t nn = size_t(N) * N;
+  ProfScope ps(kStageUpsampleResist, st, 4);
+  LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, h->d_twc, L.rowbuf2, L.spec, st, L.gain));
   LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, planes, N, C2, h->d_tw, L.q, st));
-  LITHO_TRY_CUDA(launch_band_rows_real(L.q, planes, N, C2, 1.0f, h->d_tw, out, st));
+  LITHO_TRY_CUDA(launch_band_rows_resist(L.q, planes, N, C2, h->d_tw, fr->threshold, out, fr->iblur + p0 * nn,
+                                         fr->printed ? fr->printed + p0 * nn : nullptr, st));
   return LITHO_OK;
 }
 
@@ -341,66 +379,121 @@ litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_pr
   return LITHO_OK;
 }
 
-litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, double dose, litho_precision prec,
-                          float* intensity_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+// Argument checks shared by litho_aerial and litho_aerial_resist; fills the
+// decoded precision and the layout.
+static litho_status aerial_prepare(const litho_kernels* h, const float* mask_dev, int b, double dose, int prec,
+                                   float* intensity_dev, void* workspace_dev, size_t workspace_bytes,
+                                   litho_precision* p, bool* coarse, AerialLayout* L) {
   LITHO_REQUIRE(h && mask_dev && intensity_dev && workspace_dev, "null argument");
   LITHO_REQUIRE(b >= 1, "b must be >= 1");
   LITHO_REQUIRE(std::isfinite(dose), "dose must be finite");
-  litho_precision p;
-  bool coarse;
-  LITHO_REQUIRE(decode_precision(int(prec), &p, &coarse), "unknown precision");
-  coarse = coarse && h->nc > 0;
+  LITHO_REQUIRE(decode_precision(prec, p, coarse), "unknown precision");
+  *coarse = *coarse && h->nc > 0;
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(workspace_dev) & 255) == 0, "workspace must be 256-byte aligned");
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(mask_dev) & 15) == 0 && (reinterpret_cast<uintptr_t>(intensity_dev) & 15) == 0,
                 "mask and intensity must be 16-byte aligned");
-  const size_t need = aerial_layout(h, b, p, coarse, nullptr).bytes;
+  const size_t need = aerial_layout(h, b, *p, *coarse, nullptr).bytes;
   if (workspace_bytes < need) {
     set_error("workspace too small: %zu bytes given, %zu needed", workspace_bytes, need);
     return LITHO_ENOMEM;
   }
-  if (p != LITHO_PREC_FFT32) {
-    litho_status s = gemm_supported(h, p, coarse);
+  if (*p != LITHO_PREC_FFT32) {
+    litho_status s = gemm_supported(h, *p, *coarse);
     if (s != LITHO_OK) return s;
   }
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const AerialLayout L = aerial_layout(h, b, p, coarse, workspace_dev);
+  *L = aerial_layout(h, b, *p, *coarse, workspace_dev);
+  return LITHO_OK;
+}
+
+// The aerial image of b clips; with `fr` (coarse grid only) the resist is
+// computed inside the interpolation.
+static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, int b, double dose, litho_precision p,
+                               bool coarse, float* intensity_dev, const AerialLayout& L, const FusedResist* fr,
+                               cudaStream_t st) {
   const int N = h->n, C = h->crop, F = h->n_focus, K = h->k;
   {
     ProfScope ps(kStageMaskSpectrum, st, 2);
     LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev, b, N, C, h->d_tw, L.rowbuf, L.mhat, st));
   }
+  const int G = L.group;
   if (p != LITHO_PREC_FFT32) {
-    const int G = gemm_group_clips();
     for (int c0 = 0; c0 < b; c0 += G) {
       const int g = std::min(G, b - c0);
       float* dst = intensity_dev + size_t(c0) * F * N * N;
       litho_status s =
           gemm_aerial_group(h, L.mhat + size_t(c0) * C * C, g, float(dose), p, coarse, coarse ? L.ic : dst, L.gws, st);
       if (s != LITHO_OK) return s;
-      if (coarse && (s = upsample(h, L, g * F, dst, st)) != LITHO_OK) return s;
+      if (coarse && (s = upsample(h, L, g * F, dst, fr, size_t(c0) * F, st)) != LITHO_OK) return s;
     }
     return LITHO_OK;
   }
   const int NE = coarse ? h->nc : N;
   const float2* tw = coarse ? h->d_twc : h->d_tw;
-  for (int clip = 0; clip < b; ++clip) {
-    const float2* mh = L.mhat + size_t(clip) * C * C;
-    float* img = intensity_dev + size_t(clip) * F * N * N;
+  for (int c0 = 0; c0 < b; c0 += G) {
+    const int g = std::min(G, b - c0);
+    float* img = intensity_dev + size_t(c0) * F * N * N;
     {
       ProfScope ps(kStageStage1Fft, st, 1);
-      LITHO_TRY_CUDA(launch_stage1_fft(mh, h->d_phi, F * K, NE, C, tw, L.t1, st));
+      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat + size_t(c0) * C * C, h->d_phi, F * K, NE, C, tw, L.t1, st, g));
     }
     {
       ProfScope ps(kStageStage2Fft, st, 1);
-      LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda, K, NE, C, float(dose), tw, coarse ? L.ic : img, F,
-                                       (long long)K * NE * C, (long long)NE * NE, st));
+      LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda, K, NE, C, float(dose), tw, coarse ? L.ic : img, g * F,
+                                       (long long)K * NE * C, (long long)NE * NE, st, F));
     }
     if (coarse) {
-      litho_status s = upsample(h, L, F, img, st);
+      litho_status s = upsample(h, L, g * F, img, fr, size_t(c0) * F, st);
       if (s != LITHO_OK) return s;
     }
   }
   return LITHO_OK;
+}
+
+litho_status litho_aerial(const litho_kernels* h, const float* mask_dev, int b, double dose, litho_precision prec,
+                          float* intensity_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+  litho_precision p;
+  bool coarse;
+  AerialLayout L;
+  litho_status s =
+      aerial_prepare(h, mask_dev, b, dose, int(prec), intensity_dev, workspace_dev, workspace_bytes, &p, &coarse, &L);
+  if (s != LITHO_OK) return s;
+  return aerial_run(h, mask_dev, b, dose, p, coarse, intensity_dev, L, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+litho_status litho_aerial_resist(const litho_kernels* h, const float* mask_dev, int b, double dose,
+                                 litho_precision prec, float* intensity_dev, double sigma_nm, double threshold,
+                                 float* iblur_dev, uint8_t* printed_dev, void* workspace_dev, size_t workspace_bytes,
+                                 void* stream) {
+  LITHO_REQUIRE(iblur_dev, "null argument");
+  LITHO_REQUIRE(std::isfinite(threshold), "threshold must be finite");
+  litho_precision p;
+  bool coarse;
+  AerialLayout L;
+  litho_status s =
+      aerial_prepare(h, mask_dev, b, dose, int(prec), intensity_dev, workspace_dev, workspace_bytes, &p, &coarse, &L);
+  if (s != LITHO_OK) return s;
+  ResistTaps taps;
+  std::string why;
+  if (!resist_taps(sigma_nm, h->pixel_nm, &taps, &why)) {
+    set_error("%s", why.c_str());
+    return LITHO_EINVAL;
+  }
+  LITHO_REQUIRE(2 * taps.radius < h->n, "blur radius must be below n/2");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!coarse) {
+    s = aerial_run(h, mask_dev, b, dose, p, coarse, intensity_dev, L, nullptr, st);
+    if (s != LITHO_OK) return s;
+    ProfScope ps(kStageResist, st, 1);
+    LITHO_TRY_CUDA(launch_resist(intensity_dev, b * h->n_focus, h->n, taps, float(threshold), iblur_dev, printed_dev,
+                                 st));
+    return LITHO_OK;
+  }
+  {
+    ProfScope ps(kStageUpsampleResist, st, 1);
+    LITHO_TRY_CUDA(launch_blur_gain(taps, h->n, 2 * h->crop, L.gain, st));
+  }
+  const FusedResist fr{float(threshold), iblur_dev, printed_dev};
+  return aerial_run(h, mask_dev, b, dose, p, coarse, intensity_dev, L, &fr, st);
 }
 
 // The host-buffer path images the batch in chunks of clips that alternate
@@ -472,12 +565,13 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
         reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(dblur) + align_up(size_t(cb) * F * nn * sizeof(float)));
     LITHO_TRY_CUDA(cudaMemcpyAsync(dmask, mask_host + size_t(c0) * nn, size_t(nb) * nn * sizeof(float),
                                    cudaMemcpyHostToDevice, st));
-    s = litho_aerial(h, dmask, nb, dose, prec, dimg, base, w, st);
-    if (s != LITHO_OK) return s;
     if (printed_host) {
-      s = litho_resist(dimg, int(planes), h->n, h->pixel_nm, sigma_nm, threshold, dblur, dpr, st);
+      s = litho_aerial_resist(h, dmask, nb, dose, prec, dimg, sigma_nm, threshold, dblur, dpr, base, w, st);
       if (s != LITHO_OK) return s;
       LITHO_TRY_CUDA(cudaMemcpyAsync(printed_host + size_t(c0) * F * nn, dpr, planes * nn, cudaMemcpyDeviceToHost, st));
+    } else {
+      s = litho_aerial(h, dmask, nb, dose, prec, dimg, base, w, st);
+      if (s != LITHO_OK) return s;
     }
     if (intensity_host)
       LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host + size_t(c0) * F * nn, dimg, planes * nn * sizeof(float),

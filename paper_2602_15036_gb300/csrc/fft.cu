@@ -57,9 +57,14 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_mask_rows(const float* __restri
 
 
 // ---- mask spectrum, pass 2: column DFTs of the crop columns, crop rows kept ------------------
+// With `gain` (per crop index, real and even in the frequency), the stored
+// value is S (1 + i gain[v] gain[u]): an image whose spectrum is S comes out
+// of the inverse transform as I + i (g (x) I) for the separable filter with
+// transfer function gain (x) gain, because both I and g (x) I are real.
 template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const float2* __restrict__ rowbuf, int crop,
                                                                          const float2* __restrict__ tw_g,
+                                                                         const float* __restrict__ gain,
                                                                          float2* __restrict__ mhat) {
   constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
   extern __shared__ float2 smem[];
@@ -80,9 +85,30 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const fl
   for (int i = tid; i < crop * W; i += blockDim.x) {
     const int cv = i / W, w = i % W;
     const int idx = (cv - half + N) % N;
-    const float2 v = buf[w * LD + pad16(idx)];
-    dst[(size_t)cv * crop + w] = make_float2(v.x * scale, v.y * scale);
+    float2 v = buf[w * LD + pad16(idx)];
+    v = make_float2(v.x * scale, v.y * scale);
+    if (gain) {
+      const float g = __ldg(gain + cv) * __ldg(gain + u0 + w);
+      v = make_float2(fmaf(-g, v.y, v.x), fmaf(g, v.x, v.y));
+    }
+    dst[(size_t)cv * crop + w] = v;
   }
+}
+
+// Transfer function of the periodic separable blur on an n-point grid:
+// gain[i] = sum_a g[a] cos(2 pi f a / n) for the crop frequency f = i - crop/2
+// (the taps are even, so the transform is real).  The angle is reduced
+// exactly in integers before cospi.
+__global__ void k_blur_gain(ResistTaps taps, int n, int crop, float* __restrict__ gain) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= crop) return;
+  const int f = i - crop / 2, r = taps.radius;
+  float acc = taps.g[r];
+  for (int a = 1; a <= r; ++a) {
+    const long long e = ((long long)f * a % n + n) % n;  // f a mod n, in [0, n)
+    acc = fmaf(2.0f * taps.g[r + a], cospif(2.0f * float(e) / float(n)), acc);
+  }
+  gain[i] = acc;
 }
 
 // ---- stage 1: band multiply + inverse transform over v (stage1.cuh), FP32 output ------------------
@@ -102,7 +128,7 @@ template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const float2* __restrict__ t1, const float* __restrict__ lam,
                                                         int nk, int crop, float dose,
                                                         const float2* __restrict__ tw_g, float* __restrict__ img,
-                                                        long long t1_plane, long long img_plane, int lam_plane) {
+                                                        long long t1_plane, long long img_plane, int lam_period) {
   using PL = Plan<N>;
   constexpr int NT = PL::NT;
   constexpr int RL = PL::R[PL::P - 1];
@@ -113,7 +139,7 @@ __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const
   __syncthreads();
   const int y = blockIdx.x, plane = blockIdx.y, t = threadIdx.x, half = crop / 2;
   const float2* base = t1 + plane * t1_plane + (size_t)y * crop;
-  const float* lp = lam + plane * lam_plane;
+  const float* lp = lam + (plane % lam_period) * nk;  // planes repeat every lam_period (clips of a batch)
   float acc[PERL][RL];
 #pragma unroll
   for (int p = 0; p < PERL; ++p)
@@ -162,6 +188,40 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_real(const float2* __
   fft_load_use<N, +1>(buf, tw, threadIdx.x, load, use);
 }
 
+// Same transform for band rows carrying S (1 + i gain (x) gain) (see
+// k_mask_cols): the real part is the image, the imaginary part its blur, and
+// printed = [blur >= threshold].  `img` may be NULL (not written).
+template <int N>
+__global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_resist(const float2* __restrict__ q, int crop,
+                                                                  const float2* __restrict__ tw_g, float thr,
+                                                                  float* __restrict__ img, float* __restrict__ iblur,
+                                                                  uint8_t* __restrict__ printed) {
+  __shared__ float2 buf[PadLen<N>::value];
+  __shared__ float2 tw[N];
+  load_twiddles<N>(tw, tw_g);
+  __syncthreads();
+  const int y = blockIdx.x, p = blockIdx.y, half = crop / 2;
+  const float2* row = q + ((size_t)p * N + y) * crop;
+  auto load = [&](int idx) {
+    const int c = freq_of(idx, N) + half;
+    return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
+  };
+  const size_t o = ((size_t)p * N + y) * N;
+  auto use = [&](int, int, int x, float2 v) {
+    if (img) img[o + x] = v.x;
+    iblur[o + x] = v.y;
+    if (printed) printed[o + x] = v.y >= thr ? 1 : 0;
+  };
+  fft_load_use<N, +1>(buf, tw, threadIdx.x, load, use);
+}
+
+template <int N>
+cudaError_t band_rows_resist_n(const float2* q, int planes, int crop, const float2* tw, float thr, float* img,
+                               float* iblur, uint8_t* printed, cudaStream_t st) {
+  k_band_rows_resist<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed);
+  return cudaGetLastError();
+}
+
 template <int N>
 cudaError_t band_rows_real_n(const float2* q, int planes, int crop, float scale, const float2* tw, float* out,
                              cudaStream_t st) {
@@ -176,7 +236,7 @@ size_t col_smem_bytes() {
 
 template <int N>
 cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, float2* rowbuf, float2* mhat,
-                            cudaStream_t st) {
+                            const float* gain, cudaStream_t st) {
   const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
   cudaError_t e = smem_attrs(k_mask_rows<N>, smr);
   if (e != cudaSuccess) return e;
@@ -184,20 +244,21 @@ cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, f
   const size_t sm = col_smem_bytes<N>();
   e = smem_attrs(k_mask_cols<N>, sm);
   if (e != cudaSuccess) return e;
-  k_mask_cols<N><<<dim3(crop / ColW<N>::W, b), Plan<N>::NT * ColW<N>::W, sm, st>>>(rowbuf, crop, tw, mhat);
+  k_mask_cols<N><<<dim3(crop / ColW<N>::W, b), Plan<N>::NT * ColW<N>::W, sm, st>>>(rowbuf, crop, tw, gain, mhat);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t stage1_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, float2* t1,
-                     cudaStream_t st) {
-  return launch_stage1_cols<N, ColW<N>::W>(mhat, phi, nk, crop, tw, OutC64{t1, N, crop}, st);
+                     cudaStream_t st, int clips) {
+  return launch_stage1_cols<N, ColW<N>::W>(mhat, phi, nk, crop, tw, OutC64{t1, N, crop}, st, clips);
 }
 
 template <int N>
 cudaError_t stage2_n(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw, float* img,
-                     int planes, long long t1_plane, long long img_plane, cudaStream_t st) {
-  k_stage2<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(t1, lam, nk, crop, dose, tw, img, t1_plane, img_plane, nk);
+                     int planes, long long t1_plane, long long img_plane, int lam_period, cudaStream_t st) {
+  k_stage2<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(t1, lam, nk, crop, dose, tw, img, t1_plane, img_plane,
+                                                       lam_period);
   return cudaGetLastError();
 }
 
@@ -229,8 +290,8 @@ bool fft_twiddle_table(int n, float2* out) {
 }
 
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
-                                 float2* mhat, cudaStream_t st) {
-#define CALL(N) mask_spectrum_n<N>(m, b, crop, tw, rowbuf, mhat, st)
+                                 float2* mhat, cudaStream_t st, const float* gain) {
+#define CALL(N) mask_spectrum_n<N>(m, b, crop, tw, rowbuf, mhat, gain, st)
   LITHO_DISPATCH_N(n, CALL)
 #undef CALL
 }
@@ -242,17 +303,31 @@ cudaError_t launch_band_rows_real(const float2* q, int planes, int n, int crop, 
 #undef CALL
 }
 
+cudaError_t launch_blur_gain(const ResistTaps& taps, int n, int crop, float* gain, cudaStream_t st) {
+  if (n < 1 || crop < 1) return cudaErrorInvalidValue;
+  k_blur_gain<<<(crop + 127) / 128, 128, 0, st>>>(taps, n, crop, gain);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_band_rows_resist(const float2* q, int planes, int n, int crop, const float2* tw, float threshold,
+                                    float* img, float* iblur, uint8_t* printed, cudaStream_t st) {
+#define CALL(N) band_rows_resist_n<N>(q, planes, crop, tw, threshold, img, iblur, printed, st)
+  LITHO_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
 cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int n, int crop, const float2* tw,
-                              float2* t1, cudaStream_t st) {
-#define CALL(N) stage1_n<N>(mhat, phi, nk, crop, tw, t1, st)
+                              float2* t1, cudaStream_t st, int clips) {
+#define CALL(N) stage1_n<N>(mhat, phi, nk, crop, tw, t1, st, clips)
   LITHO_DISPATCH_N(n, CALL)
 #undef CALL
 }
 
 cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
-                              long long img_plane_stride, cudaStream_t st) {
-#define CALL(N) stage2_n<N>(t1, lam, nk, crop, dose, tw, img, planes, t1_plane_stride, img_plane_stride, st)
+                              long long img_plane_stride, cudaStream_t st, int lam_period) {
+  if (lam_period <= 0) lam_period = planes;
+#define CALL(N) stage2_n<N>(t1, lam, nk, crop, dose, tw, img, planes, t1_plane_stride, img_plane_stride, lam_period, st)
   LITHO_DISPATCH_N(n, CALL)
 #undef CALL
 }

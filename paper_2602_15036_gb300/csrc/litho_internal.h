@@ -39,6 +39,7 @@ enum Stage {
   kStageIltBackward,
   kStageIltReduce,
   kStageUpsample,
+  kStageUpsampleResist,
   kStageCount
 };
 // Records a CUDA event pair around its lifetime on `st` when profiling is on.
@@ -106,17 +107,22 @@ namespace litho {
 // The N-entry per-pass twiddle table the FFT kernels expect (false if n unsupported).
 bool fft_twiddle_table(int n, float2* out);
 // Mask spectrum: m[b][n][n] -> mhat[b][C][C] = N^-2 DFT(m) on the crop.  rowbuf: [b][n][C].
+// With `gain` [C] the stored value is mhat (1 + i gain[v] gain[u]) (blur channel, see fft.cu).
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
-                                 float2* mhat, cudaStream_t st);
+                                 float2* mhat, cudaStream_t st, const float* gain = nullptr);
 // Stage 1 (band multiply + inverse DFT over v): for kernels phi[nk][C][C],
 // t1[j][y][c] = sum_v mhat[v][c] phi_j[v][c] e^{+2 pi i v y/N}, j in [0, nk).
-// phi == NULL transforms nk spectra mhat[j][C][C] themselves.
+// phi == NULL transforms nk spectra mhat[j][C][C] themselves.  With kernels,
+// `clips` spectra mhat[clips][C][C] are imaged in one launch; clip i writes
+// t1[j + i nk].
 cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int n, int crop, const float2* tw,
-                              float2* t1, cudaStream_t st);
-// Stage 2 FFT path: I[y][x] (+)= dose * sum_j lam[j] |sum_c t1[j][y][c] e^{+2 pi i u_c x/N}|^2.
+                              float2* t1, cudaStream_t st, int clips = 1);
+// Stage 2 FFT path: I[y][x] = dose * sum_j lam[j] |sum_c t1[j][y][c] e^{+2 pi i u_c x/N}|^2
+// for each of `planes` planes; plane p takes lam[(p mod lam_period) nk ...]
+// (lam_period <= 0: planes, no repetition).
 cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
-                              long long img_plane_stride, cudaStream_t st);
+                              long long img_plane_stride, cudaStream_t st, int lam_period = 0);
 
 // Device address of the per-clip FP64 losses inside an ILT workspace (ilt.cu).
 double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes);
@@ -124,6 +130,14 @@ double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t w
 // out[p][y][x] = scale Re(sum_c q[p][y][c] e^{+2 pi i u_c x/N}) for band rows q[p][N][C].
 cudaError_t launch_band_rows_real(const float2* q, int planes, int n, int crop, float scale, const float2* tw,
                                   float* out, cudaStream_t st);
+
+struct ResistTaps;
+// gain[i] = sum_a g[a] cos(2 pi (i - crop/2) a / n): the blur's transfer function on the crop.
+cudaError_t launch_blur_gain(const ResistTaps& taps, int n, int crop, float* gain, cudaStream_t st);
+// Band rows carrying the blur channel: z = sum_c q[p][y][c] e^{+2 pi i u_c x/N};
+// img = Re z (skipped when NULL), iblur = Im z, printed = [Im z >= threshold] (skipped when NULL).
+cudaError_t launch_band_rows_resist(const float2* q, int planes, int n, int crop, const float2* tw, float threshold,
+                                    float* img, float* iblur, uint8_t* printed, cudaStream_t st);
 
 // ---- resist (resist.cu) ---------------------------------------------------------------------
 constexpr int kMaxResistRadius = 64;

@@ -9,6 +9,11 @@
 // Without kernels (phi == NULL) each j transforms its own spectrum mhat[j].
 // The output policy `Out` stores element (j, y, c): FP32 complex for the FFT
 // path, split 16-bit hi/lo rows for the tensor-core path.
+//
+// With kernels, one launch can image several clips (grid x = clip, the
+// fastest-varying block index): the CTAs of all clips that need the same Phi
+// block run side by side, so each block comes from DRAM once and from L2
+// for the other clips.  Clip i writes j + i nk.
 #pragma once
 
 #include "fft_common.cuh"
@@ -45,9 +50,10 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
   float2* const blk0 = buf + W * LD;  // Phi (or spectrum) blocks, double-buffered: blk0 + s W bld
   auto blk = [&](int s) { return blk0 + s * W * bld; };
   float2* msk = buf + W * LD + 2 * W * bld;                 // mask-spectrum block (with kernels)
-  const int tid = threadIdx.x, u0 = blockIdx.x * W, half = crop / 2;
-  const int j0 = blockIdx.y * jb, j1 = min(nk, j0 + jb);
+  const int tid = threadIdx.x, u0 = blockIdx.y * W, half = crop / 2;
+  const int j0 = blockIdx.z * jb, j1 = min(nk, j0 + jb), jofs = blockIdx.x * nk;
   if (j0 >= j1) return;
+  mhat += (size_t)blockIdx.x * crop * crop;
   load_twiddles<N>(tw, tw_g);
   const float2* src_base = phi ? phi : mhat;  // the per-j operand
   auto issue = [&](int j, float2* dst) {
@@ -89,29 +95,31 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
         float2 v[W];
 #pragma unroll
         for (int w = 0; w < W; ++w) v[w] = buf[w * LD + pad16(y)];
-        out.template store_row<W>(j, y, u0, v);
+        out.template store_row<W>(jofs + j, y, u0, v);
       }
     } else {
       // consecutive threads write consecutive columns of a row (full sectors per warp)
       for (int i = tid; i < N * W; i += T) {
         const int y = i / W, w = i % W;
-        out.store(j, y, u0 + w, buf[w * LD + pad16(y)]);
+        out.store(jofs + j, y, u0 + w, buf[w * LD + pad16(y)]);
       }
     }
     __syncthreads();  // copy-out done before the next transform overwrites buf
   }
 }
 
-// W columns per CTA (a divisor of 32; crop is a multiple of 32).
+// W columns per CTA (a divisor of 32; crop is a multiple of 32).  `clips`
+// spectra mhat[clips][C][C] share the kernels (clips must be 1 without them).
 template <int N, int W, class Out>
 cudaError_t launch_stage1_cols(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, Out out,
-                               cudaStream_t st) {
+                               cudaStream_t st, int clips = 1) {
+  if (clips < 1 || (!phi && clips != 1)) return cudaErrorInvalidValue;
   constexpr int JB = 8;
   const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop);
   cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out>, sm);
   if (e != cudaSuccess) return e;
-  k_stage1_cols<N, W, Out><<<dim3(crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(mhat, phi, crop, nk,
-                                                                                             JB, tw, out);
+  k_stage1_cols<N, W, Out><<<dim3(clips, crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(
+      mhat, phi, crop, nk, JB, tw, out);
   return cudaGetLastError();
 }
 

@@ -75,6 +75,8 @@ _SIGS = {
     "litho_free_kernels": (None, [c_void_p]),
     "litho_aerial_workspace_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
     "litho_aerial": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "litho_aerial_resist": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_double, c_double,
+                                    c_void_p, c_void_p, c_void_p, c_size_t, c_void_p]),
     "litho_aerial_host_workspace_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
     "litho_aerial_host": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_double, c_double,
                                   c_void_p, c_void_p, c_size_t, c_void_p]),
@@ -237,6 +239,29 @@ def litho_aerial(kern: Kernels, mask, dose=1.0, precision="fft32", out=None, wor
                               c_void_p(out.data_ptr()), c_void_p(workspace.data_ptr()), workspace.numel(),
                               _stream_ptr(stream)))
     return out
+
+
+def litho_aerial_resist(kern: Kernels, mask, dose=1.0, precision="fft32", sigma_nm=10.0, threshold=0.3, out=None,
+                        iblur=None, printed=None, want_printed=True, workspace=None, stream=None):
+    """mask: torch float32 CUDA tensor [b][n][n] -> (intensity, iblur, printed u8 or None), each [b][F][n][n]."""
+    import torch
+    assert mask.is_cuda and mask.dtype == torch.float32 and mask.is_contiguous()
+    b = mask.shape[0]
+    shape = (b, kern.n_focus, kern.n, kern.n)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=mask.device)
+    if iblur is None:
+        iblur = torch.empty(shape, dtype=torch.float32, device=mask.device)
+    if printed is None and want_printed:
+        printed = torch.empty(shape, dtype=torch.uint8, device=mask.device)
+    if workspace is None:
+        workspace = torch.empty(litho_aerial_workspace_size(kern, b, precision), dtype=torch.uint8,
+                                device=mask.device)
+    _check(lib().litho_aerial_resist(kern.handle, c_void_p(mask.data_ptr()), b, dose, prec_code(precision),
+                                     c_void_p(out.data_ptr()), sigma_nm, threshold, c_void_p(iblur.data_ptr()),
+                                     c_void_p(printed.data_ptr()) if printed is not None else None,
+                                     c_void_p(workspace.data_ptr()), workspace.numel(), _stream_ptr(stream)))
+    return out, iblur, printed
 
 
 def litho_aerial_host_workspace_size(kern: Kernels, b: int, precision="fft32") -> int:

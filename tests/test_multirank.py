@@ -55,7 +55,19 @@ def test_stage_models_are_consistent():
     peaks = {"hbm_gbs": 6785.5, "bf16_tflops_sustained": 1709.2}
     m = bench.stage_models("fp16x3/coarse", 64, 2048, 448, 3, 24, 1024, peaks)
     # 8 N'^2 C flops per kernel and plane, three products for the split operands
-    assert m["stage2_gemm"][1] == pytest.approx(64 * 3 * 24 * 8.0 * 1024 ** 2 * 448 * 3)
-    assert m["resist"][0] == "hbm" and "upsample" in m
+    assert m["stage2_gemm"][0] == pytest.approx(64 * 3 * 24 * 8.0 * 1024 ** 2 * 448 * 3)
+    # resist: 9 bytes per pixel and plane (f32 in, f32 blur and u8 printed out)
+    assert m["resist"][1] == pytest.approx(64 * 3 * 2048 ** 2 * 9.0)
+    assert "upsample" in m and "upsample_resist" in m
     m2 = bench.stage_models("fft32", 64, 2048, 448, 3, 24, 1024, peaks)
     assert "upsample" not in m2
+    # FP32 stage 1 on the coarse grid: 8 clips per launch, so Phi is read 8 times per 64 clips
+    m3 = bench.stage_models("fft32/coarse", 64, 2048, 448, 3, 24, 1024, peaks)
+    assert bench.fft_group(64, 3, 24, 1024, 448) == 8
+    phi, t1 = 72 * 448 ** 2 * 8.0, 64 * 72 * 1024 * 448 * 8.0
+    assert m3["stage1_fft"][1] == pytest.approx(8 * phi + 64 * 448 ** 2 * 8.0 + t1)
+    assert m3["stage2_fft"][1] == pytest.approx(t1 + 64 * 3 * 1024 ** 2 * 4.0)
+    # roofline: the binding resource is the one with the longer time at peak
+    r = bench.rooflines({"stage1_fft": (10.0, 8), "stage2_fft": (10.0, 8)}, 1, m3, peaks)
+    assert r["stage1_fft"]["bound"] == "hbm" and r["stage2_fft"]["bound"] == "alu"
+    assert r["stage1_fft"]["achieved"] == pytest.approx(m3["stage1_fft"][1] / 1e-2 / 1e9)
