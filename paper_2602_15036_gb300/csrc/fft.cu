@@ -124,7 +124,7 @@ struct OutC64 {
 };
 
 // ---- stage 2 (FP32 path): one image row per CTA, all kernels of the plane ------------------------
-template <int N>
+template <int N, bool BANDED>
 __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const float2* __restrict__ t1, const float* __restrict__ lam,
                                                         int nk, int crop, float dose,
                                                         const float2* __restrict__ tw_g, float* __restrict__ img,
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const
       return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
     };
     auto use = [&](int p, int q, int, float2 v) { acc[p][q] = fmaf(l, fmaf(v.x, v.x, v.y * v.y), acc[p][q]); };
-    fft_load_use<N, +1>(buf, tw, t, load, use);
+    fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, t, load, use);
   }
   float* out = img + plane * img_plane + (size_t)y * N;
 #pragma unroll
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const
 
 // ---- band rows to real image rows: out[p][y][x] = scale Re(sum_c q[p][y][c] e^{2 pi i u_c x/N}) ----------
 // Second half of the exact Fourier interpolation from the coarse grid.
-template <int N>
+template <int N, bool BANDED>
 __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_real(const float2* __restrict__ q, int crop, float scale,
                                                                 const float2* __restrict__ tw_g,
                                                                 float* __restrict__ out) {
@@ -185,13 +185,13 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_real(const float2* __
   };
   float* o = out + ((size_t)p * N + y) * N;
   auto use = [&](int, int, int x, float2 v) { o[x] = scale * v.x; };
-  fft_load_use<N, +1>(buf, tw, threadIdx.x, load, use);
+  fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, threadIdx.x, load, use);
 }
 
 // Same transform for band rows carrying S (1 + i gain (x) gain) (see
 // k_mask_cols): the real part is the image, the imaginary part its blur, and
 // printed = [blur >= threshold].  `img` may be NULL (not written).
-template <int N>
+template <int N, bool BANDED>
 __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_resist(const float2* __restrict__ q, int crop,
                                                                   const float2* __restrict__ tw_g, float thr,
                                                                   float* __restrict__ img, float* __restrict__ iblur,
@@ -212,20 +212,26 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_resist(const float2* 
     iblur[o + x] = v.y;
     if (printed) printed[o + x] = v.y >= thr ? 1 : 0;
   };
-  fft_load_use<N, +1>(buf, tw, threadIdx.x, load, use);
+  fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, threadIdx.x, load, use);
 }
 
 template <int N>
 cudaError_t band_rows_resist_n(const float2* q, int planes, int crop, const float2* tw, float thr, float* img,
                                float* iblur, uint8_t* printed, cudaStream_t st) {
-  k_band_rows_resist<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed);
+  if (2 * crop <= N)
+    k_band_rows_resist<N, true><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed);
+  else
+    k_band_rows_resist<N, false><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t band_rows_real_n(const float2* q, int planes, int crop, float scale, const float2* tw, float* out,
                              cudaStream_t st) {
-  k_band_rows_real<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out);
+  if (2 * crop <= N)
+    k_band_rows_real<N, true><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out);
+  else
+    k_band_rows_real<N, false><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out);
   return cudaGetLastError();
 }
 
@@ -257,8 +263,12 @@ cudaError_t stage1_n(const float2* mhat, const float2* phi, int nk, int crop, co
 template <int N>
 cudaError_t stage2_n(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw, float* img,
                      int planes, long long t1_plane, long long img_plane, int lam_period, cudaStream_t st) {
-  k_stage2<N><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(t1, lam, nk, crop, dose, tw, img, t1_plane, img_plane,
-                                                       lam_period);
+  if (2 * crop <= N)
+    k_stage2<N, true><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(t1, lam, nk, crop, dose, tw, img, t1_plane,
+                                                               img_plane, lam_period);
+  else
+    k_stage2<N, false><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(t1, lam, nk, crop, dose, tw, img, t1_plane,
+                                                                img_plane, lam_period);
   return cudaGetLastError();
 }
 

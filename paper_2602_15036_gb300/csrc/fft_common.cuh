@@ -67,18 +67,33 @@ __host__ __device__ __forceinline__ constexpr int bitrev(int q, int bits) {
 }
 
 // In-register R-point DFT, v'[q] = sum_r v[r] e^{SIGN 2 pi i r q / R}.
-template <int R, int SIGN>
+// BANDED: only v[r] with r < R/4 or r >= 3R/4 may be nonzero and the others
+// are not read, so the first radix-2 layer reduces to copies, negations and
+// twiddles.  A first pass (stride N/R) over a spectrum whose nonzero entries
+// lie in the lowest and highest quarter of the indices has this form.
+template <int R, int SIGN, bool BANDED = false>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
   static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
+  static_assert(!BANDED || R >= 4, "banded input needs R >= 4");
 #pragma unroll
   for (int span = R / 2; span >= 1; span /= 2) {
 #pragma unroll
     for (int b = 0; b < R; b += 2 * span) {
 #pragma unroll
       for (int i = 0; i < span; ++i) {
-        const float2 a = v[b + i], c = v[b + i + span];
-        v[b + i] = cadd(a, c);
-        float2 d = csub(a, c);
+        float2 d;
+        if (BANDED && span == R / 2) {
+          if (i < R / 4) {
+            d = v[i];  // v[i + span] is zero
+          } else {     // v[i] is zero
+            v[i] = v[i + span];
+            d = make_float2(-v[i].x, -v[i].y);
+          }
+        } else {
+          const float2 a = v[b + i], c = v[b + i + span];
+          v[b + i] = cadd(a, c);
+          d = csub(a, c);
+        }
         const int t = i * (16 / (2 * span));  // e^{SIGN 2 pi i i/(2 span)} = e^{SIGN 2 pi i t/16}
         if (t != 0) {
           const float wr = cos16(t), wi = SIGN * sin16(t);
@@ -124,7 +139,7 @@ struct TwOff {
 };
 
 // Twiddle + DFT of one butterfly's R values.
-template <int N, int R, int NS, int SIGN, int OFF>
+template <int N, int R, int NS, int SIGN, int OFF, bool BANDED = false>
 __device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2* __restrict__ tw) {
   if (NS > 1) {
     const int k = j % NS;
@@ -135,22 +150,31 @@ __device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2*
       v[r] = cmul(v[r], w);
     }
   }
-  dft_reg<R, SIGN>(v);
+  dft_reg<R, SIGN, BANDED>(v);
 }
 
 // One pass whose inputs come from `load(index)` (or shared memory when
 // FROM_SMEM) and whose outputs go to shared memory.  Ends with a barrier.
-template <int N, int NT, int R, int NS, int SIGN, int OFF, bool FROM_SMEM, class Load>
+// BANDED (first pass only): indices in [N/4, 3N/4) are known to be zero and
+// are neither loaded nor added.
+template <int N, int NT, int R, int NS, int SIGN, int OFF, bool FROM_SMEM, class Load, bool BANDED = false>
 __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int t, Load& load) {
   using S = PassShape<N, NT, R>;
+  static_assert(!BANDED || NS == 1, "banded input applies to the first pass");
   float2 v[S::PER][R];
 #pragma unroll
   for (int p = 0; p < S::PER; ++p) {
     const int j = t + p * NT;
     if (j < S::NB) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[p][r] = FROM_SMEM ? buf[pad16(j + r * S::NB)] : load(j + r * S::NB);
-      twiddle_dft<N, R, NS, SIGN, OFF>(v[p], j, tw);
+      for (int r = 0; r < R; ++r) {
+        if (BANDED && r >= R / 4 && r < 3 * R / 4) {
+          v[p][r] = make_float2(0.f, 0.f);  // never read
+        } else {
+          v[p][r] = FROM_SMEM ? buf[pad16(j + r * S::NB)] : load(j + r * S::NB);
+        }
+      }
+      twiddle_dft<N, R, NS, SIGN, OFF, BANDED>(v[p], j, tw);
     }
   }
   __syncthreads();
@@ -196,15 +220,15 @@ struct SmemLoadUnused {
 // Full transform: first pass from `load`, middle passes in shared memory,
 // last pass into `use`.  Threads t in [0, NT) of the calling group take part;
 // every thread of the block must call it (it contains __syncthreads).
-template <int N, int SIGN, class Load, class Use>
+template <int N, int SIGN, class Load, class Use, bool BANDED = false>
 __device__ __forceinline__ void fft_load_use(float2* buf, const float2* tw, int t, Load& load, Use& use) {
   using PL = Plan<N>;
   constexpr int NT = PL::NT;
   if constexpr (PL::P == 2) {
-    pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false>(buf, tw, t, load);
+    pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false, Load, BANDED>(buf, tw, t, load);
     pass_last<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1>(buf, tw, t, use);
   } else {
-    pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false>(buf, tw, t, load);
+    pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false, Load, BANDED>(buf, tw, t, load);
     SmemLoadUnused none;
     pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
     pass_last<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, TwOff<N>::p2>(buf, tw, t, use);
@@ -229,12 +253,12 @@ __device__ __forceinline__ void fft_smem(float2* buf, const float2* tw, int t) {
 
 // Full transform with the first pass from `load` and every pass's output in
 // shared memory (padded layout, natural order on return).  Ends with a barrier.
-template <int N, int SIGN, class Load>
+template <int N, int SIGN, class Load, bool BANDED = false>
 __device__ __forceinline__ void fft_load_smem(float2* buf, const float2* tw, int t, Load& load) {
   using PL = Plan<N>;
   constexpr int NT = PL::NT;
   SmemLoadUnused none;
-  pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false>(buf, tw, t, load);
+  pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false, Load, BANDED>(buf, tw, t, load);
   if constexpr (PL::P == 2) {
     pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
   } else {

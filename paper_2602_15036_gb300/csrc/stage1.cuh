@@ -38,7 +38,7 @@ struct Stage1Shape {
   static size_t smem_elems(int crop) { return size_t(N) + size_t(W) * LD + 3 * size_t(W) * bld(crop); }
 };
 
-template <int N, int W, class Out>
+template <int N, int W, class Out, bool BANDED>
 __global__ void __launch_bounds__(Plan<N>::NT * W)
     k_stage1_cols(const float2* __restrict__ mhat, const float2* __restrict__ phi, int crop, int nk, int jb,
                   const float2* __restrict__ tw_g, Out out) {
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
       if (c < 0 || c >= crop) return make_float2(0.f, 0.f);
       return phi ? cmul(m[c], b[c]) : b[c];
     };
-    fft_load_smem<N, +1>(buf + g * LD, tw, t, load);
+    fft_load_smem<N, +1, decltype(load), BANDED>(buf + g * LD, tw, t, load);
     if constexpr (Out::kRowWise) {
       // one thread per output row writes the block's W consecutive columns
       for (int y = tid; y < N; y += T) {
@@ -108,19 +108,27 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
   }
 }
 
+template <int N, int W, class Out, bool BANDED>
+cudaError_t launch_stage1_cols_t(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, Out out,
+                                 cudaStream_t st, int clips) {
+  constexpr int JB = 8;
+  const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop);
+  cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out, BANDED>, sm);
+  if (e != cudaSuccess) return e;
+  k_stage1_cols<N, W, Out, BANDED><<<dim3(clips, crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(
+      mhat, phi, crop, nk, JB, tw, out);
+  return cudaGetLastError();
+}
+
 // W columns per CTA (a divisor of 32; crop is a multiple of 32).  `clips`
 // spectra mhat[clips][C][C] share the kernels (clips must be 1 without them).
+// A crop of at most N/2 takes the banded first pass.
 template <int N, int W, class Out>
 cudaError_t launch_stage1_cols(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, Out out,
                                cudaStream_t st, int clips = 1) {
   if (clips < 1 || (!phi && clips != 1)) return cudaErrorInvalidValue;
-  constexpr int JB = 8;
-  const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop);
-  cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out>, sm);
-  if (e != cudaSuccess) return e;
-  k_stage1_cols<N, W, Out><<<dim3(clips, crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(
-      mhat, phi, crop, nk, JB, tw, out);
-  return cudaGetLastError();
+  if (2 * crop <= N) return launch_stage1_cols_t<N, W, Out, true>(mhat, phi, nk, crop, tw, out, st, clips);
+  return launch_stage1_cols_t<N, W, Out, false>(mhat, phi, nk, crop, tw, out, st, clips);
 }
 
 }  // namespace litho
