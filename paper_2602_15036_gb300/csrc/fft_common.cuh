@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <type_traits>
 
 namespace litho {
 
@@ -155,8 +156,10 @@ __device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2*
 
 // One pass whose inputs come from `load(index)` (or shared memory when
 // FROM_SMEM) and whose outputs go to shared memory.  Ends with a barrier.
-// BANDED (first pass only): indices in [N/4, 3N/4) are known to be zero and
-// are neither loaded nor added.
+// A loader that also takes (p, r, index) gets the butterfly slot p and the
+// element r (compile-time after unrolling), so it can keep per-element
+// operands in registers.  BANDED (first pass only): indices in [N/4, 3N/4)
+// are known to be zero and are neither loaded nor added.
 template <int N, int NT, int R, int NS, int SIGN, int OFF, bool FROM_SMEM, class Load, bool BANDED = false>
 __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int t, Load& load) {
   using S = PassShape<N, NT, R>;
@@ -171,7 +174,13 @@ __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int 
         if (BANDED && r >= R / 4 && r < 3 * R / 4) {
           v[p][r] = make_float2(0.f, 0.f);  // never read
         } else {
-          v[p][r] = FROM_SMEM ? buf[pad16(j + r * S::NB)] : load(j + r * S::NB);
+          if constexpr (FROM_SMEM) {
+            v[p][r] = buf[pad16(j + r * S::NB)];
+          } else if constexpr (std::is_invocable_v<Load&, int, int, int>) {
+            v[p][r] = load(p, r, j + r * S::NB);
+          } else {
+            v[p][r] = load(j + r * S::NB);
+          }
         }
       }
       twiddle_dft<N, R, NS, SIGN, OFF, BANDED>(v[p], j, tw);

@@ -2,13 +2,19 @@
 // transform over the y frequency, T_j[y][c] = sum_v mhat[v][c] Phi_j[v][c] e^{+2 pi i v y/N},
 // for a block of W crop columns c and a run of kernels j.
 //
-// A CTA keeps its column block of the mask spectrum and the twiddle table in
-// shared memory and loops over JB kernels; the next kernel's Phi block is
-// copied in with cp.async (two buffers) while the current block's W column
-// transforms run, and the band multiply happens inside the first pass's load.
+// A CTA keeps the twiddle table in shared memory and loops over JB kernels;
+// the next kernel's Phi block is copied in with cp.async (two buffers) while
+// the current block's W column transforms run.  The band multiply happens in
+// the first pass's load: the mask-spectrum values a thread multiplies are
+// the same for every kernel, so they are loaded once into registers.
 // Without kernels (phi == NULL) each j transforms its own spectrum mhat[j].
-// The output policy `Out` stores element (j, y, c): FP32 complex for the FFT
-// path, split 16-bit hi/lo rows for the tensor-core path.
+//
+// Thread layout: column w = tid mod W, transform thread t = tid / W, so a
+// warp holds 32/W consecutive t of all W columns.  In the last pass a warp's
+// outputs for one element are then 32/W rows x W adjacent columns: whole
+// 32-byte sectors for W = 4, stored straight from registers (FP32 output).
+// The split 16-bit output for the tensor-core path packs a row's W columns
+// in one thread and goes through shared memory.
 //
 // With kernels, one launch can image several clips (grid x = clip, the
 // fastest-varying block index): the CTAs of all clips that need the same Phi
@@ -35,7 +41,7 @@ template <int N, int W>
 struct Stage1Shape {
   static constexpr int LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
   static int bld(int crop) { return crop + 16 / W; }
-  static size_t smem_elems(int crop) { return size_t(N) + size_t(W) * LD + 3 * size_t(W) * bld(crop); }
+  static size_t smem_elems(int crop) { return size_t(N) + size_t(W) * LD + 2 * size_t(W) * bld(crop); }
 };
 
 template <int N, int W, class Out, bool BANDED>
@@ -43,13 +49,14 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     k_stage1_cols(const float2* __restrict__ mhat, const float2* __restrict__ phi, int crop, int nk, int jb,
                   const float2* __restrict__ tw_g, Out out) {
   constexpr int NT = Plan<N>::NT, LD = Stage1Shape<N, W>::LD, T = W * NT;
+  constexpr int R0 = Plan<N>::R[0], NB0 = N / R0;  // first pass: radix and butterflies
+  static_assert(PassShape<N, NT, R0>::PER == 1, "one first-pass butterfly per thread");
   extern __shared__ float2 smem[];
   const int bld = crop + 16 / W;
   float2* tw = smem;
   float2* buf = smem + N;
   float2* const blk0 = buf + W * LD;  // Phi (or spectrum) blocks, double-buffered: blk0 + s W bld
   auto blk = [&](int s) { return blk0 + s * W * bld; };
-  float2* msk = buf + W * LD + 2 * W * bld;                 // mask-spectrum block (with kernels)
   const int tid = threadIdx.x, u0 = blockIdx.y * W, half = crop / 2;
   const int j0 = blockIdx.z * jb, j1 = min(nk, j0 + jb), jofs = blockIdx.x * nk;
   if (j0 >= j1) return;
@@ -64,14 +71,16 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     }
     cp_async_commit();
   };
-  if (phi) {
-    for (int i = tid; i < crop * W; i += T) {
-      const int cv = i / W, w = i % W;
-      msk[w * bld + cv] = __ldg(mhat + (size_t)cv * crop + u0 + w);
-    }
-  }
   issue(j0, blk(0));
-  const int g = tid / NT, t = tid % NT;
+  const int g = tid % W, t = tid / W;
+  auto band_row = [&](int idx) { return (idx < N / 2 ? idx : idx - N) + half; };  // crop row of index idx
+  float2 mreg[R0];  // mask spectrum at this thread's first-pass inputs (column u0 + g)
+#pragma unroll
+  for (int r = 0; r < R0; ++r) {
+    const int c = band_row(t + r * NB0);
+    const bool zero = !phi || t >= NB0 || c < 0 || c >= crop || (BANDED && r >= R0 / 4 && r < 3 * R0 / 4);
+    mreg[r] = zero ? make_float2(0.f, 0.f) : __ldg(mhat + (size_t)c * crop + u0 + g);
+  }
   for (int j = j0; j < j1; ++j) {
     const int s = (j - j0) & 1;
     if (j + 1 < j1) {
@@ -80,16 +89,17 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     } else {
       cp_async_wait_all();
     }
-    __syncthreads();  // block j (and, first time round, msk and tw) visible to all threads
+    // Block j (and, first time round, tw) visible to all threads; every thread
+    // has finished transform j - 1, so buf and the other Phi buffer are free.
+    __syncthreads();
     const float2* b = blk(s) + g * bld;
-    const float2* m = msk + g * bld;
-    auto load = [&](int idx) {
-      const int c = (idx < N / 2 ? idx : idx - N) + half;
+    auto load = [&](int, int r, int idx) {
+      const int c = band_row(idx);
       if (c < 0 || c >= crop) return make_float2(0.f, 0.f);
-      return phi ? cmul(m[c], b[c]) : b[c];
+      return phi ? cmul(mreg[r], b[c]) : b[c];
     };
-    fft_load_smem<N, +1, decltype(load), BANDED>(buf + g * LD, tw, t, load);
     if constexpr (Out::kRowWise) {
+      fft_load_smem<N, +1, decltype(load), BANDED>(buf + g * LD, tw, t, load);
       // one thread per output row writes the block's W consecutive columns
       for (int y = tid; y < N; y += T) {
         float2 v[W];
@@ -98,13 +108,9 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
         out.template store_row<W>(jofs + j, y, u0, v);
       }
     } else {
-      // consecutive threads write consecutive columns of a row (full sectors per warp)
-      for (int i = tid; i < N * W; i += T) {
-        const int y = i / W, w = i % W;
-        out.store(jofs + j, y, u0 + w, buf[w * LD + pad16(y)]);
-      }
+      auto use = [&](int, int, int y, float2 v) { out.store(jofs + j, y, u0 + g, v); };
+      fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf + g * LD, tw, t, load, use);
     }
-    __syncthreads();  // copy-out done before the next transform overwrites buf
   }
 }
 
