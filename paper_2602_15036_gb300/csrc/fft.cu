@@ -116,9 +116,7 @@ struct OutC64 {
   static constexpr bool kRowWise = false;
   float2* t1;
   int n, crop;
-  __device__ __forceinline__ void store(int j, int y, int c, float2 v) const {
-    t1[((size_t)j * n + y) * crop + c] = v;
-  }
+  __device__ __forceinline__ float2* column(int j, int c) const { return t1 + (size_t)j * n * crop + c; }
   template <int W>
   __device__ void store_row(int, int, int, const float2 (&)[W]) const {}
 };

@@ -403,7 +403,7 @@ __device__ __forceinline__ void split16(float x, float scale, uint32_t& h, uint3
 template <int MODE>
 struct OutSplit {
   static constexpr bool kRowWise = true;
-  __device__ void store(int, int, int, float2) const {}
+  __device__ float2* column(int, int) const { return nullptr; }
   void* hi;
   void* lo;
   const float* scales;

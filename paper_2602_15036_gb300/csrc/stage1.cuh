@@ -26,22 +26,25 @@
 
 namespace litho {
 
-__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+__device__ __forceinline__ void cp_async16_cg(void* smem_dst, const void* gmem_src) {
   const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// Strides for a block of W columns: each column's padded transform, rounded
-// up to 16 complex values plus 16/W, and the compact band buffers crop + 16/W,
-// so that the cooperative copies (w fastest) hit 16 different bank pairs.
+// Shared memory of a CTA: the twiddle table, W column transforms at stride LD
+// (the padded length rounded up to 16 complex values plus 16/W, so that a
+// half-warp of 16/W transform threads x W columns touches 16 different bank
+// pairs) and two operand blocks [crop][W] in the operand's own row-major
+// order (a row's W values are one or more whole 16-byte copies; a half-warp
+// reading rows c..c+16/W-1 of all W columns again hits 16 bank pairs).
 template <int N, int W>
 struct Stage1Shape {
+  static_assert(W % 2 == 0, "W even: rows of whole 16-byte pieces");
   static constexpr int LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
-  static int bld(int crop) { return crop + 16 / W; }
-  static size_t smem_elems(int crop) { return size_t(N) + size_t(W) * LD + 2 * size_t(W) * bld(crop); }
+  static size_t smem_elems(int crop) { return size_t(N) + size_t(W) * LD + 2 * size_t(W) * crop; }
 };
 
 template <int N, int W, class Out, bool BANDED>
@@ -51,23 +54,23 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
   constexpr int NT = Plan<N>::NT, LD = Stage1Shape<N, W>::LD, T = W * NT;
   constexpr int R0 = Plan<N>::R[0], NB0 = N / R0;  // first pass: radix and butterflies
   static_assert(PassShape<N, NT, R0>::PER == 1, "one first-pass butterfly per thread");
-  extern __shared__ float2 smem[];
-  const int bld = crop + 16 / W;
+  extern __shared__ float4 smem_raw[];
+  float2* smem = reinterpret_cast<float2*>(smem_raw);
   float2* tw = smem;
   float2* buf = smem + N;
-  float2* const blk0 = buf + W * LD;  // Phi (or spectrum) blocks, double-buffered: blk0 + s W bld
-  auto blk = [&](int s) { return blk0 + s * W * bld; };
+  float2* const blk0 = buf + W * LD;  // Phi (or spectrum) blocks [crop][W], double-buffered
+  auto blk = [&](int s) { return blk0 + s * W * crop; };
   const int tid = threadIdx.x, u0 = blockIdx.y * W, half = crop / 2;
   const int j0 = blockIdx.z * jb, j1 = min(nk, j0 + jb), jofs = blockIdx.x * nk;
   if (j0 >= j1) return;
   mhat += (size_t)blockIdx.x * crop * crop;
   load_twiddles<N>(tw, tw_g);
   const float2* src_base = phi ? phi : mhat;  // the per-j operand
-  auto issue = [&](int j, float2* dst) {
+  auto issue = [&](int j, float2* dst) {  // W/2 16-byte pieces per row
     const float2* src = src_base + (size_t)j * crop * crop + u0;
-    for (int i = tid; i < crop * W; i += T) {
-      const int cv = i / W, w = i % W;
-      cp_async8(dst + w * bld + cv, src + (size_t)cv * crop + w);
+    for (int i = tid; i < crop * (W / 2); i += T) {
+      const int cv = i / (W / 2), part = i % (W / 2);
+      cp_async16_cg(dst + 2 * i, src + (size_t)cv * crop + 2 * part);
     }
     cp_async_commit();
   };
@@ -92,11 +95,11 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     // Block j (and, first time round, tw) visible to all threads; every thread
     // has finished transform j - 1, so buf and the other Phi buffer are free.
     __syncthreads();
-    const float2* b = blk(s) + g * bld;
+    const float2* b = blk(s) + g;
     auto load = [&](int, int r, int idx) {
       const int c = band_row(idx);
       if (c < 0 || c >= crop) return make_float2(0.f, 0.f);
-      return phi ? cmul(mreg[r], b[c]) : b[c];
+      return phi ? cmul(mreg[r], b[c * W]) : b[c * W];
     };
     if constexpr (Out::kRowWise) {
       fft_load_smem<N, +1, decltype(load), BANDED>(buf + g * LD, tw, t, load);
@@ -108,7 +111,8 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
         out.template store_row<W>(jofs + j, y, u0, v);
       }
     } else {
-      auto use = [&](int, int, int y, float2 v) { out.store(jofs + j, y, u0 + g, v); };
+      float2* const col = out.column(jofs + j, u0 + g);  // element y at col[y crop]
+      auto use = [&](int, int, int y, float2 v) { col[y * crop] = v; };
       fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf + g * LD, tw, t, load, use);
     }
   }
