@@ -368,11 +368,7 @@ def run_aerial(args):
     kern = P.litho_make_kernels(P.make_optics(**OPTICS), N, PIXEL, FOCUS, K)
     info = kern.info()
     k_eff = min(K, min(info["rank"]))
-    nc = 0
     c = kern.crop
-    while nc < 2 * c:
-        nc = 32 if nc == 0 else 2 * nc
-    nc = nc if nc < N else 0
     masks_np = np.stack([synth.manhattan_mask(N, seed=s) for s in clip_seeds(ctx.rank, clips)])
     masks = torch.from_numpy(masks_np).to(ctx.dev)
     F = len(FOCUS)
@@ -402,7 +398,7 @@ def run_aerial(args):
         L.litho_profile_enable(False)
         total_ms = ctx.max_over_ranks(sum(step_ms))
         value = whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total_ms * 1e-3])
-        models = stage_models(prec, clips, N, c, F, k_eff, nc, peaks)
+        models = stage_models(prec, clips, N, c, F, k_eff, kern.grid(prec), peaks)
         roofs = rooflines(prof, args.steps, models, peaks)
         results[prec] = dict(value=value, step_ms=step_ms, total_ms=total_ms, clocks=clk, prof=prof, roofs=roofs,
                              launches=sum(v[1] for v in prof.values()))

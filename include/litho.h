@@ -82,7 +82,8 @@ typedef enum {
   LITHO_PREC_FP16 = 4    /* tcgen05 DFT-GEMM, fp16 operands (scaled), FP32 accumulation */
 } litho_precision;
 /* OR-ed into a precision: evaluate the coherent fields on the coarse grid
- * nc x nc, nc the smallest power of two >= 2C, and interpolate I to N x N
+ * nc x nc, nc >= 2C (litho_kernels_grid: the smallest power of two, or 896 =
+ * 16 x 8 x 7 for the tensor-core path), and interpolate I to N x N
  * exactly (I = sum_k lam_k |E_k|^2 has no frequency at or beyond C along
  * either axis, so nc >= 2C samples determine it; the interpolation is a
  * forward transform on nc and an inverse transform on N).  Ignored when
@@ -128,6 +129,14 @@ litho_status litho_upload_kernels(int n, double pixel_nm, int n_focus, int k, in
  * below 1e-12 * lam_1 means the cut at k splits a degenerate cluster. */
 litho_status litho_kernels_info(const litho_kernels* h, int* n, int* crop, int* n_focus, int* k, int* rank_host,
                                 double* lambda_host, double* trace_host, double* gap_host);
+
+/* The coarse evaluation grids LITHO_GRID_COARSE uses (the image has no
+ * frequency at or beyond crop, so 2 crop samples per axis determine it
+ * exactly): *nc_fft for LITHO_PREC_FFT32, the smallest power of two >= 2 crop;
+ * *nc_tensor for the tensor-core precisions, the same or 896 = 16 x 8 x 7 when
+ * 2 crop <= 896 is smaller.  0 when the grid is not below n (the flag is then
+ * ignored for that path).  Either output may be NULL. */
+litho_status litho_kernels_grid(const litho_kernels* h, int* nc_fft, int* nc_tensor);
 
 /* Copies the FP64 kernels phi[n_focus][k][crop][crop][2] back to the host. */
 litho_status litho_kernels_phi(const litho_kernels* h, double* phi_host);

@@ -11,6 +11,20 @@
 
 namespace litho {
 
+// Coarse evaluation grid for a field band of C columns on an N grid: the
+// smallest power of two that is at least 2C, or with `allow896` also
+// 896 = 16 x 8 x 7, or 0 when it is not below N.  The FP32 FFT path keeps
+// powers of two: its 896-point transform issues more instructions per row
+// than the 1024-point one (idle butterfly slots in the radix-16 and radix-8
+// passes), so the smaller grid does not pay there; the tensor-core path's
+// work scales with the grid's square.
+int coarse_grid(int C, int N, bool allow896) {
+  int nc = 32;
+  while (nc < 2 * C) nc *= 2;
+  if (allow896 && 2 * C <= 896 && 896 < nc) nc = 896;
+  return nc < N ? nc : 0;
+}
+
 namespace {
 thread_local char g_err[1024] = "";
 
@@ -54,14 +68,20 @@ litho_status upload(litho_kernels* h) {
   LITHO_TRY_CUDA(cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
   // coarse grid: I has no frequency at or beyond C along either axis, so
   // nc >= 2C samples determine it exactly
-  int nc = 32;
-  while (nc < 2 * C) nc *= 2;
-  h->nc = nc < N ? nc : 0;
-  if (h->nc) {
-    std::vector<float2> twc(h->nc);
-    fft_twiddle_table(h->nc, twc.data());
-    LITHO_TRY_CUDA(cudaMalloc(&h->d_twc, twc.size() * sizeof(float2)));
-    LITHO_TRY_CUDA(cudaMemcpy(h->d_twc, twc.data(), twc.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  h->nc = coarse_grid(C, N, false);
+  h->nc_tc = coarse_grid(C, N, true);
+  for (int pass = 0; pass < 2; ++pass) {
+    const int nc = pass ? h->nc_tc : h->nc;
+    float2** dst = pass ? &h->d_twc_tc : &h->d_twc;
+    if (!nc) continue;
+    if (pass && nc == h->nc) {
+      h->d_twc_tc = h->d_twc;
+      continue;
+    }
+    std::vector<float2> twc(nc);
+    fft_twiddle_table(nc, twc.data());
+    LITHO_TRY_CUDA(cudaMalloc(dst, twc.size() * sizeof(float2)));
+    LITHO_TRY_CUDA(cudaMemcpy(*dst, twc.data(), twc.size() * sizeof(float2), cudaMemcpyHostToDevice));
   }
   return LITHO_OK;
 }
@@ -100,6 +120,7 @@ void litho_free_kernels(litho_kernels* h) {
   cudaFree(h->d_lambda);
   cudaFree(h->d_phi);
   cudaFree(h->d_tw);
+  if (h->d_twc_tc != h->d_twc) cudaFree(h->d_twc_tc);
   cudaFree(h->d_twc);
   for (auto& s : h->host_streams)
     if (s) cudaStreamDestroy(s);
@@ -270,6 +291,13 @@ litho_status litho_kernels_info(const litho_kernels* h, int* n, int* crop, int* 
   return LITHO_OK;
 }
 
+litho_status litho_kernels_grid(const litho_kernels* h, int* nc_fft, int* nc_tensor) {
+  LITHO_REQUIRE(h, "null handle");
+  if (nc_fft) *nc_fft = h->nc;
+  if (nc_tensor) *nc_tensor = h->nc_tc;
+  return LITHO_OK;
+}
+
 litho_status litho_kernels_phi(const litho_kernels* h, double* phi_host) {
   LITHO_REQUIRE(h && phi_host, "null argument");
   std::memcpy(phi_host, h->phi_host.data(), h->phi_host.size() * sizeof(double));
@@ -299,7 +327,7 @@ struct AerialLayout {
 // share of the launch, with the group's stage-1 fields within 2 GiB, and
 // groups of equal size.
 static int fft_group_clips(const litho_kernels* h, int b, bool coarse) {
-  const size_t NE = coarse ? h->nc : h->n;
+  const size_t NE = coarse ? coarse_n(h, LITHO_PREC_FFT32) : h->n;
   const size_t per_clip = size_t(h->n_focus) * h->k * NE * h->crop * sizeof(float2);
   const size_t cap = std::max<size_t>(1, std::min<size_t>(64, (size_t(2) << 30) / per_clip));
   const size_t groups = (size_t(b) + cap - 1) / cap;
@@ -308,7 +336,7 @@ static int fft_group_clips(const litho_kernels* h, int b, bool coarse) {
 
 static AerialLayout aerial_layout(const litho_kernels* h, int b, litho_precision prec, bool coarse, void* ws) {
   Carve c(ws, 0);
-  const size_t N = h->n, C = h->crop, F = h->n_focus, K = h->k, NE = coarse ? h->nc : h->n;
+  const size_t N = h->n, C = h->crop, F = h->n_focus, K = h->k, NE = coarse ? coarse_n(h, prec) : h->n;
   AerialLayout L;
   L.rowbuf = c.take<float2>(size_t(b) * N * C);
   L.mhat = c.take<float2>(size_t(b) * C * C);
@@ -350,19 +378,20 @@ struct FusedResist {
 
 // `planes` coarse images in L.ic -> N x N planes at `out` (plane offset `p0`
 // of the call for the fused resist outputs).
-static litho_status upsample(const litho_kernels* h, const AerialLayout& L, int planes, float* out,
+static litho_status upsample(const litho_kernels* h, litho_precision p, const AerialLayout& L, int planes, float* out,
                              const FusedResist* fr, size_t p0, cudaStream_t st) {
-  const int N = h->n, NC = h->nc, C2 = 2 * h->crop;
+  const int N = h->n, NC = coarse_n(h, p), C2 = 2 * h->crop;
+  const float2* twc = coarse_tw(h, p);
   if (!fr) {
     ProfScope ps(kStageUpsample, st, 4);
-    LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, h->d_twc, L.rowbuf2, L.spec, st));
+    LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, twc, L.rowbuf2, L.spec, st));
     LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, planes, N, C2, h->d_tw, L.q, st));
     LITHO_TRY_CUDA(launch_band_rows_real(L.q, planes, N, C2, 1.0f, h->d_tw, out, st));
     return LITHO_OK;
   }
   const size_t nn = size_t(N) * N;
   ProfScope ps(kStageUpsampleResist, st, 4);
-  LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, h->d_twc, L.rowbuf2, L.spec, st, L.gain));
+  LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, twc, L.rowbuf2, L.spec, st, L.gain));
   LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, planes, N, C2, h->d_tw, L.q, st));
   LITHO_TRY_CUDA(launch_band_rows_resist(L.q, planes, N, C2, h->d_tw, fr->threshold, out, fr->iblur + p0 * nn,
                                          fr->printed ? fr->printed + p0 * nn : nullptr, st));
@@ -375,7 +404,7 @@ litho_status litho_aerial_workspace_size(const litho_kernels* h, int b, litho_pr
   litho_precision p;
   bool coarse;
   LITHO_REQUIRE(decode_precision(int(prec), &p, &coarse), "unknown precision");
-  *bytes = aerial_layout(h, b, p, coarse && h->nc > 0, nullptr).bytes;
+  *bytes = aerial_layout(h, b, p, coarse && coarse_n(h, p) > 0, nullptr).bytes;
   return LITHO_OK;
 }
 
@@ -388,7 +417,7 @@ static litho_status aerial_prepare(const litho_kernels* h, const float* mask_dev
   LITHO_REQUIRE(b >= 1, "b must be >= 1");
   LITHO_REQUIRE(std::isfinite(dose), "dose must be finite");
   LITHO_REQUIRE(decode_precision(prec, p, coarse), "unknown precision");
-  *coarse = *coarse && h->nc > 0;
+  *coarse = *coarse && coarse_n(h, *p) > 0;
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(workspace_dev) & 255) == 0, "workspace must be 256-byte aligned");
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(mask_dev) & 15) == 0 && (reinterpret_cast<uintptr_t>(intensity_dev) & 15) == 0,
                 "mask and intensity must be 16-byte aligned");
@@ -423,12 +452,12 @@ static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, in
       litho_status s =
           gemm_aerial_group(h, L.mhat + size_t(c0) * C * C, g, float(dose), p, coarse, coarse ? L.ic : dst, L.gws, st);
       if (s != LITHO_OK) return s;
-      if (coarse && (s = upsample(h, L, g * F, dst, fr, size_t(c0) * F, st)) != LITHO_OK) return s;
+      if (coarse && (s = upsample(h, p, L, g * F, dst, fr, size_t(c0) * F, st)) != LITHO_OK) return s;
     }
     return LITHO_OK;
   }
-  const int NE = coarse ? h->nc : N;
-  const float2* tw = coarse ? h->d_twc : h->d_tw;
+  const int NE = coarse ? coarse_n(h, p) : N;
+  const float2* tw = coarse ? coarse_tw(h, p) : h->d_tw;
   for (int c0 = 0; c0 < b; c0 += G) {
     const int g = std::min(G, b - c0);
     float* img = intensity_dev + size_t(c0) * F * N * N;
@@ -442,7 +471,7 @@ static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, in
                                        (long long)K * NE * C, (long long)NE * NE, st, F));
     }
     if (coarse) {
-      litho_status s = upsample(h, L, g * F, img, fr, size_t(c0) * F, st);
+      litho_status s = upsample(h, p, L, g * F, img, fr, size_t(c0) * F, st);
       if (s != LITHO_OK) return s;
     }
   }

@@ -270,6 +270,7 @@ cudaError_t stage2_n(const float2* t1, const float* lam, int nk, int crop, float
   return cudaGetLastError();
 }
 
+// Transform sizes of the full grid (powers of two) ...
 #define LITHO_DISPATCH_N(n, CALL)          \
   switch (n) {                             \
     case 32: return CALL(32);              \
@@ -279,6 +280,20 @@ cudaError_t stage2_n(const float2* t1, const float* lam, int nk, int crop, float
     case 512: return CALL(512);            \
     case 1024: return CALL(1024);          \
     case 2048: return CALL(2048);          \
+    default: return cudaErrorInvalidValue; \
+  }
+
+// ... and of the forward transforms on a coarse grid (also 896, tensor-core path)
+#define LITHO_DISPATCH_NC(n, CALL)          \
+  switch (n) {                             \
+    case 32: return CALL(32);              \
+    case 64: return CALL(64);              \
+    case 128: return CALL(128);            \
+    case 256: return CALL(256);            \
+    case 512: return CALL(512);            \
+    case 1024: return CALL(1024);          \
+    case 2048: return CALL(2048);          \
+    case 896: return CALL(896);            \
     default: return cudaErrorInvalidValue; \
   }
 
@@ -293,6 +308,7 @@ bool fft_twiddle_table(int n, float2* out) {
     case 512: fill_twiddle_table<512>(out); return true;
     case 1024: fill_twiddle_table<1024>(out); return true;
     case 2048: fill_twiddle_table<2048>(out); return true;
+    case 896: fill_twiddle_table<896>(out); return true;
     default: return false;
   }
 }
@@ -300,7 +316,7 @@ bool fft_twiddle_table(int n, float2* out) {
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
                                  float2* mhat, cudaStream_t st, const float* gain) {
 #define CALL(N) mask_spectrum_n<N>(m, b, crop, tw, rowbuf, mhat, gain, st)
-  LITHO_DISPATCH_N(n, CALL)
+  LITHO_DISPATCH_NC(n, CALL)
 #undef CALL
 }
 

@@ -1,7 +1,7 @@
 // Shared-memory Stockham FFT building blocks for sm_103a.
 //
-// A length-N transform (N a power of two, 32..2048) is a sequence of radix-R
-// passes (R in {4, 8, 16}); before pass p, `NS` is the product of the earlier
+// A length-N transform (N a power of two, 32..2048, or 896) is a sequence of
+// radix-R passes (R in {4, 7, 8, 16}); before pass p, `NS` is the product of the earlier
 // radices.  Butterfly j in [0, N/R) of a pass reads x[j + r N/R] (r < R),
 // multiplies element r by w^(r (j mod NS) N/(NS R)) (w = e^{-2 pi i/N}, or its
 // conjugate for the inverse), takes an R-point DFT in registers and writes
@@ -19,7 +19,7 @@
 // shared memory: for each pass after the first, entries (r-1) NS + k hold
 // w^(r k N/(NS R)) for r in [1, R), k in [0, NS), so consecutive butterflies
 // read consecutive entries.  The R-point DFTs are radix-2
-// decimation-in-frequency networks in registers.
+// decimation-in-frequency networks in registers (R = 7: symmetric pairs).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -53,6 +53,45 @@ __device__ __forceinline__ constexpr float sin16(int t) {
        : t == 6 ? 0.70710678118654752f : t == 7 ? 0.38268343236508977f : 0.0f;
 }
 
+// cos and sin of 2 pi t / 7, t = 1, 2, 3 (exact mathematical constants rounded to float)
+__device__ __forceinline__ constexpr float cos7(int t) {
+  return t == 1 ? 0.62348980185873353f : t == 2 ? -0.22252093395631440f : -0.90096886790241913f;
+}
+__device__ __forceinline__ constexpr float sin7(int t) {
+  return t == 1 ? 0.78183148246802981f : t == 2 ? 0.97492791218182361f : 0.43388373911755812f;
+}
+
+// 7-point DFT, v'[q] = sum_r v[r] e^{SIGN 2 pi i r q / 7}, from the symmetric
+// pairs a_m = v[m] + v[7-m] and b_m = v[m] - v[7-m] (m = 1..3):
+// v'[q] = v[0] + sum_m a_m cos(2 pi m q/7) + SIGN i sum_m b_m sin(2 pi m q/7),
+// and v'[7-q] the same with the sine term negated.
+template <int SIGN>
+__device__ __forceinline__ void dft7(float2 (&v)[7]) {
+  float2 a[4], b[4];
+#pragma unroll
+  for (int m = 1; m <= 3; ++m) {
+    a[m] = cadd(v[m], v[7 - m]);
+    b[m] = csub(v[m], v[7 - m]);
+  }
+  const float2 x0 = v[0];
+  v[0] = make_float2(x0.x + a[1].x + a[2].x + a[3].x, x0.y + a[1].y + a[2].y + a[3].y);
+#pragma unroll
+  for (int q = 1; q <= 3; ++q) {
+    float2 p = x0, s = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int m = 1; m <= 3; ++m) {
+      const int k = (m * q) % 7;  // angle 2 pi k / 7; k > 3 is the mirror 7 - k with the sine negated
+      const float c = k <= 3 ? cos7(k) : cos7(7 - k);
+      const float sn = k <= 3 ? sin7(k) : -sin7(7 - k);
+      p = make_float2(fmaf(a[m].x, c, p.x), fmaf(a[m].y, c, p.y));
+      s = make_float2(fmaf(b[m].x, sn, s.x), fmaf(b[m].y, sn, s.y));
+    }
+    // SIGN i s = (-SIGN s.y, SIGN s.x)
+    v[q] = make_float2(p.x - SIGN * s.y, p.y + SIGN * s.x);
+    v[7 - q] = make_float2(p.x + SIGN * s.y, p.y - SIGN * s.x);
+  }
+}
+
 __host__ __device__ __forceinline__ constexpr int ilog2(int x) {
   int r = 0;
   while (x > 1) {
@@ -74,8 +113,12 @@ __host__ __device__ __forceinline__ constexpr int bitrev(int q, int bits) {
 // lie in the lowest and highest quarter of the indices has this form.
 template <int R, int SIGN, bool BANDED = false>
 __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
-  static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
-  static_assert(!BANDED || R >= 4, "banded input needs R >= 4");
+  static_assert(R == 2 || R == 4 || R == 7 || R == 8 || R == 16, "radix");
+  static_assert(!BANDED || (R >= 4 && R != 7), "banded input needs a power-of-two R >= 4");
+  if constexpr (R == 7) {
+    dft7<SIGN>(v);
+    return;
+  } else {
 #pragma unroll
   for (int span = R / 2; span >= 1; span /= 2) {
 #pragma unroll
@@ -114,9 +157,12 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
   for (int q = 0; q < R; ++q) o[q] = v[bitrev(q, LB)];
 #pragma unroll
   for (int q = 0; q < R; ++q) v[q] = o[q];
+  }
 }
 
 // Radix plans: passes in order, product N.  NT = threads per transform.
+// Besides the powers of two, 896 = 16 x 8 x 7: the smallest grid that holds
+// the 2C - 1 frequencies of an image whose field band has C = 448 columns.
 template <int N> struct Plan;
 template <> struct Plan<32>   { static constexpr int NT = 32;  static constexpr int R[2] = {8, 4}; static constexpr int P = 2; };
 template <> struct Plan<64>   { static constexpr int NT = 32;  static constexpr int R[2] = {8, 8}; static constexpr int P = 2; };
@@ -125,6 +171,7 @@ template <> struct Plan<256>  { static constexpr int NT = 32;  static constexpr 
 template <> struct Plan<512>  { static constexpr int NT = 64;  static constexpr int R[3] = {8, 8, 8}; static constexpr int P = 3; };
 template <> struct Plan<1024> { static constexpr int NT = 64;  static constexpr int R[3] = {16, 8, 8}; static constexpr int P = 3; };
 template <> struct Plan<2048> { static constexpr int NT = 128; static constexpr int R[3] = {16, 16, 8}; static constexpr int P = 3; };
+template <> struct Plan<896>  { static constexpr int NT = 64;  static constexpr int R[3] = {16, 8, 7}; static constexpr int P = 3; };
 
 template <int N, int NT, int R>
 struct PassShape {

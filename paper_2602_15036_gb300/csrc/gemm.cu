@@ -451,6 +451,7 @@ cudaError_t stage1_split_mode(int n, const float2* mhat, const float2* phi, int 
     case 128: return stage1_split_n<128, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
     case 256: return stage1_split_n<256, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
     case 512: return stage1_split_n<512, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
+    case 896: return stage1_split_n<896, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
     case 1024: return stage1_split_n<1024, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
     case 2048: return stage1_split_n<2048, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
     default: return cudaErrorInvalidValue;
@@ -502,7 +503,7 @@ struct GemmOperands {
 
 namespace {
 
-int eval_n(const litho_kernels* h, bool coarse) { return coarse ? h->nc : h->n; }
+int eval_n(const litho_kernels* h, bool coarse) { return coarse ? h->nc_tc : h->n; }
 
 size_t per_clip_bytes(const litho_kernels* h, int mode, bool coarse) {
   const size_t rows = size_t(h->n_focus) * h->k * eval_n(h, coarse), cols = size_t(2) * h->crop;
@@ -630,7 +631,7 @@ litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int c
   const int mode = mode_of(prec), gi = coarse ? 1 : 0;
   GemmOperands* g = h->gemm;
   const int N = eval_n(h, coarse), C = h->crop, F = h->n_focus, K = h->k;
-  const float2* tw = coarse ? h->d_twc : h->d_tw;
+  const float2* tw = coarse ? h->d_twc_tc : h->d_tw;
   const size_t half =
       up256(size_t(std::min(clips, GROUP_CLIPS)) * per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1));
   char* a_hi = static_cast<char*>(ws);

@@ -91,8 +91,10 @@ struct litho_kernels {
   float* d_lambda = nullptr;               // [F*K]
   float2* d_phi = nullptr;                 // [F][K][C][C]
   float2* d_tw = nullptr;                  // FFT twiddle table for N
-  int nc = 0;                              // coarse grid: smallest power of two >= 2 crop, 0 if not below N
+  int nc = 0;                              // FP32 FFT coarse grid: smallest power of two >= 2 crop (0: not below N)
   float2* d_twc = nullptr;                 // FFT twiddle table for nc
+  int nc_tc = 0;                           // tensor-core coarse grid: as nc, or 896 when 2 crop <= 896 < nc
+  float2* d_twc_tc = nullptr;              // FFT twiddle table for nc_tc (d_twc when nc_tc == nc)
   litho::GemmOperands* gemm = nullptr;     // lazily built per precision
   int device = 0;
   // streams and events of the pipelined host-buffer path (created on first use)
@@ -102,6 +104,16 @@ struct litho_kernels {
 };
 
 namespace litho {
+
+// Coarse grid for a band of C columns on an N grid (api.cpp): smallest power
+// of two >= 2C, or with allow896 also 896; 0 when not below N.
+int coarse_grid(int C, int N, bool allow896);
+
+// Coarse evaluation grid of a precision's path (0 when it does not apply) and its twiddle table.
+inline int coarse_n(const litho_kernels* h, litho_precision p) { return p == LITHO_PREC_FFT32 ? h->nc : h->nc_tc; }
+inline const float2* coarse_tw(const litho_kernels* h, litho_precision p) {
+  return p == LITHO_PREC_FFT32 ? h->d_twc : h->d_twc_tc;
+}
 
 // ---- launchers (fft.cu) ---------------------------------------------------------------------
 // The N-entry per-pass twiddle table the FFT kernels expect (false if n unsupported).

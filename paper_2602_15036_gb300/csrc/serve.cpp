@@ -110,9 +110,8 @@ size_t request_bytes(const litho_request& r, int crop) {
   shape.n_focus = 1;
   shape.k = r.k;
   shape.pixel_nm = r.pixel_nm;
-  int nc = 32;
-  while (nc < 2 * crop) nc *= 2;
-  shape.nc = nc < r.n ? nc : 0;  // as the kernel upload computes it
+  shape.nc = coarse_grid(crop, r.n, false);  // as the kernel upload computes them
+  shape.nc_tc = coarse_grid(crop, r.n, true);
   const size_t nn = size_t(r.n) * r.n;
   size_t ws = 0;
   if (r.kind == LITHO_REQ_IMAGE) {

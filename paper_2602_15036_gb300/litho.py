@@ -71,6 +71,7 @@ _SIGS = {
                                      POINTER(c_void_p)]),
     "litho_kernels_info": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                    POINTER(c_int), POINTER(c_double), POINTER(c_double), POINTER(c_double)]),
+    "litho_kernels_grid": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int)]),
     "litho_kernels_phi": (c_int, [c_void_p, POINTER(c_double)]),
     "litho_free_kernels": (None, [c_void_p]),
     "litho_aerial_workspace_size": (c_int, [c_void_p, c_int, c_int, POINTER(c_size_t)]),
@@ -169,6 +170,12 @@ class Kernels:
         out = np.zeros((self.n_focus, self.k, self.crop, self.crop, 2))
         _check(lib().litho_kernels_phi(self.handle, out.ctypes.data_as(POINTER(c_double))))
         return out[..., 0] + 1j * out[..., 1]
+
+    def grid(self, precision: str = "fft32") -> int:
+        """Coarse evaluation grid of a precision's path with "/coarse" (0: not below n)."""
+        fft, tc = c_int(), c_int()
+        _check(lib().litho_kernels_grid(self.handle, byref(fft), byref(tc)))
+        return fft.value if precision.split("/")[0] == "fft32" else tc.value
 
     def close(self):
         if self.handle is not None and self.handle.value:

@@ -63,3 +63,36 @@ def test_coarse_flag_ignored_when_grid_is_not_smaller(litho_lib, cuda):
     a, _ = _run(litho_lib, cuda, lam, phi, n, 16.0, masks, "fft32")
     b, _ = _run(litho_lib, cuda, lam, phi, n, 16.0, masks, "fft32/coarse")
     assert np.array_equal(a, b)
+
+
+def test_coarse_grid_sizes(litho_lib, cuda):
+    """Coarse grids per path: the FP32 FFT path takes the smallest power of two >= 2C,
+    the tensor-core path also 896 = 16 x 8 x 7 when that is smaller; 0 when not below N."""
+    L = litho_lib
+    cases = [(2048, 8.0, 448, 1024, 896), (1024, 16.0, 448, 0, 896), (1024, 8.0, 224, 512, 512),
+             (256, 8.0, 64, 128, 128), (64, 8.0, 32, 0, 0)]
+    for n, pixel, crop, fft, tc in cases:
+        lam = np.ones((1, 1))
+        phi = np.zeros((1, 1, crop, crop), dtype=np.complex128)
+        kern = L.litho_upload_kernels(n, pixel, lam, phi)
+        assert (kern.grid("fft32"), kern.grid("fp16x3")) == (fft, tc), (n, crop)
+
+
+@pytest.mark.parametrize("precision", ["fp16x3/coarse", "fp16/coarse", "fft32/coarse"])
+def test_coarse_grid_896_matches_oracle(litho_lib, cuda, precision):
+    """1024^2 at 16 nm (band of 448 columns): the tensor-core path evaluates on the
+    896 x 896 grid (radix 16, 8, 7 transforms for its operands and the interpolation);
+    for the FFT path the flag does not apply (1024 is not below N).  Whole images
+    against the oracle."""
+    n, pixel, k, focus = 1024, 16.0, 8, [0.0, 60.0]
+    lam, phi = oracle_kernel_set(DUV_QUAD41, n, pixel, focus, k)
+    assert phi.shape[-1] == 448
+    masks = np.stack([synth.random_rect_mask(n, seed=700 + i, count=150, side_lo=3, side_hi=10) for i in range(2)])
+    got, kern = _run(litho_lib, cuda, lam, phi, n, pixel, masks, precision)
+    assert kern.grid(precision) == (0 if precision.startswith("fft32") else 896)
+    worst = 0.0
+    for i in range(2):
+        for f in range(2):
+            worst = max(worst, np.abs(got[i, f] - OI.socs_image(masks[i].astype(np.float64), lam[f], phi[f])).max())
+    print(f"{precision} max|err|={worst:.3e}")
+    assert worst <= TOL[precision]
