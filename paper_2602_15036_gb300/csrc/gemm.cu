@@ -407,12 +407,12 @@ struct OutSplit {
   void* hi;
   void* lo;
   const float* scales;
-  int n, crop;
+  int n, crop, nk;  // row j of the operand belongs to kernel j mod nk
   template <int W>
   __device__ __forceinline__ void store_row(int j, int y, int c0, const float2 (&v)[W]) const {
     static_assert(W % 4 == 0 && CH % W == 0, "column block");
     const size_t o = ((size_t)j * n + y) * (size_t)(2 * crop) + (size_t)(c0 / CH) * KE + (c0 % CH);
-    const float s = scales[j];
+    const float s = scales[j % nk];
     uint32_t rh[W], rl[W], ih[W], il[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -438,22 +438,24 @@ struct OutSplit {
   }
 };
 
+// `clips` spectra in one launch; clip i writes the operand rows of kernels j + i nk.
 template <int N, int MODE>
 cudaError_t stage1_split_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
-                           const float* scales, void* a_hi, void* a_lo, cudaStream_t st) {
-  return launch_stage1_cols<N, ColW<N>::W>(mhat, phi, nk, crop, tw, OutSplit<MODE>{a_hi, a_lo, scales, N, crop}, st);
+                           const float* scales, void* a_hi, void* a_lo, int clips, cudaStream_t st) {
+  return launch_stage1_cols<N, ColW<N>::W>(mhat, phi, nk, crop, tw,
+                                           OutSplit<MODE>{a_hi, a_lo, scales, N, crop, nk}, st, clips);
 }
 
 template <int MODE>
 cudaError_t stage1_split_mode(int n, const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
-                              const float* scales, void* a_hi, void* a_lo, cudaStream_t st) {
+                              const float* scales, void* a_hi, void* a_lo, int clips, cudaStream_t st) {
   switch (n) {
-    case 128: return stage1_split_n<128, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
-    case 256: return stage1_split_n<256, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
-    case 512: return stage1_split_n<512, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
-    case 896: return stage1_split_n<896, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
-    case 1024: return stage1_split_n<1024, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
-    case 2048: return stage1_split_n<2048, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, st);
+    case 128: return stage1_split_n<128, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
+    case 256: return stage1_split_n<256, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
+    case 512: return stage1_split_n<512, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
+    case 896: return stage1_split_n<896, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
+    case 1024: return stage1_split_n<1024, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
+    case 2048: return stage1_split_n<2048, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -636,26 +638,18 @@ litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int c
       up256(size_t(std::min(clips, GROUP_CLIPS)) * per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1));
   char* a_hi = static_cast<char*>(ws);
   char* a_lo = is_split(mode) ? a_hi + half : a_hi;
-  const size_t clip_half = per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1);
   {
-    ProfScope ps(kStageGemmOperands, st, clips);
-    for (int c = 0; c < clips; ++c) {
-      const float2* mh = mhat + size_t(c) * C * C;
-      cudaError_t e;
-      if (mode == kBF16)
-        e = stage1_split_mode<kBF16>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
-                                     nullptr, st);
-      else if (mode == kFP16)
-        e = stage1_split_mode<kFP16>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
-                                     nullptr, st);
-      else if (mode == kBF16X3)
-        e = stage1_split_mode<kBF16X3>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
-                                       a_lo + c * clip_half, st);
-      else
-        e = stage1_split_mode<kFP16X3>(N, mh, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi + c * clip_half,
-                                       a_lo + c * clip_half, st);
-      LITHO_TRY_CUDA(e);
-    }
+    ProfScope ps(kStageGemmOperands, st, 1);  // one launch for the group
+    cudaError_t e;
+    if (mode == kBF16)
+      e = stage1_split_mode<kBF16>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, nullptr, clips, st);
+    else if (mode == kFP16)
+      e = stage1_split_mode<kFP16>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, nullptr, clips, st);
+    else if (mode == kBF16X3)
+      e = stage1_split_mode<kBF16X3>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, a_lo, clips, st);
+    else
+      e = stage1_split_mode<kFP16X3>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, a_lo, clips, st);
+    LITHO_TRY_CUDA(e);
   }
   const int fmt = is_fp16(mode) ? 0 : 1;
   const unsigned long long rows = (unsigned long long)clips * F * K * N;
