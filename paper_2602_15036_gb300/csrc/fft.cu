@@ -255,7 +255,7 @@ cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, f
 template <int N>
 cudaError_t stage1_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, float2* t1,
                      cudaStream_t st, int clips) {
-  return launch_stage1_cols<N, ColW<N>::W>(mhat, phi, nk, crop, tw, OutC64{t1, N, crop}, st, clips);
+  return launch_stage1_cols<N, Stage1W<N>::W>(mhat, phi, nk, crop, tw, OutC64{t1, N, crop}, st, clips);
 }
 
 template <int N>

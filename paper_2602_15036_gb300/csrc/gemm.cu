@@ -442,7 +442,7 @@ struct OutSplit {
 template <int N, int MODE>
 cudaError_t stage1_split_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
                            const float* scales, void* a_hi, void* a_lo, int clips, cudaStream_t st) {
-  return launch_stage1_cols<N, ColW<N>::W>(mhat, phi, nk, crop, tw,
+  return launch_stage1_cols<N, Stage1W<N>::W>(mhat, phi, nk, crop, tw,
                                            OutSplit<MODE>{a_hi, a_lo, scales, N, crop, nk}, st, clips);
 }
 

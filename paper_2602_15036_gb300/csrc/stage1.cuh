@@ -40,6 +40,14 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // pairs) and two operand blocks [crop][W] in the operand's own row-major
 // order (a row's W values are one or more whole 16-byte copies; a half-warp
 // reading rows c..c+16/W-1 of all W columns again hits 16 bank pairs).
+// Columns per CTA: as many as fit one CTA of at most 512 threads, since a
+// warp's final-pass stores then cover longer pieces of each output row (W = 8:
+// 64-byte pieces; measured faster than W = 4 at 2 CTAs per SM for N = 1024).
+template <int N>
+struct Stage1W {
+  static constexpr int W = Plan<N>::NT <= 64 ? 8 : 4;
+};
+
 template <int N, int W>
 struct Stage1Shape {
   static_assert(W % 2 == 0, "W even: rows of whole 16-byte pieces");
