@@ -29,11 +29,15 @@
 
 namespace litho {
 
+// Complex arithmetic on the packed two-lane FP32 instructions of sm_100+
+// (one instruction for both components, each rounded as the scalar form).
+// cmul: (a.x b.x - a.y b.y, a.x b.y + a.y b.x) = fma(a.x, b, (-a.y b.y, a.y b.x)).
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+  return __ffma2_rn(make_float2(a.x, a.x), b, __fmul2_rn(make_float2(a.y, a.y), make_float2(-b.y, b.x)));
 }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as fma(b, -1, a): exact product, one rounding, as the scalar subtraction
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 __host__ __device__ __forceinline__ constexpr int pad16(int i) { return i + (i >> 4); }
 template <int N>
@@ -144,7 +148,7 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
           if (t == 4) {
             d = make_float2(-wi * d.y, wi * d.x);  // multiply by +-i
           } else {
-            d = make_float2(fmaf(d.x, wr, -d.y * wi), fmaf(d.x, wi, d.y * wr));
+            d = cmul(d, make_float2(wr, wi));
           }
         }
         v[b + i + span] = d;
