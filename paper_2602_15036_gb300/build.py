@@ -21,7 +21,8 @@ OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblitho.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cpp", "optics.cpp", "prof.cpp", "serve.cpp", "fft.cu", "resist.cu", "gemm.cu", "ilt.cu", "noalloc.cu"]
+SOURCES = ["api.cpp", "optics.cpp", "prof.cpp", "serve.cpp", "fft.cu", "interp.cu", "resist.cu", "gemm.cu", "ilt.cu",
+           "noalloc.cu"]
 
 
 def _nvcc() -> str:

@@ -382,17 +382,20 @@ static litho_status upsample(const litho_kernels* h, litho_precision p, const Ae
                              const FusedResist* fr, size_t p0, cudaStream_t st) {
   const int N = h->n, NC = coarse_n(h, p), C2 = 2 * h->crop;
   const float2* twc = coarse_tw(h, p);
-  if (!fr) {
-    ProfScope ps(kStageUpsample, st, 4);
-    LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, twc, L.rowbuf2, L.spec, st));
+  const float* gain = fr ? L.gain : nullptr;
+  ProfScope ps(fr ? kStageUpsampleResist : kStageUpsample, st, 3);
+  if (interp_cols_supported(NC, N)) {
+    LITHO_TRY_CUDA(launch_mask_rows(L.ic, planes, NC, C2, twc, L.rowbuf2, st));
+    LITHO_TRY_CUDA(launch_interp_cols(L.rowbuf2, planes, NC, N, C2, twc, h->d_tw, gain, L.q, st));
+  } else {
+    LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, twc, L.rowbuf2, L.spec, st, gain));
     LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, planes, N, C2, h->d_tw, L.q, st));
+  }
+  if (!fr) {
     LITHO_TRY_CUDA(launch_band_rows_real(L.q, planes, N, C2, 1.0f, h->d_tw, out, st));
     return LITHO_OK;
   }
   const size_t nn = size_t(N) * N;
-  ProfScope ps(kStageUpsampleResist, st, 4);
-  LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, twc, L.rowbuf2, L.spec, st, L.gain));
-  LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, planes, N, C2, h->d_tw, L.q, st));
   LITHO_TRY_CUDA(launch_band_rows_resist(L.q, planes, N, C2, h->d_tw, fr->threshold, out, fr->iblur + p0 * nn,
                                          fr->printed ? fr->printed + p0 * nn : nullptr, st));
   return LITHO_OK;

@@ -239,6 +239,15 @@ size_t col_smem_bytes() {
 }
 
 template <int N>
+cudaError_t mask_rows_n(const float* m, int b, int crop, const float2* tw, float2* rowbuf, cudaStream_t st) {
+  const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
+  cudaError_t e = smem_attrs(k_mask_rows<N>, smr);
+  if (e != cudaSuccess) return e;
+  k_mask_rows<N><<<dim3(N / 2, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf);
+  return cudaGetLastError();
+}
+
+template <int N>
 cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, float2* rowbuf, float2* mhat,
                             const float* gain, cudaStream_t st) {
   const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
@@ -324,6 +333,13 @@ cudaError_t launch_band_rows_real(const float2* q, int planes, int n, int crop, 
                                   float* out, cudaStream_t st) {
 #define CALL(N) band_rows_real_n<N>(q, planes, crop, scale, tw, out, st)
   LITHO_DISPATCH_N(n, CALL)
+#undef CALL
+}
+
+cudaError_t launch_mask_rows(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
+                             cudaStream_t st) {
+#define CALL(N) mask_rows_n<N>(m, b, crop, tw, rowbuf, st)
+  LITHO_DISPATCH_NC(n, CALL)
 #undef CALL
 }
 

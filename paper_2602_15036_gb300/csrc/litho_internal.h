@@ -122,6 +122,14 @@ bool fft_twiddle_table(int n, float2* out);
 // With `gain` [C] the stored value is mhat (1 + i gain[v] gain[u]) (blur channel, see fft.cu).
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
                                  float2* mhat, cudaStream_t st, const float* gain = nullptr);
+// Row pass of the mask spectrum alone: rowbuf[b][n][C] = row DFT of m, crop columns kept.
+cudaError_t launch_mask_rows(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf, cudaStream_t st);
+// Column pass of the interpolation from an nc grid to an n grid (interp.cu):
+// q[p][n][c2] = inverse transform on n of the crop c2 of nc^-2 x forward
+// transform on nc of rspec[p][nc][c2] (times 1 + i gain[v] gain[u] with gain).
+bool interp_cols_supported(int nc, int n);
+cudaError_t launch_interp_cols(const float2* rspec, int planes, int nc, int n, int c2, const float2* tw_nc,
+                               const float2* tw_n, const float* gain, float2* q, cudaStream_t st);
 // Stage 1 (band multiply + inverse DFT over v): for kernels phi[nk][C][C],
 // t1[j][y][c] = sum_v mhat[v][c] phi_j[v][c] e^{+2 pi i v y/N}, j in [0, nk).
 // phi == NULL transforms nk spectra mhat[j][C][C] themselves.  With kernels,
