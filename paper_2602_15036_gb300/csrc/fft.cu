@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const
     const float l = __ldg(lp + j);
     if (l == 0.f) continue;  // uniform across the block
     const float2* row = base + (size_t)j * N * crop;
-    auto load = [&](int idx) {
-      const int c = freq_of(idx, N) + half;
+    auto load = [&](int, int r, int idx) {
+      const int c = (r < PL::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
       return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
     };
     auto use = [&](int p, int q, int, float2 v) { acc[p][q] = fmaf(l, fmaf(v.x, v.x, v.y * v.y), acc[p][q]); };
@@ -177,8 +177,8 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_real(const float2* __
   __syncthreads();
   const int y = blockIdx.x, p = blockIdx.y, half = crop / 2;
   const float2* row = q + ((size_t)p * N + y) * crop;
-  auto load = [&](int idx) {
-    const int c = freq_of(idx, N) + half;
+  auto load = [&](int, int r, int idx) {
+    const int c = (r < Plan<N>::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
     return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
   };
   float* o = out + ((size_t)p * N + y) * N;
@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_resist(const float2* 
   __syncthreads();
   const int y = blockIdx.x, p = blockIdx.y, half = crop / 2;
   const float2* row = q + ((size_t)p * N + y) * crop;
-  auto load = [&](int idx) {
-    const int c = freq_of(idx, N) + half;
+  auto load = [&](int, int r, int idx) {
+    const int c = (r < Plan<N>::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
     return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
   };
   const size_t o = ((size_t)p * N + y) * N;

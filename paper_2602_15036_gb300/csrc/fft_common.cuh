@@ -183,6 +183,18 @@ struct PassShape {
   static constexpr int PER = (NB + NT - 1) / NT;    // butterflies per thread
 };
 
+// Padded offset of element i + step from that of i when step is a multiple
+// of 16: pad16(i + step) = pad16(i) + step + step/16, a compile-time
+// distance.  Otherwise (small transforms) the full index is formed.
+template <int STEP>
+__device__ __forceinline__ int pad16_step(int i, int r) {
+  if constexpr (STEP % 16 == 0) {
+    return pad16(i) + r * (STEP + STEP / 16);
+  } else {
+    return pad16(i + r * STEP);
+  }
+}
+
 // Offsets of the passes' twiddle blocks: pass 1 at 0, pass 2 after it.
 template <int N>
 struct TwOff {
@@ -226,7 +238,7 @@ __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int 
           v[p][r] = make_float2(0.f, 0.f);  // never read
         } else {
           if constexpr (FROM_SMEM) {
-            v[p][r] = buf[pad16(j + r * S::NB)];
+            v[p][r] = buf[pad16_step<S::NB>(j, r)];
           } else if constexpr (std::is_invocable_v<Load&, int, int, int>) {
             v[p][r] = load(p, r, j + r * S::NB);
           } else {
@@ -243,8 +255,15 @@ __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int 
     const int j = t + p * NT;
     if (j < S::NB) {
       const int base = (j / NS) * NS * R + (j % NS);
+      if constexpr (NS == 1 && 16 % R == 0) {
+        // base is a multiple of R, which divides 16: base + r stays in one run of 16
+        float2* wb = buf + pad16(base);
 #pragma unroll
-      for (int r = 0; r < R; ++r) buf[pad16(base + r * NS)] = v[p][r];
+        for (int r = 0; r < R; ++r) wb[r] = v[p][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad16_step<NS>(base, r)] = v[p][r];
+      }
     }
   }
   __syncthreads();
@@ -265,7 +284,7 @@ __device__ __forceinline__ void pass_last(const float2* buf, const float2* tw, i
     if (j < S::NB) {
       float2 v[R];
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[r] = buf[pad16(j + r * S::NB)];
+      for (int r = 0; r < R; ++r) v[r] = buf[pad16_step<S::NB>(j, r)];
       twiddle_dft<N, R, NS, SIGN, OFF>(v, j, tw);
 #pragma unroll
       for (int q = 0; q < R; ++q) use(p, q, j + q * S::NB, v[q]);

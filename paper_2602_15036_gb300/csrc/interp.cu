@@ -51,8 +51,8 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
   // crop, scale, blur channel, and the inverse transform over v on N
   const float scale = 1.0f / (float(NC) * float(NC));
   const float gu = gain ? __ldg(gain + u0 + g) : 0.f;
-  auto load_f = [&](int idx) {
-    const int v = idx < N / 2 ? idx : idx - N;
+  auto load_f = [&](int, int r, int idx) {
+    const int v = r < Plan<N>::R[0] / 2 ? idx : idx - N;  // first pass: idx < N/2 exactly when r < R/2
     if (v < -half || v >= half) return make_float2(0.f, 0.f);
     float2 s = col[pad16(v < 0 ? v + NC : v)];
     s = make_float2(s.x * scale, s.y * scale);

@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     __syncthreads();
     const float2* b = blk(s) + g;
     auto load = [&](int, int r, int idx) {
-      const int c = band_row(idx);
+      const int c = (r < R0 / 2 ? idx : idx - N) + half;  // idx < N/2 exactly when r < R0/2
       if (c < 0 || c >= crop) return make_float2(0.f, 0.f);
       return phi ? cmul(mreg[r], b[c * W]) : b[c * W];
     };
