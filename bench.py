@@ -415,12 +415,16 @@ def run_aerial(args):
         P.litho_aerial_host(kern, mask_host, ws_host, printed_host=printed_host, precision=args.precision,
                             sigma_nm=SIGMA_NM, threshold=THRESH, stream=stream)
 
-    e2e_step()
+    for _ in range(2):
+        e2e_step()
     ctx.barrier()
-    e2e_steps = max(1, min(args.steps, 5))
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_ms = []
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        e2e_step()
+        t1 = time.perf_counter()
+        e2e_step()                       # synchronous: returns after the printed bytes are on the host
+        e2e_ms.append(1e3 * (time.perf_counter() - t1))
     e2e_s = ctx.max_over_ranks(time.perf_counter() - t0)
     ctx.barrier()
     e2e_val = whole_job_rate(clips * N * N * e2e_steps / 1e6, ctx.world, [e2e_s])
@@ -449,7 +453,8 @@ def run_aerial(args):
             "gpu_launches": head["launches"],
             "gpu_launches_per_step": head["launches"] / args.steps,
             "e2e": {"value": e2e_val, "unit": "Mpx/s", "h2d_bytes_per_step": int(mask_host.numel() * 4),
-                    "d2h_bytes_per_step": int(printed_host.numel())},
+                    "d2h_bytes_per_step": int(printed_host.numel()), "steps": e2e_steps,
+                    "step_ms": [round(x, 3) for x in e2e_ms]},
             "roofline": roof, "peaks_source": peak_src, "clocks": head["clocks"]}
     if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
