@@ -17,6 +17,9 @@ eye against the paper's equations:
   crossings used for the edge-placement difference.
 * `ilt`     - the ILT loss over focus planes and its adjoint gradient,
   plus central finite differences.
+* `contour` - marching-squares contours of the resist image (section II.D)
+  and the edge-placement error at control points with its through-focus
+  average and effective value (Eqs. (6)-(8)).
 
 Parity status: every function here is pinned by tests under `tests/` against
 closed forms, brute-force direct DFTs on 16x16 grids, invariants and finite

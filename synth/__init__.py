@@ -151,3 +151,18 @@ def random_field(shape, seed: int, lo: float = -1.0, hi: float = 1.0) -> np.ndar
     """Plain U[lo, hi) doubles, for property tests."""
     st = Stream(seed)
     return lo + (hi - lo) * st.uniform(int(np.prod(shape))).reshape(shape)
+
+
+def edge_sites(target: np.ndarray, stride: int = 1) -> np.ndarray:
+    """Control points on the edges of a binary target raster: the midpoint of
+    every pixel boundary whose two pixels differ (periodic), as (x, y) in pixel
+    units (x = column, y = row), vertical boundaries (x = j + 0.5) first, each
+    set in row-major order, then every `stride`-th point.  Input construction
+    only (the targets' segment control points); float64 [M][2]."""
+    t = np.asarray(target) != 0
+    i, j = np.nonzero(t != np.roll(t, -1, axis=1))
+    vert = np.stack([j + 0.5, i.astype(np.float64)], axis=1)
+    i, j = np.nonzero(t != np.roll(t, -1, axis=0))
+    horz = np.stack([j.astype(np.float64), i + 0.5], axis=1)
+    pts = np.concatenate([vert, horz], axis=0)
+    return pts[::stride].copy()
