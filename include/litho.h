@@ -6,6 +6,8 @@
  *     I(x) = D * sum_k lam_k |(phi_k (x) m)(x)|^2, over K TCC eigen-kernels and
  *     several focus planes (paper Section III.A, Eqs. (1)-(4));
  *   - the Gaussian-blur + threshold resist (Eq. (5));
+ *   - marching-squares contours of the resist image and the edge-placement
+ *     error at target control points, through focus (Section II.D, Eqs. (6)-(8));
  *   - the ILT mask gradient through the resist and imaging (the adjoint of the
  *     above; pixel-based ILT is the paper's Section I prior art);
  *   - a continuous-batching request server over all of it.
@@ -236,6 +238,52 @@ size_t litho_aerial_noalloc_max_bytes(void);
  * radius must be below n/2. */
 litho_status litho_resist(const float* intensity_dev, int planes, int n, double pixel_nm, double sigma_nm,
                           double threshold, float* iblur_dev, uint8_t* printed_dev, void* stream);
+
+/* ---- contours and edge placement (paper section II.D, Eqs. (6)-(8)) ----------------------------- */
+
+/* Marching-squares contours of `planes` resist images iblur[p][n][n] (f32) at
+ * `threshold` (compared in FP32).  Cell (i, j) has the corners TL = I[i][j],
+ * TR = I[i][j+1], BR = I[i+1][j+1], BL = I[i+1][j] (periodic); a corner is
+ * inside (printed) when I >= T.  A cell edge whose corners differ is crossed
+ * at the linear interpolation of I - T; a saddle (only TL and BR, or only TR
+ * and BL, inside) joins its inside corners when ((TL + TR) + (BR + BL))/4 >= T
+ * and separates them otherwise.  Each segment is oriented so that the corner
+ * it cuts off lies on its left when inside and on its right when outside, and
+ * a segment between opposite edges has the inside pair on its left (left of
+ * p0 -> p1: cross(p1 - p0, q - p0) > 0): closed contours chain end to start
+ * with the printed region on the left.
+ * Output, deterministic: segment s = (x0, y0, x1, y1) in pixels (x = column,
+ * y = row, absolute cell coordinates in FP32, so a cell of the last row or
+ * column can reach n) at seg_dev[4 s .. 4 s + 3], its cell i n + j at cell_dev[s] (may be
+ * NULL); segments in plane order, cells row-major, the two of a saddle by
+ * their start edge (0 top, 1 right, 2 bottom, 3 left).  plane_start_dev
+ * [planes + 1] (int64) receives the index of each plane's first segment and
+ * the total; segments at or beyond `capacity` are counted but not written,
+ * so a caller that sees total > capacity calls again with more room.
+ * Workspace: litho_contours_workspace_size bytes, 256-byte aligned; seg_dev
+ * 16-byte aligned.  Asynchronous on `stream` (three launches).  Errors:
+ * EINVAL, ENOMEM (workspace too small), ECUDA. */
+litho_status litho_contours_workspace_size(int planes, int n, size_t* bytes);
+litho_status litho_contours(const float* iblur_dev, int planes, int n, double threshold, float* seg_dev,
+                            int32_t* cell_dev, int64_t capacity, int64_t* plane_start_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* stream);
+
+/* Edge-placement error, Eq. (6), at m control points on target edges:
+ * epe[p][k] = -(I_b(r_k) - T) / |grad I_b(r_k)| in nm for every plane p, with
+ * the target's value at its own edge read as the threshold T, r_k =
+ * (points[2k], points[2k+1]) = (x, y) in pixels (f32), I_b and its gradient
+ * interpolated bilinearly from the pixels and from their periodic central
+ * differences, the gradient per nm (divided by pixel_nm).  NaN where the
+ * gradient vanishes.  Asynchronous. */
+litho_status litho_epe(const float* iblur_dev, int planes, int n, double pixel_nm, double threshold,
+                       const float* points_dev, int m, float* epe_dev, void* stream);
+
+/* Eqs. (7)-(8) from epe[planes][m]: avg[k] = mean of the on-focus plane f0 and
+ * the defocused planes fp and fn; eff[k] = e0 - tol_pos if e0 > tol_pos,
+ * e0 - tol_neg if e0 < tol_neg, else avg[k] (e0 = epe[f0][k]; a value equal to
+ * a tolerance takes the average).  Either output may be NULL.  Asynchronous. */
+litho_status litho_epe_through_focus(const float* epe_dev, int planes, int m, int f0, int fp, int fn, double tol_neg,
+                                     double tol_pos, float* avg_dev, float* eff_dev, void* stream);
 
 /* ---- ILT gradient -------------------------------------------------------------------------------- */
 

@@ -93,17 +93,18 @@ def _cell_segments(v, thr):
     return segs
 
 
-def marching_squares(iblur, threshold):
+def marching_squares(iblur, threshold, rows=None):
     """All contour segments of one plane: list of (cell, x0, y0, x1, y1, e0, e1)
     with cell = i N + j, coordinates in pixels (absolute, not wrapped: a cell in
-    the last row or column reaches N)."""
+    the last row or column reaches N).  `rows`: only these cell rows i (for
+    large planes)."""
     img = np.asarray(iblur)
     if img.dtype not in (np.float32, np.float64):
         img = img.astype(np.float64)
     thr = img.dtype.type(threshold)
     n = img.shape[-1]
     out = []
-    for i in range(n):
+    for i in (range(n) if rows is None else sorted(rows)):
         for j in range(n):
             v = {(dy, dx): img[(i + dy) % n, (j + dx) % n] for dy, dx in (_TL, _TR, _BR, _BL)}
             for (x0, y0), (x1, y1), e0, e1 in _cell_segments(v, thr):

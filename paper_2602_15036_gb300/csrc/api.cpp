@@ -650,4 +650,59 @@ litho_status litho_resist(const float* intensity_dev, int planes, int n, double 
   return LITHO_OK;
 }
 
+// ---- contours and edge placement ---------------------------------------------------------------
+
+litho_status litho_contours_workspace_size(int planes, int n, size_t* bytes) {
+  LITHO_REQUIRE(bytes && planes >= 1 && n >= 2, "bad argument");
+  *bytes = contour_workspace_bytes(planes, n);
+  return LITHO_OK;
+}
+
+litho_status litho_contours(const float* iblur_dev, int planes, int n, double threshold, float* seg_dev,
+                            int32_t* cell_dev, int64_t capacity, int64_t* plane_start_dev, void* workspace_dev,
+                            size_t workspace_bytes, void* stream) {
+  LITHO_REQUIRE(iblur_dev && plane_start_dev && workspace_dev, "null argument");
+  LITHO_REQUIRE(planes >= 1 && planes <= 65535 && n >= 2 && n <= 65536, "planes in [1, 65535] and n in [2, 65536] required");
+  LITHO_REQUIRE(capacity >= 0 && (capacity == 0 || seg_dev), "seg_dev needed for a nonzero capacity");
+  LITHO_REQUIRE(std::isfinite(threshold), "threshold must be finite");
+  LITHO_REQUIRE((reinterpret_cast<uintptr_t>(seg_dev) & 15) == 0 && (reinterpret_cast<uintptr_t>(workspace_dev) & 255) == 0,
+                "seg_dev must be 16-byte and workspace 256-byte aligned");
+  if (workspace_bytes < contour_workspace_bytes(planes, n)) {
+    set_error("workspace too small: %zu bytes given, %zu needed", workspace_bytes, contour_workspace_bytes(planes, n));
+    return LITHO_ENOMEM;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ProfScope ps(kStageContours, st, 3);
+  LITHO_TRY_CUDA(launch_contours(iblur_dev, planes, n, float(threshold), reinterpret_cast<float4*>(seg_dev), cell_dev,
+                                 capacity, reinterpret_cast<long long*>(plane_start_dev), workspace_dev, st));
+  return LITHO_OK;
+}
+
+litho_status litho_epe(const float* iblur_dev, int planes, int n, double pixel_nm, double threshold,
+                       const float* points_dev, int m, float* epe_dev, void* stream) {
+  LITHO_REQUIRE(iblur_dev && points_dev && epe_dev, "null argument");
+  LITHO_REQUIRE(planes >= 1 && planes <= 65535 && n >= 2 && m >= 0, "planes in [1, 65535], n >= 2, m >= 0 required");
+  LITHO_REQUIRE(pixel_nm > 0 && std::isfinite(threshold), "pixel_nm > 0 and a finite threshold required");
+  LITHO_REQUIRE((reinterpret_cast<uintptr_t>(points_dev) & 7) == 0, "points_dev must be 8-byte aligned");
+  if (m == 0) return LITHO_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ProfScope ps(kStageEpe, st, 1);
+  LITHO_TRY_CUDA(launch_epe(iblur_dev, planes, n, float(pixel_nm), float(threshold),
+                            reinterpret_cast<const float2*>(points_dev), m, epe_dev, st));
+  return LITHO_OK;
+}
+
+litho_status litho_epe_through_focus(const float* epe_dev, int planes, int m, int f0, int fp, int fn, double tol_neg,
+                                     double tol_pos, float* avg_dev, float* eff_dev, void* stream) {
+  LITHO_REQUIRE(epe_dev && (avg_dev || eff_dev), "null argument");
+  LITHO_REQUIRE(m >= 0 && f0 >= 0 && fp >= 0 && fn >= 0 && f0 < planes && fp < planes && fn < planes,
+                "plane indices must lie in [0, planes)");
+  LITHO_REQUIRE(tol_neg <= tol_pos, "tol_neg <= tol_pos required");
+  if (m == 0) return LITHO_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ProfScope ps(kStageEpe, st, 1);
+  LITHO_TRY_CUDA(launch_epe_focus(epe_dev, m, f0, fp, fn, float(tol_neg), float(tol_pos), avg_dev, eff_dev, st));
+  return LITHO_OK;
+}
+
 }  // extern "C"

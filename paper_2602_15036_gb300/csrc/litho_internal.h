@@ -40,6 +40,8 @@ enum Stage {
   kStageIltReduce,
   kStageUpsample,
   kStageUpsampleResist,
+  kStageContours,
+  kStageEpe,
   kStageCount
 };
 // Records a CUDA event pair around its lifetime on `st` when profiling is on.
@@ -158,6 +160,15 @@ cudaError_t launch_blur_gain(const ResistTaps& taps, int n, int crop, float* gai
 // img = Re z (skipped when NULL), iblur = Im z, printed = [Im z >= threshold] (skipped when NULL).
 cudaError_t launch_band_rows_resist(const float2* q, int planes, int n, int crop, const float2* tw, float threshold,
                                     float* img, float* iblur, uint8_t* printed, cudaStream_t st);
+
+// ---- contours and edge placement (contour.cu) -----------------------------------------------
+size_t contour_workspace_bytes(int planes, int n);
+cudaError_t launch_contours(const float* img, int planes, int n, float thr, float4* seg, int* cell_id,
+                            long long capacity, long long* plane_start, void* ws, cudaStream_t st);
+cudaError_t launch_epe(const float* img, int planes, int n, float pixel_nm, float thr, const float2* pts, int m,
+                       float* epe, cudaStream_t st);
+cudaError_t launch_epe_focus(const float* epe, int m, int f0, int fp, int fn, float tol_neg, float tol_pos,
+                             float* avg, float* eff, cudaStream_t st);
 
 // ---- resist (resist.cu) ---------------------------------------------------------------------
 constexpr int kMaxResistRadius = 64;

@@ -86,6 +86,12 @@ _SIGS = {
     "litho_aerial_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]),
     "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
+    "litho_contours_workspace_size": (c_int, [c_int, c_int, POINTER(c_size_t)]),
+    "litho_contours": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p, c_void_p, ctypes.c_int64, c_void_p,
+                               c_void_p, c_size_t, c_void_p]),
+    "litho_epe": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_void_p, c_int, c_void_p, c_void_p]),
+    "litho_epe_through_focus": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_double, c_double, c_void_p,
+                                        c_void_p, c_void_p]),
     "litho_ilt_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
     "litho_ilt_grad": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_double, c_double, c_double,
                                c_int, c_void_p, POINTER(c_double), c_void_p, c_size_t, c_void_p]),
@@ -332,6 +338,63 @@ def litho_resist(intensity, pixel_nm, sigma_nm=10.0, threshold=0.3, iblur=None, 
                               c_void_p(iblur.data_ptr()), c_void_p(printed.data_ptr()) if printed is not None else None,
                               _stream_ptr(stream)))
     return iblur, printed
+
+
+def litho_contours(iblur, threshold=0.3, capacity=None, with_cells=True, stream=None):
+    """iblur: CUDA float32 [..., n, n] -> (segments [S][4] (x0, y0, x1, y1), cells [S] int32 or None,
+    plane_start [planes + 1] int64 numpy).  With capacity=None the call runs once to count and
+    again into buffers of the exact size."""
+    import torch
+    n = iblur.shape[-1]
+    planes = iblur.numel() // (n * n)
+    dev = iblur.device
+    ws_bytes = c_size_t()
+    _check(lib().litho_contours_workspace_size(planes, n, byref(ws_bytes)))
+    ws = torch.empty(ws_bytes.value, dtype=torch.uint8, device=dev)
+    starts = torch.empty(planes + 1, dtype=torch.int64, device=dev)
+
+    def run(cap):
+        seg = torch.empty((max(cap, 1), 4), dtype=torch.float32, device=dev)
+        cell = torch.empty(max(cap, 1), dtype=torch.int32, device=dev) if with_cells else None
+        _check(lib().litho_contours(c_void_p(iblur.data_ptr()), planes, n, threshold, c_void_p(seg.data_ptr()),
+                                    c_void_p(cell.data_ptr()) if cell is not None else None, cap,
+                                    c_void_p(starts.data_ptr()), c_void_p(ws.data_ptr()), ws.numel(),
+                                    _stream_ptr(stream)))
+        return seg, cell
+
+    if capacity is None:
+        run(0)
+        capacity = int(starts[-1].item())
+    seg, cell = run(capacity)
+    st = starts.cpu().numpy()
+    kept = min(capacity, int(st[-1]))
+    return seg[:kept], (cell[:kept] if cell is not None else None), st
+
+
+def litho_epe(iblur, points, pixel_nm, threshold=0.3, out=None, stream=None):
+    """iblur: CUDA float32 [planes][n][n] (or [n][n]); points: CUDA float32 [m][2] (x, y) in
+    pixels -> EPE [planes][m] in nm (Eq. (6))."""
+    import torch
+    n = iblur.shape[-1]
+    planes = iblur.numel() // (n * n)
+    m = points.shape[0]
+    assert points.is_cuda and points.dtype == torch.float32 and points.is_contiguous()
+    if out is None:
+        out = torch.empty((planes, m), dtype=torch.float32, device=iblur.device)
+    _check(lib().litho_epe(c_void_p(iblur.data_ptr()), planes, n, pixel_nm, threshold, c_void_p(points.data_ptr()),
+                           m, c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def litho_epe_through_focus(epe, f0, fp, fn, tol_neg, tol_pos, stream=None):
+    """epe: CUDA float32 [planes][m] -> (EPE_avg [m], EPE_eff [m]) (Eqs. (7)-(8))."""
+    import torch
+    planes, m = epe.shape
+    avg = torch.empty(m, dtype=torch.float32, device=epe.device)
+    eff = torch.empty(m, dtype=torch.float32, device=epe.device)
+    _check(lib().litho_epe_through_focus(c_void_p(epe.data_ptr()), planes, m, f0, fp, fn, tol_neg, tol_pos,
+                                         c_void_p(avg.data_ptr()), c_void_p(eff.data_ptr()), _stream_ptr(stream)))
+    return avg, eff
 
 
 def litho_ilt_workspace_size(kern: Kernels, b: int):
