@@ -506,6 +506,74 @@ def run_ilt(args):
     ctx.close()
 
 
+def run_contour(args):
+    """Contours and edge placement on the headline's resist images: 64 clips of 2048^2 x 3 focus
+    planes (made once, untimed, by litho_aerial_resist); one step = marching squares on every plane
+    + Eq. (6) EPE at the edge sites of every clip's target (its mask) on its 3 planes + Eqs. (7)-(8)."""
+    import paper_2602_15036_gb300 as P
+    from paper_2602_15036_gb300 import litho as L
+    ctx = Ctx(args)
+    torch = ctx.torch
+    clips = args.clips
+    kern = P.litho_make_kernels(P.make_optics(**OPTICS), N, PIXEL, FOCUS, K)
+    F = len(FOCUS)
+    masks_np = np.stack([synth.manhattan_mask(N, seed=s) for s in clip_seeds(ctx.rank, clips)])
+    stream = torch.cuda.current_stream()
+    _, iblur, _ = P.litho_aerial_resist(kern, torch.from_numpy(masks_np).to(ctx.dev), precision=HEADLINE,
+                                        sigma_nm=SIGMA_NM, threshold=THRESH, stream=stream)
+    pts = [torch.from_numpy(synth.edge_sites(m).astype(np.float32)).to(ctx.dev) for m in masks_np]
+    n_pts = sum(int(p.shape[0]) for p in pts)
+    planes = clips * F
+    ws = torch.empty(L.contours_workspace_size(planes, N), dtype=torch.uint8, device=ctx.dev)
+    starts = torch.empty(planes + 1, dtype=torch.int64, device=ctx.dev)
+    _, _, st0 = P.litho_contours(iblur, THRESH, capacity=0, with_cells=False, stream=stream)
+    capacity = int(st0[-1]) + 1024
+    seg = torch.empty((capacity, 4), dtype=torch.float32, device=ctx.dev)
+    cell = torch.empty(capacity, dtype=torch.int32, device=ctx.dev)
+    epe = [torch.empty((F, int(p.shape[0])), dtype=torch.float32, device=ctx.dev) for p in pts]
+    avg = [torch.empty(int(p.shape[0]), dtype=torch.float32, device=ctx.dev) for p in pts]
+    eff = [torch.empty(int(p.shape[0]), dtype=torch.float32, device=ctx.dev) for p in pts]
+
+    def step():
+        L.contours_into(iblur, planes, N, THRESH, seg, cell, capacity, starts, ws, stream)
+        for c in range(clips):
+            P.litho_epe(iblur[c], pts[c], PIXEL, THRESH, out=epe[c], stream=stream)
+            L.epe_through_focus_into(epe[c], 1, 2, 0, -1.0, 1.0, avg[c], eff[c], stream)
+
+    L.litho_profile_enable(True)
+    L.litho_profile_reset()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    L.litho_profile_reset()
+    step_ms, clk = time_steps(ctx, step, args.steps, 0, stream, sample_clocks=True)
+    prof = L.litho_profile_read()
+    L.litho_profile_enable(False)
+    total = ctx.max_over_ranks(sum(step_ms))
+    n_seg = int(starts[-1].item())
+    sec = lambda name: prof.get(name, (0.0, 0))[0] / args.steps * 1e-3  # noqa: E731
+    c_bytes = planes * N * N * 4.0 + n_seg * 20.0        # read every plane once, write each segment + cell
+    e_bytes = n_pts * (8.0 + F * 4.0 + 8.0)              # points in, EPE per plane and avg/eff out
+    peaks, peak_src = _peaks()
+    roof = {"bound": "hbm", "achieved": c_bytes / sec("contours") / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "kernel": "contours", "algorithmic_bytes_per_step": c_bytes, "ms_per_step": sec("contours") * 1e3,
+            "traffic": None, "peak_source": f"{peak_src} HBM copy bandwidth"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": "contour + EPE Mpx/s (2048² resist images, 3 focus planes)", "workload": "contour",
+            "value": whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
+            "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"contours+epe {clips}x2048^2 x3 focus, {n_pts} edge sites", "clips_per_gpu": clips},
+            "segments_per_step": n_seg, "edge_sites": n_pts,
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "epe_roofline": {"bound": "hbm", "achieved": e_bytes / sec("epe") / 1e9 if sec("epe") else None,
+                             "unit": "GB/s"},
+            "gpu_launches": sum(v[1] for v in prof.values()), "roofline": roof, "clocks": clk}
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Poisson stream of mixed requests through litho_serve (sizes 256..2048, DUV and EUV optics,
     K in {8,16,24}, half images and half ILT steps) at 80 % of the measured saturated rate."""
@@ -619,7 +687,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["aerial", "ilt", "serve"], default="aerial")
+    ap.add_argument("--workload", choices=["aerial", "ilt", "serve", "contour"], default="aerial")
     ap.add_argument("--precision", default=HEADLINE,
                     choices=sorted(ERROR_BOUND) + ["bf16/coarse"])
     ap.add_argument("--clips", type=int, default=64)
@@ -633,6 +701,8 @@ def main():
         run_ilt(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "contour":
+        run_contour(args)
     else:
         run_aerial(args)
 

@@ -17,6 +17,8 @@ eye against the paper's equations:
   crossings used for the edge-placement difference.
 * `ilt`     - the ILT loss over focus planes and its adjoint gradient,
   plus central finite differences.
+* `raster`  - exact area coverage of rectangle masks (the grey-level m of
+  Eq. (1) for shapes that do not fall on pixel boundaries).
 * `contour` - marching-squares contours of the resist image (section II.D)
   and the edge-placement error at control points with its through-focus
   average and effective value (Eqs. (6)-(8)).

@@ -681,7 +681,7 @@ litho_status litho_contours(const float* iblur_dev, int planes, int n, double th
 litho_status litho_epe(const float* iblur_dev, int planes, int n, double pixel_nm, double threshold,
                        const float* points_dev, int m, float* epe_dev, void* stream) {
   LITHO_REQUIRE(iblur_dev && points_dev && epe_dev, "null argument");
-  LITHO_REQUIRE(planes >= 1 && planes <= 65535 && n >= 2 && m >= 0, "planes in [1, 65535], n >= 2, m >= 0 required");
+  LITHO_REQUIRE(planes >= 1 && n >= 2 && m >= 0, "planes >= 1, n >= 2, m >= 0 required");
   LITHO_REQUIRE(pixel_nm > 0 && std::isfinite(threshold), "pixel_nm > 0 and a finite threshold required");
   LITHO_REQUIRE((reinterpret_cast<uintptr_t>(points_dev) & 7) == 0, "points_dev must be 8-byte aligned");
   if (m == 0) return LITHO_OK;

@@ -13,10 +13,12 @@
 // its inside corners when ((TL + TR) + (BR + BL)) / 4 >= T and separates them
 // otherwise.  The segment table below is that rule worked out per case.
 //
-// Three launches, all deterministic: per row of cells the number of segments
-// (block scan), one CTA scanning the row counts of every plane into global
-// offsets, and per row again the segments written at those offsets in
-// row-major cell order (saddle segments ordered by their start edge).
+// Three launches, all deterministic: per row of cells the number of segments,
+// one CTA scanning the row counts of every plane into global offsets, and per
+// row again the segments written at those offsets in row-major cell order
+// (saddle segments ordered by their start edge).  A row CTA walks its row in
+// chunks of one cell per thread, so the corner loads and the segment stores
+// of a warp are contiguous; a block scan per chunk places the segments.
 #include <cstdint>
 
 #include "litho_internal.h"
@@ -107,13 +109,6 @@ __device__ __forceinline__ float2 edge_point(const Cell& c, int e, float thr) {
   return make_float2(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y));
 }
 
-// Cells [j0, j1) of row i handled by thread `tid` of a row CTA.
-__device__ __forceinline__ void thread_cells(int n, int tid, int& j0, int& j1) {
-  const int per = (n + kRowThreads - 1) / kRowThreads;
-  j0 = min(n, tid * per);
-  j1 = min(n, j0 + per);
-}
-
 // Exclusive block scan of one int per thread; returns the thread's offset, *total the sum.
 __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
   __shared__ int warp_sums[kRowThreads / 32];
@@ -146,10 +141,8 @@ __global__ void __launch_bounds__(kRowThreads) k_ms_count(const float* __restric
                                                           int* __restrict__ row_count) {
   const int i = blockIdx.x, p = blockIdx.y;
   const float* plane = img + (size_t)p * n * n;
-  int j0, j1;
-  thread_cells(n, threadIdx.x, j0, j1);
   int cnt = 0;
-  for (int j = j0; j < j1; ++j) cnt += cell_entry(load_cell(plane, n, i, j), thr) >> 8;
+  for (int j = threadIdx.x; j < n; j += kRowThreads) cnt += cell_entry(load_cell(plane, n, i, j), thr) >> 8;
   int total;
   block_exclusive_scan(cnt, &total);
   if (threadIdx.x == 0) row_count[(size_t)p * n + i] = total;
@@ -157,30 +150,23 @@ __global__ void __launch_bounds__(kRowThreads) k_ms_count(const float* __restric
 
 // One CTA: exclusive scan of all rows' counts (planes * n of them) into
 // row_start, and plane_start[p] = row_start[p n], plane_start[planes] = total.
-__global__ void __launch_bounds__(1024) k_ms_scan(const int* __restrict__ row_count, long long rows, int n,
-                                                  int planes, long long* __restrict__ row_start,
-                                                  long long* __restrict__ plane_start) {
-  __shared__ long long part[1024];
-  const int t = threadIdx.x;
-  const long long per = (rows + 1023) / 1024, r0 = min(rows, t * per), r1 = min(rows, r0 + per);
-  long long s = 0;
-  for (long long r = r0; r < r1; ++r) s += row_count[r];
-  part[t] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the 1024 partial sums
-    const long long y = t >= o ? part[t - o] : 0;
-    __syncthreads();
-    part[t] += y;
-    __syncthreads();
-  }
-  long long run = t > 0 ? part[t - 1] : 0;
-  for (long long r = r0; r < r1; ++r) {
-    row_start[r] = run;
-    run += row_count[r];
+// Chunks of one row per thread (contiguous loads and stores), a block scan
+// per chunk, the running total carried from chunk to chunk.
+__global__ void __launch_bounds__(kRowThreads) k_ms_scan(const int* __restrict__ row_count, long long rows, int n,
+                                                         int planes, long long* __restrict__ row_start,
+                                                         long long* __restrict__ plane_start) {
+  long long run = 0;
+  for (long long r0 = 0; r0 < rows; r0 += kRowThreads) {
+    const long long r = r0 + threadIdx.x;
+    const int c = r < rows ? row_count[r] : 0;
+    int chunk;
+    const int before = block_exclusive_scan(c, &chunk);
+    if (r < rows) row_start[r] = run + before;
+    run += chunk;
   }
   __syncthreads();
-  if (t == 0) plane_start[planes] = part[1023];
-  for (int p = t; p < planes; p += 1024) plane_start[p] = row_start[(long long)p * n];
+  if (threadIdx.x == 0) plane_start[planes] = run;
+  for (int p = threadIdx.x; p < planes; p += kRowThreads) plane_start[p] = row_start[(long long)p * n];
 }
 
 __global__ void __launch_bounds__(kRowThreads) k_ms_emit(const float* __restrict__ img, int n, float thr,
@@ -189,16 +175,19 @@ __global__ void __launch_bounds__(kRowThreads) k_ms_emit(const float* __restrict
                                                          int* __restrict__ cell_id) {
   const int i = blockIdx.x, p = blockIdx.y;
   const float* plane = img + (size_t)p * n * n;
-  int j0, j1;
-  thread_cells(n, threadIdx.x, j0, j1);
-  int cnt = 0;
-  for (int j = j0; j < j1; ++j) cnt += cell_entry(load_cell(plane, n, i, j), thr) >> 8;
-  int total;
-  long long o = row_start[(size_t)p * n + i] + block_exclusive_scan(cnt, &total);
-  for (int j = j0; j < j1; ++j) {
-    const Cell c = load_cell(plane, n, i, j);
-    const uint16_t ent = cell_entry(c, thr);
+  long long base = row_start[(size_t)p * n + i];
+  for (int j0 = 0; j0 < n; j0 += kRowThreads) {  // uniform trip count: every thread takes part in each scan
+    const int j = j0 + threadIdx.x;
+    Cell c{0.f, 0.f, 0.f, 0.f};
+    uint16_t ent = 0;
+    if (j < n) {
+      c = load_cell(plane, n, i, j);
+      ent = cell_entry(c, thr);
+    }
     const int ns = ent >> 8;
+    int chunk;
+    long long o = base + block_exclusive_scan(ns, &chunk);
+    base += chunk;
     for (int k = 0; k < ns; ++k, ++o) {
       if (o >= capacity) continue;
       const int s0 = (ent >> (4 * k)) & 3, e0 = (ent >> (4 * k + 2)) & 3;
@@ -214,12 +203,14 @@ __device__ __forceinline__ float bilin(float a, float b, float c, float d, float
   return (1.f - fy) * ((1.f - fx) * a + fx * b) + fy * ((1.f - fx) * c + fx * d);
 }
 
-__global__ void k_epe(const float* __restrict__ img, int n, int m, float inv_pixel, float thr,
+// One thread per control point, every plane in turn.
+__global__ void k_epe(const float* __restrict__ img, int planes, int n, int m, float inv_pixel, float thr,
                       const float2* __restrict__ pts, float* __restrict__ epe) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x, p = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= m) return;
-  const float* I = img + (size_t)p * n * n;
   const float2 r = pts[k];
+  for (int p = 0; p < planes; ++p) {
+  const float* I = img + (size_t)p * n * n;
   const float fj = floorf(r.x), fi = floorf(r.y);
   const float fx = r.x - fj, fy = r.y - fi;
   auto wrap = [&](int v) { return ((v % n) + n) % n; };
@@ -239,6 +230,7 @@ __global__ void k_epe(const float* __restrict__ img, int n, int m, float inv_pix
                          0.5f * (v[3][2] - v[1][2]), fx, fy);
   const float g = sqrtf(gx * gx + gy * gy) * inv_pixel;
   epe[(size_t)p * m + k] = g > 0.f ? -(e - thr) / g : __int_as_float(0x7fc00000);
+  }
 }
 
 __global__ void k_epe_focus(const float* __restrict__ epe, int m, int f0, int fp, int fn, float tol_neg,
@@ -265,14 +257,14 @@ cudaError_t launch_contours(const float* img, int planes, int n, float thr, floa
   long long* row_start =
       reinterpret_cast<long long*>(static_cast<char*>(ws) + (rows * sizeof(int) + 255) / 256 * 256);
   k_ms_count<<<dim3(n, planes), kRowThreads, 0, st>>>(img, n, thr, row_count);
-  k_ms_scan<<<1, 1024, 0, st>>>(row_count, (long long)rows, n, planes, row_start, plane_start);
+  k_ms_scan<<<1, kRowThreads, 0, st>>>(row_count, (long long)rows, n, planes, row_start, plane_start);
   k_ms_emit<<<dim3(n, planes), kRowThreads, 0, st>>>(img, n, thr, row_start, capacity, seg, cell_id);
   return cudaGetLastError();
 }
 
 cudaError_t launch_epe(const float* img, int planes, int n, float pixel_nm, float thr, const float2* pts, int m,
                        float* epe, cudaStream_t st) {
-  k_epe<<<dim3((m + 255) / 256, planes), 256, 0, st>>>(img, n, m, 1.0f / pixel_nm, thr, pts, epe);
+  k_epe<<<(m + 255) / 256, 256, 0, st>>>(img, planes, n, m, 1.0f / pixel_nm, thr, pts, epe);
   return cudaGetLastError();
 }
 

@@ -371,6 +371,28 @@ def litho_contours(iblur, threshold=0.3, capacity=None, with_cells=True, stream=
     return seg[:kept], (cell[:kept] if cell is not None else None), st
 
 
+def contours_workspace_size(planes: int, n: int) -> int:
+    out = c_size_t()
+    _check(lib().litho_contours_workspace_size(planes, n, byref(out)))
+    return out.value
+
+
+def contours_into(iblur, planes, n, threshold, seg, cell, capacity, plane_start, workspace, stream=None):
+    """litho_contours into caller buffers (CUDA tensors), asynchronous: no host synchronisation."""
+    _check(lib().litho_contours(c_void_p(iblur.data_ptr()), planes, n, threshold, c_void_p(seg.data_ptr()),
+                                c_void_p(cell.data_ptr()) if cell is not None else None, capacity,
+                                c_void_p(plane_start.data_ptr()), c_void_p(workspace.data_ptr()), workspace.numel(),
+                                _stream_ptr(stream)))
+
+
+def epe_through_focus_into(epe, f0, fp, fn, tol_neg, tol_pos, avg, eff, stream=None):
+    """litho_epe_through_focus into caller buffers, asynchronous."""
+    planes, m = epe.shape
+    _check(lib().litho_epe_through_focus(c_void_p(epe.data_ptr()), planes, m, f0, fp, fn, tol_neg, tol_pos,
+                                         c_void_p(avg.data_ptr()) if avg is not None else None,
+                                         c_void_p(eff.data_ptr()) if eff is not None else None, _stream_ptr(stream)))
+
+
 def litho_epe(iblur, points, pixel_nm, threshold=0.3, out=None, stream=None):
     """iblur: CUDA float32 [planes][n][n] (or [n][n]); points: CUDA float32 [m][2] (x, y) in
     pixels -> EPE [planes][m] in nm (Eq. (6))."""
