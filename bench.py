@@ -574,6 +574,61 @@ def run_contour(args):
     ctx.close()
 
 
+def run_raster(args):
+    """Area-coverage rasterisation of the headline's masks as shapes off the pixel grid: the
+    Manhattan generator's rectangles of 64 clips of 2048^2, shifted by (0.3, 0.6) px so that
+    every edge is a grey level; one step = litho_rasterize of all clips."""
+    import paper_2602_15036_gb300 as P  # noqa: F401
+    from paper_2602_15036_gb300 import litho as L
+    ctx = Ctx(args)
+    torch = ctx.torch
+    clips = args.clips
+    rl = []
+    for s_ in clip_seeds(ctx.rank, clips):
+        r, _ = synth.manhattan_rects(N, seed=s_)
+        x0, y0 = r[:, 0] + 0.3, r[:, 1] + 0.6
+        rl.append(np.stack([x0, y0, x0 + r[:, 2], y0 + r[:, 3]], axis=1).astype(np.float32))
+    counts = [len(r) for r in rl]
+    start = torch.from_numpy(np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)).to(ctx.dev)
+    rects = torch.from_numpy(np.concatenate(rl)).to(ctx.dev)
+    max_rects, max_side = max(counts), 16
+    ws = torch.empty(L.rasterize_workspace_size(clips, N, max_rects, max_side), dtype=torch.uint8, device=ctx.dev)
+    mask = torch.empty((clips, N, N), dtype=torch.float32, device=ctx.dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        L.rasterize_into(rects, start, clips, max_rects, max_side, N, mask, ws, stream)
+
+    L.litho_profile_enable(True)
+    L.litho_profile_reset()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    L.litho_profile_reset()
+    step_ms, clk = time_steps(ctx, step, args.steps, 0, stream, sample_clocks=True)
+    prof = L.litho_profile_read()
+    L.litho_profile_enable(False)
+    total = ctx.max_over_ranks(sum(step_ms))
+    grey = float(((mask > 0) & (mask < 1)).float().mean().item())
+    nbytes = clips * N * N * 4.0 + sum(counts) * 16.0
+    peaks, peak_src = _peaks()
+    sec = total / args.steps * 1e-3
+    roof = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "kernel": "raster", "algorithmic_bytes_per_step": nbytes, "traffic": None,
+            "peak_source": f"{peak_src} HBM copy bandwidth"}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    line = {"metric": "area-coverage rasterisation Mpx/s (2048² clips)", "workload": "raster",
+            "value": whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
+            "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"raster {clips}x2048^2, {sum(counts)} rectangles", "clips_per_gpu": clips},
+            "grey_pixel_fraction": grey, "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "gpu_launches": sum(v[1] for v in prof.values()), "roofline": roof, "clocks": clk}
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Poisson stream of mixed requests through litho_serve (sizes 256..2048, DUV and EUV optics,
     K in {8,16,24}, half images and half ILT steps) at 80 % of the measured saturated rate."""
@@ -687,7 +742,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["aerial", "ilt", "serve", "contour"], default="aerial")
+    ap.add_argument("--workload", choices=["aerial", "ilt", "serve", "contour", "raster"], default="aerial")
     ap.add_argument("--precision", default=HEADLINE,
                     choices=sorted(ERROR_BOUND) + ["bf16/coarse"])
     ap.add_argument("--clips", type=int, default=64)
@@ -703,6 +758,8 @@ def main():
         run_serve(args)
     elif args.workload == "contour":
         run_contour(args)
+    elif args.workload == "raster":
+        run_raster(args)
     else:
         run_aerial(args)
 

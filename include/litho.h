@@ -6,6 +6,7 @@
  *     I(x) = D * sum_k lam_k |(phi_k (x) m)(x)|^2, over K TCC eigen-kernels and
  *     several focus planes (paper Section III.A, Eqs. (1)-(4));
  *   - the Gaussian-blur + threshold resist (Eq. (5));
+ *   - exact area-coverage rasterisation of rectangle masks;
  *   - marching-squares contours of the resist image and the edge-placement
  *     error at target control points, through focus (Section II.D, Eqs. (6)-(8));
  *   - the ILT mask gradient through the resist and imaging (the adjoint of the
@@ -238,6 +239,27 @@ size_t litho_aerial_noalloc_max_bytes(void);
  * radius must be below n/2. */
 litho_status litho_resist(const float* intensity_dev, int planes, int n, double pixel_nm, double sigma_nm,
                           double threshold, float* iblur_dev, uint8_t* printed_dev, void* stream);
+
+/* ---- rectangle masks to grey levels (the object m of Eq. (1)) --------------------------------- */
+
+/* Area-coverage rasterisation: mask[c][i][j] = area of the union of clip c's
+ * rectangles inside pixel [j, j+1) x [i, i+1) (pixel units, x = column,
+ * y = row), periodic with period n, overlapping rectangles counted once; so
+ * shapes off the pixel grid become exact grey levels instead of centre
+ * samples (exact up to FP32 rounding).  Rectangles rects_dev[4 r .. 4 r + 3] =
+ * (x0, y0, x1, y1) (f32, 16-byte aligned), clip c owning r in
+ * [rect_start[c], rect_start[c+1]) (int64, device); max_rects bounds any one
+ * clip's count, max_side_px every side (0 < x1 - x0 <= max_side_px, same in
+ * y); a clip with more rectangles or one outside those bounds gets an all-NaN
+ * mask.  n a multiple
+ * of 16.  Workspace: litho_rasterize_workspace_size bytes (it holds the
+ * rectangles' tile lists, (ceil(max_side_px/16) + 5)^2 entries of 16 bytes per
+ * rectangle), 256-byte aligned.  Asynchronous (five launches).  Errors: EINVAL,
+ * ENOMEM (workspace too small), ECUDA. */
+litho_status litho_rasterize_workspace_size(int b, int n, int64_t max_rects, int max_side_px, size_t* bytes);
+litho_status litho_rasterize(const float* rects_dev, const int64_t* rect_start_dev, int b, int64_t max_rects,
+                             int max_side_px, int n, float* mask_dev, void* workspace_dev, size_t workspace_bytes,
+                             void* stream);
 
 /* ---- contours and edge placement (paper section II.D, Eqs. (6)-(8)) ----------------------------- */
 

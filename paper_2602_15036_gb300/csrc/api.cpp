@@ -650,6 +650,42 @@ litho_status litho_resist(const float* intensity_dev, int planes, int n, double 
   return LITHO_OK;
 }
 
+// ---- rectangle rasterisation -------------------------------------------------------------------
+
+static bool raster_args_ok(int b, int n, int64_t max_rects, int max_side_px) {
+  return b >= 1 && b <= 65535 && n >= 16 && n % 16 == 0 && n <= 65536 && max_rects >= 0 && max_side_px >= 1 &&
+         max_side_px <= n && max_rects * raster_tiles_per_rect(max_side_px) < (int64_t(1) << 31);
+}
+
+litho_status litho_rasterize_workspace_size(int b, int n, int64_t max_rects, int max_side_px, size_t* bytes) {
+  LITHO_REQUIRE(bytes, "null argument");
+  LITHO_REQUIRE(raster_args_ok(b, n, max_rects, max_side_px),
+                "need 1 <= b <= 65535, n a multiple of 16, 1 <= max_side_px <= n and a bounded tile list");
+  *bytes = raster_workspace_bytes(b, n, max_rects, max_side_px);
+  return LITHO_OK;
+}
+
+litho_status litho_rasterize(const float* rects_dev, const int64_t* rect_start_dev, int b, int64_t max_rects,
+                             int max_side_px, int n, float* mask_dev, void* workspace_dev, size_t workspace_bytes,
+                             void* stream) {
+  LITHO_REQUIRE(rect_start_dev && mask_dev && workspace_dev && (rects_dev || max_rects == 0), "null argument");
+  LITHO_REQUIRE(raster_args_ok(b, n, max_rects, max_side_px),
+                "need 1 <= b <= 65535, n a multiple of 16, 1 <= max_side_px <= n and a bounded tile list");
+  LITHO_REQUIRE((reinterpret_cast<uintptr_t>(rects_dev) & 15) == 0 && (reinterpret_cast<uintptr_t>(workspace_dev) & 255) == 0,
+                "rects_dev must be 16-byte and workspace 256-byte aligned");
+  const size_t need = raster_workspace_bytes(b, n, max_rects, max_side_px);
+  if (workspace_bytes < need) {
+    set_error("workspace too small: %zu bytes given, %zu needed", workspace_bytes, need);
+    return LITHO_ENOMEM;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ProfScope ps(kStageRaster, st, 5);
+  LITHO_TRY_CUDA(launch_raster(reinterpret_cast<const float4*>(rects_dev),
+                               reinterpret_cast<const long long*>(rect_start_dev), b, max_rects, max_side_px, n,
+                               mask_dev, workspace_dev, st));
+  return LITHO_OK;
+}
+
 // ---- contours and edge placement ---------------------------------------------------------------
 
 litho_status litho_contours_workspace_size(int planes, int n, size_t* bytes) {

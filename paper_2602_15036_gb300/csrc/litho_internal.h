@@ -42,6 +42,7 @@ enum Stage {
   kStageUpsampleResist,
   kStageContours,
   kStageEpe,
+  kStageRaster,
   kStageCount
 };
 // Records a CUDA event pair around its lifetime on `st` when profiling is on.
@@ -160,6 +161,12 @@ cudaError_t launch_blur_gain(const ResistTaps& taps, int n, int crop, float* gai
 // img = Re z (skipped when NULL), iblur = Im z, printed = [Im z >= threshold] (skipped when NULL).
 cudaError_t launch_band_rows_resist(const float2* q, int planes, int n, int crop, const float2* tw, float threshold,
                                     float* img, float* iblur, uint8_t* printed, cudaStream_t st);
+
+// ---- rectangle rasterisation (raster.cu) -----------------------------------------------------
+long long raster_tiles_per_rect(int max_side);
+size_t raster_workspace_bytes(int b, int n, long long max_rects, int max_side);
+cudaError_t launch_raster(const float4* rects, const long long* rect_start, int b, long long max_rects,
+                          int max_side, int n, float* mask, void* ws, cudaStream_t st);
 
 // ---- contours and edge placement (contour.cu) -----------------------------------------------
 size_t contour_workspace_bytes(int planes, int n);

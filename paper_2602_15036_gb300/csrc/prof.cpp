@@ -14,7 +14,7 @@ namespace {
 const char* kStageNames[kStageCount] = {"mask_spectrum", "stage1_fft", "stage2_fft", "stage1_gemm_operands",
                                         "stage2_gemm",   "resist",     "ilt_forward", "ilt_backward",
                                         "ilt_reduce",    "upsample",   "upsample_resist", "contours",
-                                        "epe"};
+                                        "epe",           "raster"};
 
 struct Rec {
   int stage, launches;

@@ -86,6 +86,9 @@ _SIGS = {
     "litho_aerial_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]),
     "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
+    "litho_rasterize_workspace_size": (c_int, [c_int, c_int, ctypes.c_int64, c_int, POINTER(c_size_t)]),
+    "litho_rasterize": (c_int, [c_void_p, c_void_p, c_int, ctypes.c_int64, c_int, c_int, c_void_p, c_void_p,
+                                c_size_t, c_void_p]),
     "litho_contours_workspace_size": (c_int, [c_int, c_int, POINTER(c_size_t)]),
     "litho_contours": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p, c_void_p, ctypes.c_int64, c_void_p,
                                c_void_p, c_size_t, c_void_p]),
@@ -369,6 +372,42 @@ def litho_contours(iblur, threshold=0.3, capacity=None, with_cells=True, stream=
     st = starts.cpu().numpy()
     kept = min(capacity, int(st[-1]))
     return seg[:kept], (cell[:kept] if cell is not None else None), st
+
+
+def litho_rasterize(rects, n, max_side_px, device="cuda", out=None, stream=None):
+    """rects: list (one entry per clip) of float arrays [R_c][4] (x0, y0, x1, y1) in pixels ->
+    CUDA float32 [b][n][n] area-coverage masks."""
+    import torch
+    b = len(rects)
+    counts = [int(np.asarray(r).reshape(-1, 4).shape[0]) for r in rects]
+    start = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    flat = np.concatenate([np.asarray(r, dtype=np.float32).reshape(-1, 4) for r in rects] +
+                          [np.zeros((1, 4), np.float32)])
+    d_rects = torch.from_numpy(flat).to(device)
+    d_start = torch.from_numpy(start).to(device)
+    max_rects = max(counts) if counts else 0
+    ws_bytes = c_size_t()
+    _check(lib().litho_rasterize_workspace_size(b, n, max_rects, max_side_px, byref(ws_bytes)))
+    ws = torch.empty(ws_bytes.value, dtype=torch.uint8, device=device)
+    if out is None:
+        out = torch.empty((b, n, n), dtype=torch.float32, device=device)
+    _check(lib().litho_rasterize(c_void_p(d_rects.data_ptr()), c_void_p(d_start.data_ptr()), b, max_rects,
+                                 max_side_px, n, c_void_p(out.data_ptr()), c_void_p(ws.data_ptr()), ws.numel(),
+                                 _stream_ptr(stream)))
+    return out
+
+
+def rasterize_workspace_size(b: int, n: int, max_rects: int, max_side_px: int) -> int:
+    out = c_size_t()
+    _check(lib().litho_rasterize_workspace_size(b, n, max_rects, max_side_px, byref(out)))
+    return out.value
+
+
+def rasterize_into(rects, rect_start, b, max_rects, max_side_px, n, mask, workspace, stream=None):
+    """litho_rasterize on CUDA tensors (rects [R][4] f32, rect_start [b+1] int64), asynchronous."""
+    _check(lib().litho_rasterize(c_void_p(rects.data_ptr()), c_void_p(rect_start.data_ptr()), b, max_rects,
+                                 max_side_px, n, c_void_p(mask.data_ptr()), c_void_p(workspace.data_ptr()),
+                                 workspace.numel(), _stream_ptr(stream)))
 
 
 def contours_workspace_size(planes: int, n: int) -> int:

@@ -84,10 +84,11 @@ def random_rect_mask(n: int, seed: int, count: int = 40, side_lo: int = 5, side_
     return rasterize_rects(n, np.array(rects))
 
 
-def manhattan_mask(n: int, seed: int, density: float = 0.35, side_lo: int = 5, side_hi: int = 15,
-                   block: int = 64) -> np.ndarray:
+def manhattan_rects(n: int, seed: int, density: float = 0.35, side_lo: int = 5, side_hi: int = 15,
+                    block: int = 64):
     """Rectangles as in `random_rect_mask`, added in blocks of `block` until the
-    covered fraction reaches `density` (checked after each block).
+    covered fraction reaches `density` (checked after each block).  Returns
+    (rects [R][4] as integer (x0, y0, w, h), the centre-sampled mask).
 
     Draw order per block: `block` (width, height) pairs, then `block` (x0, y0)
     pairs.  Coverage is counted incrementally (newly covered pixels per rectangle).
@@ -96,10 +97,12 @@ def manhattan_mask(n: int, seed: int, density: float = 0.35, side_lo: int = 5, s
     m = np.zeros((n, n), dtype=np.float32)
     covered = 0
     target = density * n * n
+    rects = []
     while covered < target:
         wh = st.integers(side_lo, side_hi, 2 * block).reshape(block, 2)
         xy = st.integers(0, n - 1, 2 * block).reshape(block, 2)
         for (w, h), (x0, y0) in zip(wh, xy):
+            rects.append((int(x0), int(y0), int(w), int(h)))
             if x0 + w <= n and y0 + h <= n:
                 view = m[y0:y0 + h, x0:x0 + w]
                 covered += int(view.size - np.count_nonzero(view))
@@ -108,7 +111,13 @@ def manhattan_mask(n: int, seed: int, density: float = 0.35, side_lo: int = 5, s
                 ix = np.ix_(np.arange(y0, y0 + h) % n, np.arange(x0, x0 + w) % n)
                 covered += int(w * h - np.count_nonzero(m[ix]))
                 m[ix] = 1.0
-    return m
+    return np.array(rects, dtype=np.int64).reshape(-1, 4), m
+
+
+def manhattan_mask(n: int, seed: int, density: float = 0.35, side_lo: int = 5, side_hi: int = 15,
+                   block: int = 64) -> np.ndarray:
+    """The centre-sampled mask of `manhattan_rects`."""
+    return manhattan_rects(n, seed, density, side_lo, side_hi, block)[1]
 
 
 def blob_field(n: int, pixel_nm: float, seed: int, count: int = 60, r_lo_nm: float = 30.0,
