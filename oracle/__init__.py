@@ -17,6 +17,8 @@ eye against the paper's equations:
   crossings used for the edge-placement difference.
 * `ilt`     - the ILT loss over focus planes and its adjoint gradient,
   plus central finite differences.
+* `ai`      - the AI initialiser's input channels (Eq. (9)) and the
+  print-consistency images and loss (Eqs. (15)-(17)).
 * `raster`  - exact area coverage of rectangle masks (the grey-level m of
   Eq. (1) for shapes that do not fall on pixel boundaries).
 * `contour` - marching-squares contours of the resist image (section II.D)
