@@ -240,6 +240,42 @@ size_t litho_aerial_noalloc_max_bytes(void);
 litho_status litho_resist(const float* intensity_dev, int planes, int n, double pixel_nm, double sigma_nm,
                           double threshold, float* iblur_dev, uint8_t* printed_dev, void* stream);
 
+/* ---- gradients of the image and the AI initialiser's inputs (paper Eqs. (9), (15)-(17)) ---------- */
+
+/* Vector-Jacobian product of Eq. (4): dm[c][x'] = sum over the planes f in
+ * [f_first, f_first + f_count) of sum_x q[c][f][x] dI_f(x)/dm(x') for masks
+ * mask[c] (f32 [b][n][n]), with q = upstream_dev[b][n_focus][n][n] (the
+ * planes outside the range are not read) or, when upstream_dev is NULL, 1 on
+ * every pixel (the gradient of the total intensity).  The same adjoint as
+ * litho_ilt_grad without the resist and sigmoid factors: 2 D N^-2 Re IDFT of
+ * sum_k lam_k conj(Phi_k) DFT_crop(q E_k).  Workspace as litho_ilt_workspace_size
+ * (the smaller size evaluates one plane at a time).  FP32 FFT path.  Async. */
+litho_status litho_intensity_vjp_workspace_size(const litho_kernels* h, int b, size_t* full_bytes, size_t* min_bytes);
+litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, int b, double dose, int f_first,
+                                 int f_count, const float* upstream_dev, float* dm_dev, void* workspace_dev,
+                                 size_t workspace_bytes, void* stream);
+
+/* Eq. (9): the three input channels of the AI initialiser for binary targets
+ * Z_t = target[b][n][n] (0/1 f32): x[c][0] = Z_t, x[c][1] = I0 / max I0 with I0
+ * the aerial image of the target at plane `focus`, x[c][2] = (g - min g) /
+ * (max g - min g) with g the gradient of that plane's total intensity with
+ * respect to the mask (litho_intensity_vjp of ones), the extremes taken over
+ * the batch (a constant channel becomes 0).  x is f32 [b][3][n][n].  Workspace:
+ * litho_ai_inputs_workspace_size bytes, 256-byte aligned.  Async. */
+litho_status litho_ai_inputs_workspace_size(const litho_kernels* h, size_t* bytes);
+litho_status litho_ai_inputs(const litho_kernels* h, const float* target_dev, int b, double dose, int focus,
+                             float* x_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Eqs. (15)-(17): z_round = [G (x) Z_t >= tau_round] with G the periodic,
+ * normalised Gaussian of sigma_round_nm truncated at 4 sigma (as
+ * litho_resist), z_print = [I >= tau_print] on the images intensity[b][n][n],
+ * and, when loss_dev is not NULL, loss[c] = sum |z_print - z_round| (int64, the
+ * number of pixels where the two differ).  blur_dev (f32 [b][n][n]) receives
+ * G (x) Z_t.  n a multiple of 32.  Async. */
+litho_status litho_print_images(const float* target_dev, const float* intensity_dev, int b, int n, double pixel_nm,
+                                double sigma_round_nm, double tau_round, double tau_print, uint8_t* z_round_dev,
+                                uint8_t* z_print_dev, int64_t* loss_dev, float* blur_dev, void* stream);
+
 /* ---- rectangle masks to grey levels (the object m of Eq. (1)) --------------------------------- */
 
 /* Area-coverage rasterisation: mask[c][i][j] = area of the union of clip c's

@@ -1,0 +1,213 @@
+// Input channels of the AI initialiser (paper Eq. (9)) and its
+// lithography-consistency images (Eqs. (15)-(17)).
+//
+// Eq. (9), as read here: X[c] = (Z_t, I0 / max I0, (dI/dM - min) / (max - min))
+// with I0 the aerial image of the target at one focus plane, dI/dM the
+// gradient of the plane's total intensity with respect to the mask pixels
+// (the adjoint of Eq. (4) applied to ones, litho_intensity_vjp) and the
+// extremes taken over the whole batch (a constant channel maps to 0).
+// Eqs. (15)-(17): Z_round = [G (x) Z_t >= tau_round] with the resist's
+// periodic Gaussian, Z_print = [I >= tau_print], L_litho = sum |Z_print -
+// Z_round| per clip (an integer count, reduced in a fixed order).
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "litho_internal.h"
+
+namespace litho {
+
+namespace {
+
+constexpr int kReduceBlocks = 304, kReduceThreads = 256;
+
+// Per-block minimum and maximum of channel `ch` of X[b][3][nn].
+__global__ void __launch_bounds__(kReduceThreads) k_minmax(const float* __restrict__ x, int b, size_t nn, int ch,
+                                                           float2* __restrict__ part) {
+  __shared__ float smin[kReduceThreads], smax[kReduceThreads];
+  float lo = FLT_MAX, hi = -FLT_MAX;
+  const size_t total = size_t(b) * nn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = x[(i / nn) * 3 * nn + size_t(ch) * nn + i % nn];
+    lo = fminf(lo, v);
+    hi = fmaxf(hi, v);
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int o = kReduceThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smin[threadIdx.x] = fminf(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = make_float2(smin[0], smax[0]);
+}
+
+// Channel ch of every clip: v -> (v - lo) * s, with lo and s from the block
+// partials (mode 0: lo = 0, s = 1/max; mode 1: lo = min, s = 1/(max - min);
+// s = 0 when the range is empty).
+__global__ void k_normalize(float* __restrict__ x, int b, size_t nn, int ch, const float2* __restrict__ part,
+                            int nparts, int mode) {
+  __shared__ float lo_s, s_s;
+  if (threadIdx.x == 0) {
+    float lo = FLT_MAX, hi = -FLT_MAX;
+    for (int k = 0; k < nparts; ++k) {
+      lo = fminf(lo, part[k].x);
+      hi = fmaxf(hi, part[k].y);
+    }
+    if (mode == 0) lo = 0.f;
+    lo_s = lo;
+    s_s = hi > lo ? 1.0f / (hi - lo) : 0.f;
+  }
+  __syncthreads();
+  const float lo = lo_s, s = s_s;
+  const size_t total = size_t(b) * nn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    float* p = x + (i / nn) * 3 * nn + size_t(ch) * nn + i % nn;
+    *p = (*p - lo) * s;
+  }
+}
+
+__global__ void k_copy_channel(const float* __restrict__ src, float* __restrict__ x, int b, size_t nn, int ch) {
+  const size_t total = size_t(b) * nn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    x[(i / nn) * 3 * nn + size_t(ch) * nn + i % nn] = src[i];
+}
+
+__global__ void k_threshold(const float* __restrict__ img, size_t count, float thr, uint8_t* __restrict__ z) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    z[i] = img[i] >= thr ? 1 : 0;
+}
+
+// One CTA per clip: number of pixels where the two prints differ.
+__global__ void __launch_bounds__(kReduceThreads) k_l1_count(const uint8_t* __restrict__ a,
+                                                             const uint8_t* __restrict__ b, size_t nn,
+                                                             long long* __restrict__ out) {
+  __shared__ long long s[kReduceThreads];
+  const size_t base = size_t(blockIdx.x) * nn;
+  long long c = 0;
+  for (size_t i = threadIdx.x; i < nn; i += kReduceThreads) c += a[base + i] != b[base + i];
+  s[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = kReduceThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = s[0];
+}
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+// Forward scratch of one clip at one plane: row spectrum, crop spectrum, stage-1 fields.
+size_t ai_forward_bytes(const litho_kernels* h) {
+  const size_t N = h->n, C = h->crop, K = h->k;
+  return up256(N * C * 8) + up256(C * C * 8) + up256(K * N * C * 8);
+}
+
+}  // namespace
+
+}  // namespace litho
+
+using namespace litho;
+
+extern "C" {
+
+litho_status litho_ai_inputs_workspace_size(const litho_kernels* h, size_t* bytes) {
+  if (!h || !bytes) {
+    set_error("null argument");
+    return LITHO_EINVAL;
+  }
+  size_t vjp_min = 0;
+  litho_status s = litho_intensity_vjp_workspace_size(h, 1, nullptr, &vjp_min);
+  if (s != LITHO_OK) return s;
+  *bytes = std::max(ai_forward_bytes(h), vjp_min) + up256(kReduceBlocks * sizeof(float2));
+  return LITHO_OK;
+}
+
+litho_status litho_ai_inputs(const litho_kernels* h, const float* target_dev, int b, double dose, int focus,
+                             float* x_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
+  if (!h || !target_dev || !x_dev || !workspace_dev || b < 1) {
+    set_error("null argument or b < 1");
+    return LITHO_EINVAL;
+  }
+  if (focus < 0 || focus >= h->n_focus || !std::isfinite(dose)) {
+    set_error("focus must index a plane of the kernel set; dose finite");
+    return LITHO_EINVAL;
+  }
+  size_t need = 0;
+  litho_status s = litho_ai_inputs_workspace_size(h, &need);
+  if (s != LITHO_OK) return s;
+  if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) != 0) {
+    set_error("workspace must be 256-byte aligned and hold %zu bytes (%zu given)", need, workspace_bytes);
+    return workspace_bytes < need ? LITHO_ENOMEM : LITHO_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int N = h->n, C = h->crop, K = h->k;
+  const size_t nn = size_t(N) * N;
+  char* w = static_cast<char*>(workspace_dev);
+  float2* part = reinterpret_cast<float2*>(w + (need - up256(kReduceBlocks * sizeof(float2))));
+  float2* rowbuf = reinterpret_cast<float2*>(w);
+  float2* mhat = reinterpret_cast<float2*>(w + up256(size_t(N) * C * 8));
+  float2* t1 = reinterpret_cast<float2*>(w + up256(size_t(N) * C * 8) + up256(size_t(C) * C * 8));
+  {
+    ProfScope ps(kStageIltForward, st, 1 + 4 * b);
+    k_copy_channel<<<512, 256, 0, st>>>(target_dev, x_dev, b, nn, 0);
+    LITHO_TRY_CUDA(cudaGetLastError());
+    for (int c = 0; c < b; ++c) {  // channel 1: the aerial image of the target at plane `focus`
+      LITHO_TRY_CUDA(launch_mask_spectrum(target_dev + c * nn, 1, N, C, h->d_tw, rowbuf, mhat, st));
+      LITHO_TRY_CUDA(launch_stage1_fft(mhat, h->d_phi + size_t(focus) * K * C * C, K, N, C, h->d_tw, t1, st));
+      LITHO_TRY_CUDA(launch_stage2_fft(t1, h->d_lambda + size_t(focus) * K, K, N, C, float(dose), h->d_tw,
+                                       x_dev + (size_t(c) * 3 + 1) * nn, 1, (long long)K * N * C, (long long)nn,
+                                       st));
+    }
+  }
+  for (int c = 0; c < b; ++c) {  // channel 2: the gradient of the plane's total intensity
+    s = litho_intensity_vjp(h, target_dev + c * nn, 1, dose, focus, 1, nullptr, x_dev + (size_t(c) * 3 + 2) * nn,
+                            workspace_dev, need - up256(kReduceBlocks * sizeof(float2)), stream);
+    if (s != LITHO_OK) return s;
+  }
+  ProfScope ps(kStageIltReduce, st, 4);
+  for (int ch = 1; ch <= 2; ++ch) {
+    k_minmax<<<kReduceBlocks, kReduceThreads, 0, st>>>(x_dev, b, nn, ch, part);
+    k_normalize<<<512, 256, 0, st>>>(x_dev, b, nn, ch, part, kReduceBlocks, ch == 1 ? 0 : 1);
+  }
+  LITHO_TRY_CUDA(cudaGetLastError());
+  return LITHO_OK;
+}
+
+litho_status litho_print_images(const float* target_dev, const float* intensity_dev, int b, int n, double pixel_nm,
+                                double sigma_round_nm, double tau_round, double tau_print, uint8_t* z_round_dev,
+                                uint8_t* z_print_dev, int64_t* loss_dev, float* blur_dev, void* stream) {
+  if (!target_dev || !intensity_dev || !z_round_dev || !z_print_dev || !blur_dev || b < 1 || n < 32 || n % 32) {
+    set_error("null argument, b < 1, or n not a multiple of 32");
+    return LITHO_EINVAL;
+  }
+  if (!std::isfinite(tau_round) || !std::isfinite(tau_print)) {
+    set_error("thresholds must be finite");
+    return LITHO_EINVAL;
+  }
+  ResistTaps taps;
+  std::string why;
+  if (!resist_taps(sigma_round_nm, pixel_nm, &taps, &why)) {
+    set_error("%s", why.c_str());
+    return LITHO_EINVAL;
+  }
+  if (2 * taps.radius >= n) {
+    set_error("blur radius must be below n/2");
+    return LITHO_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nn = size_t(n) * n;
+  ProfScope ps(kStageResist, st, loss_dev ? 3 : 2);
+  LITHO_TRY_CUDA(launch_resist(target_dev, b, n, taps, float(tau_round), blur_dev, z_round_dev, st));
+  k_threshold<<<1024, 256, 0, st>>>(intensity_dev, size_t(b) * nn, float(tau_print), z_print_dev);
+  if (loss_dev)
+    k_l1_count<<<b, kReduceThreads, 0, st>>>(z_print_dev, z_round_dev, nn, reinterpret_cast<long long*>(loss_dev));
+  LITHO_TRY_CUDA(cudaGetLastError());
+  return LITHO_OK;
+}
+
+}  // extern "C"

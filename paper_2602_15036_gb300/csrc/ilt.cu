@@ -165,6 +165,10 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
   }
 }
 
+__global__ void k_fill(float* __restrict__ p, float v, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
 __global__ void k_sum_planes(const float2* __restrict__ sk, int planes, size_t cc, float2* __restrict__ s,
                              int accumulate) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cc; i += (size_t)gridDim.x * blockDim.x) {
@@ -194,11 +198,15 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_grad_rows(const float2* __restr
     const int c = freq_of_idx(idx, N) + half;
     return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
   };
-  const float* mr = m + (size_t)y * N;
+  const float* mr = m ? m + (size_t)y * N : nullptr;
   float* gr = grad + (size_t)y * N;
   auto use = [&](int, int, int x, float2 v) {
-    const float mm = mr[x];
-    gr[x] = scale * v.x * alpha * mm * (1.0f - mm);
+    if (m) {
+      const float mm = mr[x];
+      gr[x] = scale * v.x * alpha * mm * (1.0f - mm);
+    } else {
+      gr[x] = scale * v.x;  // no chain factor: the gradient with respect to m itself
+    }
   };
   fft_load_use<N, +1>(buf, tw, t, load, use);
 }
@@ -408,6 +416,63 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
   if (loss_host) {
     LITHO_TRY_CUDA(cudaMemcpyAsync(loss_host, L.loss, size_t(b) * sizeof(double), cudaMemcpyDeviceToHost, st));
     LITHO_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  return LITHO_OK;
+}
+
+litho_status litho_intensity_vjp_workspace_size(const litho_kernels* h, int b, size_t* full_bytes, size_t* min_bytes) {
+  return litho_ilt_workspace_size(h, b, full_bytes, min_bytes);
+}
+
+litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, int b, double dose, int f_first,
+                                 int f_count, const float* upstream_dev, float* dm_dev, void* workspace_dev,
+                                 size_t workspace_bytes, void* stream) {
+  if (!h || !mask_dev || !dm_dev || !workspace_dev || b < 1) {
+    set_error("null argument or b < 1");
+    return LITHO_EINVAL;
+  }
+  if (f_first < 0 || f_count < 1 || f_first + f_count > h->n_focus || !std::isfinite(dose)) {
+    set_error("focus planes [f_first, f_first + f_count) must lie in [0, n_focus); dose finite");
+    return LITHO_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) != 0) {
+    set_error("workspace must be 256-byte aligned");
+    return LITHO_EINVAL;
+  }
+  const int F = h->n_focus, K = h->k, N = h->n, C = h->crop;
+  const size_t full = ilt_layout(h, b, f_count, nullptr).bytes, mn = ilt_layout(h, b, 1, nullptr).bytes;
+  int P;
+  if (workspace_bytes >= full) {
+    P = f_count;
+  } else if (workspace_bytes >= mn) {
+    P = 1;
+  } else {
+    set_error("workspace too small: %zu bytes given, at least %zu needed", workspace_bytes, mn);
+    return LITHO_ENOMEM;
+  }
+  IltLayout L = ilt_layout(h, b, P, workspace_dev);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nn = size_t(N) * N;
+  const float scale = float(2.0 * dose / (double(N) * double(N)));
+  ProfScope ps(kStageIltBackward, st, 1);
+  if (!upstream_dev) {  // dL/dI = 1 on every pixel of the selected planes
+    k_fill<<<256, 256, 0, st>>>(L.img, 1.0f, size_t(P) * nn);
+    LITHO_TRY_CUDA(cudaGetLastError());
+  }
+  for (int clip = 0; clip < b; ++clip) {
+    LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev + clip * nn, 1, N, C, h->d_tw, L.rowbuf, L.mhat, st));
+    for (int f0 = f_first; f0 < f_first + f_count; f0 += P) {
+      const int p = std::min(P, f_first + f_count - f0);
+      const float* g = upstream_dev ? upstream_dev + (size_t(clip) * F + f0) * nn : L.img;
+      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, p * K, N, C, h->d_tw, L.t1, st));
+      LITHO_TRY_CUDA(launch_adj_rows(N, L.t1, h->d_lambda + size_t(f0) * K, K, C, g, h->d_tw, L.u, p, st));
+      LITHO_TRY_CUDA(launch_adj_cols(N, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
+                                     h->d_tw, L.sk, p * K, st));
+      k_sum_planes<<<256, 256, 0, st>>>(L.sk, p * K, size_t(C) * C, L.s, f0 > f_first ? 1 : 0);
+      LITHO_TRY_CUDA(cudaGetLastError());
+    }
+    LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, 1, N, C, h->d_tw, L.qf, st));
+    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, dm_dev + clip * nn, st));
   }
   return LITHO_OK;
 }

@@ -86,6 +86,13 @@ _SIGS = {
     "litho_aerial_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]),
     "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
+    "litho_intensity_vjp_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
+    "litho_intensity_vjp": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p, c_void_p, c_void_p,
+                                    c_size_t, c_void_p]),
+    "litho_ai_inputs_workspace_size": (c_int, [c_void_p, POINTER(c_size_t)]),
+    "litho_ai_inputs": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "litho_print_images": (c_int, [c_void_p, c_void_p, c_int, c_int, c_double, c_double, c_double, c_double, c_void_p,
+                                   c_void_p, c_void_p, c_void_p, c_void_p]),
     "litho_rasterize_workspace_size": (c_int, [c_int, c_int, ctypes.c_int64, c_int, POINTER(c_size_t)]),
     "litho_rasterize": (c_int, [c_void_p, c_void_p, c_int, ctypes.c_int64, c_int, c_int, c_void_p, c_void_p,
                                 c_size_t, c_void_p]),
@@ -372,6 +379,51 @@ def litho_contours(iblur, threshold=0.3, capacity=None, with_cells=True, stream=
     st = starts.cpu().numpy()
     kept = min(capacity, int(st[-1]))
     return seg[:kept], (cell[:kept] if cell is not None else None), st
+
+
+def litho_intensity_vjp(kern: Kernels, mask, upstream=None, f_first=0, f_count=None, dose=1.0, stream=None):
+    """mask: CUDA float32 [b][n][n]; upstream: CUDA float32 [b][n_focus][n][n] or None (ones) ->
+    dm [b][n][n] = sum over planes [f_first, f_first + f_count) of J_f^T upstream_f."""
+    import torch
+    b = mask.shape[0]
+    f_count = kern.n_focus - f_first if f_count is None else f_count
+    full, mn = c_size_t(), c_size_t()
+    _check(lib().litho_intensity_vjp_workspace_size(kern.handle, b, byref(full), byref(mn)))
+    ws = torch.empty(full.value, dtype=torch.uint8, device=mask.device)
+    dm = torch.empty_like(mask)
+    _check(lib().litho_intensity_vjp(kern.handle, c_void_p(mask.data_ptr()), b, dose, f_first, f_count,
+                                     c_void_p(upstream.data_ptr()) if upstream is not None else None,
+                                     c_void_p(dm.data_ptr()), c_void_p(ws.data_ptr()), ws.numel(),
+                                     _stream_ptr(stream)))
+    return dm
+
+
+def litho_ai_inputs(kern: Kernels, targets, focus=0, dose=1.0, stream=None):
+    """targets: CUDA float32 [b][n][n] (0/1) -> X [b][3][n][n] (Eq. (9) channels)."""
+    import torch
+    b, n = targets.shape[0], targets.shape[-1]
+    sz = c_size_t()
+    _check(lib().litho_ai_inputs_workspace_size(kern.handle, byref(sz)))
+    ws = torch.empty(sz.value, dtype=torch.uint8, device=targets.device)
+    x = torch.empty((b, 3, n, n), dtype=torch.float32, device=targets.device)
+    _check(lib().litho_ai_inputs(kern.handle, c_void_p(targets.data_ptr()), b, dose, focus, c_void_p(x.data_ptr()),
+                                 c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    return x
+
+
+def litho_print_images(targets, images, pixel_nm, sigma_round_nm, tau_round, tau_print, stream=None):
+    """targets, images: CUDA float32 [b][n][n] -> (z_round u8, z_print u8, loss int64 [b], blurred target)."""
+    import torch
+    b, n = targets.shape[0], targets.shape[-1]
+    zr = torch.empty((b, n, n), dtype=torch.uint8, device=targets.device)
+    zp = torch.empty_like(zr)
+    loss = torch.empty(b, dtype=torch.int64, device=targets.device)
+    blur = torch.empty_like(targets)
+    _check(lib().litho_print_images(c_void_p(targets.data_ptr()), c_void_p(images.data_ptr()), b, n, pixel_nm,
+                                    sigma_round_nm, tau_round, tau_print, c_void_p(zr.data_ptr()),
+                                    c_void_p(zp.data_ptr()), c_void_p(loss.data_ptr()), c_void_p(blur.data_ptr()),
+                                    _stream_ptr(stream)))
+    return zr, zp, loss, blur
 
 
 def litho_rasterize(rects, n, max_side_px, device="cuda", out=None, stream=None):
