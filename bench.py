@@ -629,6 +629,49 @@ def run_raster(args):
     ctx.close()
 
 
+def run_ai(args):
+    """AI initialiser inputs for 16 clips of 2048^2 (the headline optics, nominal focus, K = 24):
+    one step = the Eq. (9) channels (target, aerial image, intensity gradient, normalised over
+    the batch) + Eqs. (15)-(17) print images and loss against the aerial image."""
+    import paper_2602_15036_gb300 as P
+    from paper_2602_15036_gb300 import litho as L
+    ctx = Ctx(args)
+    torch = ctx.torch
+    clips = min(args.clips, 16)
+    kern = P.litho_make_kernels(P.make_optics(**OPTICS), N, PIXEL, [0.0], K)
+    targets = torch.from_numpy(np.stack([synth.manhattan_mask(N, seed=s) for s in clip_seeds(ctx.rank, clips)])).to(
+        ctx.dev)
+    stream = torch.cuda.current_stream()
+    out = {}
+
+    def step():
+        x = P.litho_ai_inputs(kern, targets, focus=0, stream=stream)
+        out["x"] = x
+        out["p"] = P.litho_print_images(targets, x[:, 1].contiguous(), PIXEL, 20.0, 0.5, 0.3, stream=stream)
+
+    L.litho_profile_enable(True)
+    L.litho_profile_reset()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    L.litho_profile_reset()
+    step_ms, clk = time_steps(ctx, step, args.steps, 0, stream, sample_clocks=True)
+    prof = L.litho_profile_read()
+    L.litho_profile_enable(False)
+    total = ctx.max_over_ranks(sum(step_ms))
+    line = {"metric": "AI-input channels + print images Mpx/s (2048² targets, K=24)", "workload": "ai",
+            "value": whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
+            "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"ai inputs {clips}x2048^2 quadrupole41 K=24 nominal focus", "clips_per_gpu": clips},
+            "litho_loss_first_clips": [int(v) for v in out["p"][2][:4].cpu().tolist()],
+            "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_serve(args):
     """Poisson stream of mixed requests through litho_serve (sizes 256..2048, DUV and EUV optics,
     K in {8,16,24}, half images and half ILT steps) at 80 % of the measured saturated rate."""
@@ -742,7 +785,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["aerial", "ilt", "serve", "contour", "raster"], default="aerial")
+    ap.add_argument("--workload", choices=["aerial", "ilt", "serve", "contour", "raster", "ai"], default="aerial")
     ap.add_argument("--precision", default=HEADLINE,
                     choices=sorted(ERROR_BOUND) + ["bf16/coarse"])
     ap.add_argument("--clips", type=int, default=64)
@@ -760,6 +803,8 @@ def main():
         run_contour(args)
     elif args.workload == "raster":
         run_raster(args)
+    elif args.workload == "ai":
+        run_ai(args)
     else:
         run_aerial(args)
 

@@ -271,7 +271,8 @@ litho_status litho_ai_inputs(const litho_kernels* h, const float* target_dev, in
  * litho_resist), z_print = [I >= tau_print] on the images intensity[b][n][n],
  * and, when loss_dev is not NULL, loss[c] = sum |z_print - z_round| (int64, the
  * number of pixels where the two differ).  blur_dev (f32 [b][n][n]) receives
- * G (x) Z_t.  n a multiple of 32.  Async. */
+ * G (x) Z_t.  n a multiple of 32; z_round_dev and z_print_dev 16-byte
+ * aligned.  Async. */
 litho_status litho_print_images(const float* target_dev, const float* intensity_dev, int b, int n, double pixel_nm,
                                 double sigma_round_nm, double tau_round, double tau_print, uint8_t* z_round_dev,
                                 uint8_t* z_print_dev, int64_t* loss_dev, float* blur_dev, void* stream);
@@ -319,7 +320,7 @@ litho_status litho_rasterize(const float* rects_dev, const int64_t* rect_start_d
  * the total; segments at or beyond `capacity` are counted but not written,
  * so a caller that sees total > capacity calls again with more room.
  * Workspace: litho_contours_workspace_size bytes, 256-byte aligned; seg_dev
- * 16-byte aligned.  Asynchronous on `stream` (three launches).  Errors:
+ * 16-byte aligned.  Asynchronous on `stream` (four launches).  Errors:
  * EINVAL, ENOMEM (workspace too small), ECUDA. */
 litho_status litho_contours_workspace_size(int planes, int n, size_t* bytes);
 litho_status litho_contours(const float* iblur_dev, int planes, int n, double threshold, float* seg_dev,

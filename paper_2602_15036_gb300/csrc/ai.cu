@@ -82,21 +82,27 @@ __global__ void k_threshold(const float* __restrict__ img, size_t count, float t
     z[i] = img[i] >= thr ? 1 : 0;
 }
 
-// One CTA per clip: number of pixels where the two prints differ.
-__global__ void __launch_bounds__(kReduceThreads) k_l1_count(const uint8_t* __restrict__ a,
-                                                             const uint8_t* __restrict__ b, size_t nn,
-                                                             long long* __restrict__ out) {
-  __shared__ long long s[kReduceThreads];
-  const size_t base = size_t(blockIdx.x) * nn;
-  long long c = 0;
-  for (size_t i = threadIdx.x; i < nn; i += kReduceThreads) c += a[base + i] != b[base + i];
+// Number of pixels where the two 0/1 prints differ, per clip (grid y): each
+// block counts 16-byte pieces (the XOR of two 0/1 bytes is one bit) and adds
+// its count to the clip's total with an integer atomic (exact, so the result
+// does not depend on the order).  out must be zero on entry.
+constexpr int kL1Blocks = 64;
+__global__ void __launch_bounds__(kReduceThreads) k_l1_count(const uint4* __restrict__ a, const uint4* __restrict__ b,
+                                                             size_t pieces, unsigned long long* __restrict__ out) {
+  __shared__ unsigned long long s[kReduceThreads];
+  const size_t base = size_t(blockIdx.y) * pieces;
+  unsigned long long c = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < pieces; i += (size_t)gridDim.x * blockDim.x) {
+    const uint4 x = a[base + i], y = b[base + i];
+    c += __popc(x.x ^ y.x) + __popc(x.y ^ y.y) + __popc(x.z ^ y.z) + __popc(x.w ^ y.w);
+  }
   s[threadIdx.x] = c;
   __syncthreads();
   for (int o = kReduceThreads / 2; o > 0; o >>= 1) {
     if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[blockIdx.x] = s[0];
+  if (threadIdx.x == 0) atomicAdd(out + blockIdx.y, s[0]);
 }
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
@@ -189,6 +195,10 @@ litho_status litho_print_images(const float* target_dev, const float* intensity_
     set_error("thresholds must be finite");
     return LITHO_EINVAL;
   }
+  if (((reinterpret_cast<uintptr_t>(z_round_dev) | reinterpret_cast<uintptr_t>(z_print_dev)) & 15) != 0) {
+    set_error("z_round_dev and z_print_dev must be 16-byte aligned");
+    return LITHO_EINVAL;
+  }
   ResistTaps taps;
   std::string why;
   if (!resist_taps(sigma_round_nm, pixel_nm, &taps, &why)) {
@@ -204,8 +214,12 @@ litho_status litho_print_images(const float* target_dev, const float* intensity_
   ProfScope ps(kStageResist, st, loss_dev ? 3 : 2);
   LITHO_TRY_CUDA(launch_resist(target_dev, b, n, taps, float(tau_round), blur_dev, z_round_dev, st));
   k_threshold<<<1024, 256, 0, st>>>(intensity_dev, size_t(b) * nn, float(tau_print), z_print_dev);
-  if (loss_dev)
-    k_l1_count<<<b, kReduceThreads, 0, st>>>(z_print_dev, z_round_dev, nn, reinterpret_cast<long long*>(loss_dev));
+  if (loss_dev) {
+    LITHO_TRY_CUDA(cudaMemsetAsync(loss_dev, 0, size_t(b) * sizeof(int64_t), st));
+    k_l1_count<<<dim3(kL1Blocks, b), kReduceThreads, 0, st>>>(
+        reinterpret_cast<const uint4*>(z_print_dev), reinterpret_cast<const uint4*>(z_round_dev), nn / 16,
+        reinterpret_cast<unsigned long long*>(loss_dev));
+  }
   LITHO_TRY_CUDA(cudaGetLastError());
   return LITHO_OK;
 }

@@ -708,7 +708,7 @@ litho_status litho_contours(const float* iblur_dev, int planes, int n, double th
     return LITHO_ENOMEM;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  ProfScope ps(kStageContours, st, 3);
+  ProfScope ps(kStageContours, st, 4);
   LITHO_TRY_CUDA(launch_contours(iblur_dev, planes, n, float(threshold), reinterpret_cast<float4*>(seg_dev), cell_dev,
                                  capacity, reinterpret_cast<long long*>(plane_start_dev), workspace_dev, st));
   return LITHO_OK;

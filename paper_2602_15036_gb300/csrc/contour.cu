@@ -13,12 +13,12 @@
 // its inside corners when ((TL + TR) + (BR + BL)) / 4 >= T and separates them
 // otherwise.  The segment table below is that rule worked out per case.
 //
-// Three launches, all deterministic: per row of cells the number of segments,
-// one CTA scanning the row counts of every plane into global offsets, and per
-// row again the segments written at those offsets in row-major cell order
-// (saddle segments ordered by their start edge).  A row CTA walks its row in
-// chunks of one cell per thread, so the corner loads and the segment stores
-// of a warp are contiguous; a block scan per chunk places the segments.
+// Four launches, all deterministic: the number of segments per unit (a row
+// of cells, or a 128-cell chunk of one when rows are a multiple of 128), one
+// CTA per plane scanning its units' counts, one thread placing the planes
+// one after another, and the segments written at those offsets in row-major
+// cell order (saddle segments ordered by their start edge).
+#include <algorithm>
 #include <cstdint>
 
 #include "litho_internal.h"
@@ -85,13 +85,26 @@ __device__ __forceinline__ Cell load_cell(const float* __restrict__ img, int n, 
               __ldg(img + (size_t)i1 * n + j)};
 }
 
-__device__ __forceinline__ uint16_t cell_entry(const Cell& c, float thr) {
+// Index into the segment table (case, or 16 + case for a separated saddle).
+__device__ __forceinline__ int cell_case(const Cell& c, float thr) {
   const int cs = (c.tl >= thr) | (c.tr >= thr) << 1 | (c.br >= thr) << 2 | (c.bl >= thr) << 3;
   if (cs == 5 || cs == 10) {
     const float centre = ((c.tl + c.tr) + (c.br + c.bl)) * 0.25f;
-    if (!(centre >= thr)) return kSegTable[16 + cs];
+    if (!(centre >= thr)) return 16 + cs;
   }
-  return kSegTable[cs];
+  return cs;
+}
+
+// Segments of a case without a table look-up (lanes of a warp index the
+// table at different places, which the constant cache would serialise).
+__device__ __forceinline__ int case_segments(int cs) {
+  cs &= 15;
+  return cs == 0 || cs == 15 ? 0 : cs == 5 || cs == 10 ? 2 : 1;
+}
+
+// The table entry from a shared-memory copy (one per CTA).
+__device__ __forceinline__ uint16_t cell_entry(const Cell& c, float thr, const uint16_t* tab) {
+  return tab[cell_case(c, thr)];
 }
 
 // Crossing point of edge e in cell-local coordinates (x, y).
@@ -109,10 +122,11 @@ __device__ __forceinline__ float2 edge_point(const Cell& c, int e, float thr) {
   return make_float2(a.x + t * (b.x - a.x), a.y + t * (b.y - a.y));
 }
 
-// Exclusive block scan of one int per thread; returns the thread's offset, *total the sum.
+// Exclusive block scan of one int per thread (blockDim.x a multiple of 32, at
+// most 1024); returns the thread's offset, *total the sum.
 __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
-  __shared__ int warp_sums[kRowThreads / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __shared__ int warp_sums[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -122,17 +136,17 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
   if (lane == 31) warp_sums[w] = x;
   __syncthreads();
   if (w == 0) {
-    int s = lane < kRowThreads / 32 ? warp_sums[lane] : 0;
+    int s = lane < nw ? warp_sums[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, s, o);
       if (lane >= o) s += y;
     }
-    if (lane < kRowThreads / 32) warp_sums[lane] = s;  // inclusive
+    if (lane < nw) warp_sums[lane] = s;  // inclusive
   }
   __syncthreads();
   const int before = (w > 0 ? warp_sums[w - 1] : 0) + x - v;
-  *total = warp_sums[kRowThreads / 32 - 1];
+  *total = warp_sums[nw - 1];
   __syncthreads();  // warp_sums reusable
   return before;
 }
@@ -142,47 +156,60 @@ __global__ void __launch_bounds__(kRowThreads) k_ms_count(const float* __restric
   const int i = blockIdx.x, p = blockIdx.y;
   const float* plane = img + (size_t)p * n * n;
   int cnt = 0;
-  for (int j = threadIdx.x; j < n; j += kRowThreads) cnt += cell_entry(load_cell(plane, n, i, j), thr) >> 8;
+  for (int j = threadIdx.x; j < n; j += kRowThreads) cnt += case_segments(cell_case(load_cell(plane, n, i, j), thr));
   int total;
   block_exclusive_scan(cnt, &total);
   if (threadIdx.x == 0) row_count[(size_t)p * n + i] = total;
 }
 
-// One CTA: exclusive scan of all rows' counts (planes * n of them) into
-// row_start, and plane_start[p] = row_start[p n], plane_start[planes] = total.
-// Chunks of one row per thread (contiguous loads and stores), a block scan
-// per chunk, the running total carried from chunk to chunk.
-__global__ void __launch_bounds__(kRowThreads) k_ms_scan(const int* __restrict__ row_count, long long rows, int n,
-                                                         int planes, long long* __restrict__ row_start,
-                                                         long long* __restrict__ plane_start) {
+// One CTA per plane: exclusive scan of the plane's row counts into
+// row_start (offsets within the plane) and the plane's total.  Chunks of one
+// row per thread (contiguous loads and stores), the running total carried.
+__global__ void __launch_bounds__(1024) k_ms_scan(const int* __restrict__ row_count, int n,
+                                                         long long* __restrict__ row_start,
+                                                         long long* __restrict__ plane_total) {
+  const size_t base = (size_t)blockIdx.x * n;
   long long run = 0;
-  for (long long r0 = 0; r0 < rows; r0 += kRowThreads) {
-    const long long r = r0 + threadIdx.x;
-    const int c = r < rows ? row_count[r] : 0;
+  for (int r0 = 0; r0 < n; r0 += blockDim.x) {
+    const int r = r0 + threadIdx.x;
+    const int c = r < n ? row_count[base + r] : 0;
     int chunk;
     const int before = block_exclusive_scan(c, &chunk);
-    if (r < rows) row_start[r] = run + before;
+    if (r < n) row_start[base + r] = run + before;
     run += chunk;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) plane_start[planes] = run;
-  for (int p = threadIdx.x; p < planes; p += kRowThreads) plane_start[p] = row_start[(long long)p * n];
+  if (threadIdx.x == 0) plane_total[blockIdx.x] = run;
+}
+
+// plane_start[p] = sum of the totals of the planes before p; [planes] = all.
+__global__ void k_ms_planes(const long long* __restrict__ plane_total, int planes,
+                            long long* __restrict__ plane_start) {
+  long long run = 0;
+  for (int p = 0; p < planes; ++p) {
+    plane_start[p] = run;
+    run += plane_total[p];
+  }
+  plane_start[planes] = run;
 }
 
 __global__ void __launch_bounds__(kRowThreads) k_ms_emit(const float* __restrict__ img, int n, float thr,
                                                          const long long* __restrict__ row_start,
+                                                         const long long* __restrict__ plane_start,
                                                          long long capacity, float4* __restrict__ seg,
                                                          int* __restrict__ cell_id) {
+  __shared__ uint16_t tab[32];
+  if (threadIdx.x < 32) tab[threadIdx.x] = kSegTable[threadIdx.x];
+  __syncthreads();
   const int i = blockIdx.x, p = blockIdx.y;
   const float* plane = img + (size_t)p * n * n;
-  long long base = row_start[(size_t)p * n + i];
+  long long base = plane_start[p] + row_start[(size_t)p * n + i];
   for (int j0 = 0; j0 < n; j0 += kRowThreads) {  // uniform trip count: every thread takes part in each scan
     const int j = j0 + threadIdx.x;
     Cell c{0.f, 0.f, 0.f, 0.f};
     uint16_t ent = 0;
     if (j < n) {
       c = load_cell(plane, n, i, j);
-      ent = cell_entry(c, thr);
+      ent = cell_entry(c, thr, tab);
     }
     const int ns = ent >> 8;
     int chunk;
@@ -194,6 +221,93 @@ __global__ void __launch_bounds__(kRowThreads) k_ms_emit(const float* __restrict
       const float2 a = edge_point(c, s0, thr), b = edge_point(c, e0, thr);
       seg[o] = make_float4(j + a.x, i + a.y, j + b.x, i + b.y);
       if (cell_id) cell_id[o] = i * n + j;
+    }
+  }
+}
+
+// Rows whose length is a multiple of 128: each warp owns a chunk of 128
+// cells of one row (lane l: cells 4l .. 4l + 3, one 16-byte load per pixel row,
+// the fifth corner from the next lane).  The count pass writes one count per
+// chunk (warp reduction), a per-plane scan turns them into offsets, and the
+// emit pass places each lane's segments with a warp scan: no block barrier in
+// either pass; grid y = plane, warps over the plane's (row, chunk) units in a
+// grid-stride loop.
+struct Cells4 {
+  Cell c[4];
+};
+
+__device__ __forceinline__ Cells4 load_cells4(const float* __restrict__ plane, int n, int i, int j0) {
+  const int i1 = i + 1 == n ? 0 : i + 1, lane = threadIdx.x & 31, j = j0 + 4 * lane;
+  const float4 a = __ldg(reinterpret_cast<const float4*>(plane + (size_t)i * n + j));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(plane + (size_t)i1 * n + j));
+  float a4 = __shfl_down_sync(0xffffffffu, a.x, 1), b4 = __shfl_down_sync(0xffffffffu, b.x, 1);
+  if (lane == 31) {  // the next chunk's first pixels, or the row's start
+    const int j4 = j + 4 == n ? 0 : j + 4;
+    a4 = __ldg(plane + (size_t)i * n + j4);
+    b4 = __ldg(plane + (size_t)i1 * n + j4);
+  }
+  Cells4 r;
+  r.c[0] = Cell{a.x, a.y, b.y, b.x};
+  r.c[1] = Cell{a.y, a.z, b.z, b.y};
+  r.c[2] = Cell{a.z, a.w, b.w, b.z};
+  r.c[3] = Cell{a.w, a4, b4, b.w};
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_ms_count4(const float* __restrict__ img, int n, int planes, float thr,
+                                                   int* __restrict__ chunk_count) {
+  const int chunks = n / 128, per_plane = n * chunks, p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < per_plane; r += (gridDim.x * blockDim.x) >> 5) {
+    const size_t w = (size_t)p * per_plane + r;
+    const int i = r / chunks, j0 = (r - i * chunks) * 128;
+    const Cells4 cs = load_cells4(img + (size_t)p * n * n, n, i, j0);
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cnt += case_segments(cell_case(cs.c[k], thr));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    if (lane == 0) chunk_count[w] = cnt;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_ms_emit4(const float* __restrict__ img, int n, int planes, float thr,
+                                                  const long long* __restrict__ chunk_start,
+                                                  const long long* __restrict__ plane_start, long long capacity,
+                                                  float4* __restrict__ seg, int* __restrict__ cell_id) {
+  __shared__ uint16_t tab[32];
+  if (threadIdx.x < 32) tab[threadIdx.x] = kSegTable[threadIdx.x];
+  __syncthreads();
+  const int chunks = n / 128, per_plane = n * chunks, p = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < per_plane; r += (gridDim.x * blockDim.x) >> 5) {
+    const size_t w = (size_t)p * per_plane + r;
+    const int i = r / chunks, j0 = (r - i * chunks) * 128;
+    const Cells4 cs = load_cells4(img + (size_t)p * n * n, n, i, j0);
+    uint16_t ent[4];
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      ent[k] = cell_entry(cs.c[k], thr, tab);
+      cnt += ent[k] >> 8;
+    }
+    int x = cnt;  // inclusive warp scan
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    long long o = plane_start[p] + chunk_start[w] + (x - cnt);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int ns = ent[k] >> 8, j = j0 + 4 * lane + k;
+      for (int q = 0; q < ns; ++q, ++o) {
+        if (o >= capacity) continue;
+        const int s0 = (ent[k] >> (4 * q)) & 3, e0 = (ent[k] >> (4 * q + 2)) & 3;
+        const float2 a = edge_point(cs.c[k], s0, thr), b = edge_point(cs.c[k], e0, thr);
+        seg[o] = make_float4(j + a.x, i + a.y, j + b.x, i + b.y);
+        if (cell_id) cell_id[o] = i * n + j;
+      }
     }
   }
 }
@@ -245,20 +359,40 @@ __global__ void k_epe_focus(const float* __restrict__ epe, int m, int f0, int fp
 
 }  // namespace
 
+// Units the count pass produces per plane: rows (one-cell-per-thread path) or
+// 128-cell chunks (rows a multiple of 128).
+static bool contour_vec(int n) { return n % 128 == 0 && n <= 65536; }
+static size_t contour_units(int n) { return contour_vec(n) ? size_t(n) * (n / 128) : size_t(n); }
+
 size_t contour_workspace_bytes(int planes, int n) {
-  const size_t rows = size_t(planes) * n;
-  return (rows * sizeof(int) + 255) / 256 * 256 + rows * sizeof(long long);
+  const size_t units = size_t(planes) * contour_units(n);
+  return (units * sizeof(int) + 255) / 256 * 256 + (units * sizeof(long long) + 255) / 256 * 256 +
+         size_t(planes) * sizeof(long long);
 }
 
 cudaError_t launch_contours(const float* img, int planes, int n, float thr, float4* seg, int* cell_id,
                             long long capacity, long long* plane_start, void* ws, cudaStream_t st) {
-  const size_t rows = size_t(planes) * n;
-  int* row_count = static_cast<int*>(ws);
-  long long* row_start =
-      reinterpret_cast<long long*>(static_cast<char*>(ws) + (rows * sizeof(int) + 255) / 256 * 256);
-  k_ms_count<<<dim3(n, planes), kRowThreads, 0, st>>>(img, n, thr, row_count);
-  k_ms_scan<<<1, kRowThreads, 0, st>>>(row_count, (long long)rows, n, planes, row_start, plane_start);
-  k_ms_emit<<<dim3(n, planes), kRowThreads, 0, st>>>(img, n, thr, row_start, capacity, seg, cell_id);
+  const bool vec = contour_vec(n) && (reinterpret_cast<uintptr_t>(img) & 15) == 0;
+  const size_t per_plane = vec ? contour_units(n) : size_t(n);
+  // the workspace is sized for the larger (vector) layout when n allows it
+  const size_t sized = size_t(planes) * contour_units(n);
+  char* w = static_cast<char*>(ws);
+  int* count = reinterpret_cast<int*>(w);
+  long long* start = reinterpret_cast<long long*>(w + (sized * sizeof(int) + 255) / 256 * 256);
+  long long* plane_total = reinterpret_cast<long long*>(w + (sized * sizeof(int) + 255) / 256 * 256 +
+                                                        (sized * sizeof(long long) + 255) / 256 * 256);
+  if (vec) {
+    const int blocks = std::max(1, std::min(152 * 8 / std::max(1, planes / 8), n * (n / 128) / 8));
+    k_ms_count4<<<dim3(blocks, planes), 256, 0, st>>>(img, n, planes, thr, count);
+    k_ms_scan<<<planes, 1024, 0, st>>>(count, int(per_plane), start, plane_total);
+    k_ms_planes<<<1, 1, 0, st>>>(plane_total, planes, plane_start);
+    k_ms_emit4<<<dim3(blocks, planes), 256, 0, st>>>(img, n, planes, thr, start, plane_start, capacity, seg, cell_id);
+  } else {
+    k_ms_count<<<dim3(n, planes), kRowThreads, 0, st>>>(img, n, thr, count);
+    k_ms_scan<<<planes, kRowThreads, 0, st>>>(count, n, start, plane_total);
+    k_ms_planes<<<1, 1, 0, st>>>(plane_total, planes, plane_start);
+    k_ms_emit<<<dim3(n, planes), kRowThreads, 0, st>>>(img, n, thr, start, plane_start, capacity, seg, cell_id);
+  }
   return cudaGetLastError();
 }
 

@@ -65,6 +65,15 @@ def test_contours_match_oracle_on_images_blobs_and_noise(litho_lib, cuda):
     _compare(seg, cell, start, planes, thr)
 
 
+@pytest.mark.parametrize("n", [96, 64])
+def test_contours_rows_not_a_multiple_of_128(litho_lib, cuda, n):
+    """Row lengths outside the vectorised kernels' (one cell per thread in chunks)."""
+    import torch
+    planes = np.stack([_blobs(n, 31), synth.random_field((n, n), seed=32, lo=0.0, hi=1.0).astype(np.float32)])
+    seg, cell, start = litho_lib.litho_contours(torch.from_numpy(planes).to(cuda), 0.5)
+    _compare(seg.cpu().numpy(), cell.cpu().numpy(), start, planes, 0.5)
+
+
 def test_contours_capacity_and_chaining(litho_lib, cuda):
     import torch
     L = litho_lib
