@@ -332,10 +332,12 @@ __device__ __forceinline__ void fft_smem(float2* buf, const float2* tw, int t) {
 
 // Full transform with the first pass from `load` and every pass's output in
 // shared memory (padded layout, natural order on return).  Ends with a barrier.
-template <int N, int SIGN, class Load, bool BANDED = false>
+// NTX: the threads that share the transform (default: the plan's own; more
+// threads take the butterflies of a pass in fewer rounds).
+template <int N, int SIGN, class Load, bool BANDED = false, int NTX = Plan<N>::NT>
 __device__ __forceinline__ void fft_load_smem(float2* buf, const float2* tw, int t, Load& load) {
   using PL = Plan<N>;
-  constexpr int NT = PL::NT;
+  constexpr int NT = NTX;
   SmemLoadUnused none;
   pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false, Load, BANDED>(buf, tw, t, load);
   if constexpr (PL::P == 2) {

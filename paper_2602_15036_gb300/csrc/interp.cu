@@ -44,10 +44,11 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
   for (int i = tid; i < NC; i += T) tw_c[i] = tw_nc_g[i];
   __syncthreads();
   float2* col = buf + g * LD;
-  // forward transform over y on NC (threads t >= NTC take no butterflies)
+  // forward transform over y on NC, shared by all NT threads of the column
+  // (a pass with fewer butterflies than threads leaves the rest idle)
   const float2* src = rspec + (size_t)p * NC * c2 + u0 + g;
   auto load_c = [&](int y) { return __ldg(src + (size_t)y * c2); };
-  fft_load_smem<NC, -1, decltype(load_c), false>(col, tw_c, t < NTC ? t : (1 << 20), load_c);
+  fft_load_smem<NC, -1, decltype(load_c), false, NT>(col, tw_c, t, load_c);
   // crop, scale, blur channel, and the inverse transform over v on N
   const float scale = 1.0f / (float(NC) * float(NC));
   const float gu = gain ? __ldg(gain + u0 + g) : 0.f;
