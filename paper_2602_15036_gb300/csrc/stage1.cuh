@@ -2,7 +2,7 @@
 // transform over the y frequency, T_j[y][c] = sum_v mhat[v][c] Phi_j[v][c] e^{+2 pi i v y/N},
 // for a block of W crop columns c and a run of kernels j.
 //
-// A CTA keeps the twiddle table in shared memory and loops over JB kernels;
+// A CTA keeps the twiddle table in shared memory and loops over a run of kernels;
 // the next kernel's Phi block is copied in with cp.async (two buffers) while
 // the current block's W column transforms run.  The band multiply happens in
 // the first pass's load: the mask-spectrum values a thread multiplies are
@@ -21,6 +21,8 @@
 // block run side by side, so each block comes from DRAM once and from L2
 // for the other clips.  Clip i writes j + i nk.
 #pragma once
+
+#include <algorithm>
 
 #include "fft_common.cuh"
 
@@ -129,7 +131,20 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
 template <int N, int W, class Out, bool BANDED>
 cudaError_t launch_stage1_cols_t(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, Out out,
                                  cudaStream_t st, int clips) {
-  constexpr int JB = 8;
+  // Kernels per CTA: as many as keep about two waves of CTAs on the GPU
+  // (each CTA loads its twiddles and mask values once and starts its copy
+  // pipeline once, so longer runs of kernels are cheaper), split evenly.
+  static int sms = 0;  // the same GPU model throughout a process; a racing first call stores the same value
+  if (!sms) {
+    int dev = 0, v = 0;
+    sms = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0
+              ? v
+              : 152;
+  }
+  const long long ctas = (long long)clips * (crop / W);
+  const int jblocks = int(std::min<long long>(nk, std::max<long long>(1, (2LL * sms + ctas - 1) / ctas)));
+  const int JB = (nk + jblocks - 1) / jblocks;
   const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop);
   cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out, BANDED>, sm);
   if (e != cudaSuccess) return e;
