@@ -12,6 +12,8 @@
 //   mhat    [b][C][C] c64   N^-2 DFT(m) on the crop, [v][u]
 //   t1      [j][N][C] c64   stage-1 field T_j[y][u] = sum_v mhat[v][u] Phi_j[v][u] e^{2 pi i v y/N}
 //   img     [plane][N][N] f32
+#include <algorithm>
+
 #include "fft_common.cuh"
 #include "litho_internal.h"
 #include "stage1.cuh"
@@ -27,31 +29,35 @@ __device__ __forceinline__ int freq_of(int idx, int n) { return idx < n / 2 ? id
 template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT) k_mask_rows(const float* __restrict__ m, int crop,
                                                             const float2* __restrict__ tw_g,
-                                                            float2* __restrict__ rowbuf) {
+                                                            float2* __restrict__ rowbuf, int pairs_per_cta) {
   extern __shared__ float2 smem[];
   float2* tw = smem;
   float2* buf = smem + N;
   float2* zc = smem + N + PadLen<N>::value;  // Z(u) for u in [-C/2, C/2], index u + C/2 (crop + 1 <= N + 1 entries)
   load_twiddles<N>(tw, tw_g);
   __syncthreads();
-  const int b = blockIdx.y, y0 = 2 * blockIdx.x;
-  const float* r0 = m + ((size_t)b * N + y0) * N;
-  const float* r1 = r0 + N;
-  const int t = threadIdx.x, half = crop / 2;
-  auto load = [&](int i) { return make_float2(__ldg(r0 + i), __ldg(r1 + i)); };
-  auto use = [&](int, int, int idx, float2 v) {
-    const int u = freq_of(idx, N);
-    if (u >= -half && u <= half) zc[u + half] = v;
-    if (u == -N / 2 && half == N / 2) zc[crop] = v;  // crop == N: Z(N/2) is Z(-N/2)
-  };
-  fft_load_use<N, -1>(buf, tw, t, load, use);
-  __syncthreads();
-  float2* o0 = rowbuf + ((size_t)b * N + y0) * crop;
-  float2* o1 = o0 + crop;
-  for (int c = t; c < crop; c += blockDim.x) {
-    const float2 zp = zc[c], zm = zc[crop - c];
-    o0[c] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
-    o1[c] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+  const int b = blockIdx.y, t = threadIdx.x, half = crop / 2;
+  // pairs [blockIdx.x * pairs_per_cta, ...): the next pair's first pass writes
+  // buf only after a barrier that follows this pair's reads of zc
+  for (int pr = blockIdx.x * pairs_per_cta; pr < min(N / 2, (blockIdx.x + 1) * pairs_per_cta); ++pr) {
+    const int y0 = 2 * pr;
+    const float* r0 = m + ((size_t)b * N + y0) * N;
+    const float* r1 = r0 + N;
+    auto load = [&](int i) { return make_float2(__ldg(r0 + i), __ldg(r1 + i)); };
+    auto use = [&](int, int, int idx, float2 v) {
+      const int u = freq_of(idx, N);
+      if (u >= -half && u <= half) zc[u + half] = v;
+      if (u == -N / 2 && half == N / 2) zc[crop] = v;  // crop == N: Z(N/2) is Z(-N/2)
+    };
+    fft_load_use<N, -1>(buf, tw, t, load, use);
+    __syncthreads();
+    float2* o0 = rowbuf + ((size_t)b * N + y0) * crop;
+    float2* o1 = o0 + crop;
+    for (int c = t; c < crop; c += blockDim.x) {
+      const float2 zp = zc[c], zm = zc[crop - c];
+      o0[c] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+      o1[c] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+    }
   }
 }
 
@@ -170,20 +176,22 @@ __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const
 template <int N, bool BANDED>
 __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_real(const float2* __restrict__ q, int crop, float scale,
                                                                 const float2* __restrict__ tw_g,
-                                                                float* __restrict__ out) {
+                                                                float* __restrict__ out, int rows_per_cta) {
   __shared__ float2 buf[PadLen<N>::value];
   __shared__ float2 tw[N];
   load_twiddles<N>(tw, tw_g);
   __syncthreads();
-  const int y = blockIdx.x, p = blockIdx.y, half = crop / 2;
-  const float2* row = q + ((size_t)p * N + y) * crop;
-  auto load = [&](int, int r, int idx) {
-    const int c = (r < Plan<N>::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
-    return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
-  };
-  float* o = out + ((size_t)p * N + y) * N;
-  auto use = [&](int, int, int x, float2 v) { o[x] = scale * v.x; };
-  fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, threadIdx.x, load, use);
+  const int p = blockIdx.y, half = crop / 2;
+  for (int y = blockIdx.x * rows_per_cta; y < min(N, (blockIdx.x + 1) * rows_per_cta); ++y) {
+    const float2* row = q + ((size_t)p * N + y) * crop;
+    auto load = [&](int, int r, int idx) {
+      const int c = (r < Plan<N>::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
+      return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
+    };
+    float* o = out + ((size_t)p * N + y) * N;
+    auto use = [&](int, int, int x, float2 v) { o[x] = scale * v.x; };
+    fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, threadIdx.x, load, use);
+  }
 }
 
 // Same transform for band rows carrying S (1 + i gain (x) gain) (see
@@ -193,43 +201,66 @@ template <int N, bool BANDED>
 __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_resist(const float2* __restrict__ q, int crop,
                                                                   const float2* __restrict__ tw_g, float thr,
                                                                   float* __restrict__ img, float* __restrict__ iblur,
-                                                                  uint8_t* __restrict__ printed) {
+                                                                  uint8_t* __restrict__ printed, int rows_per_cta) {
   __shared__ float2 buf[PadLen<N>::value];
   __shared__ float2 tw[N];
   load_twiddles<N>(tw, tw_g);
   __syncthreads();
-  const int y = blockIdx.x, p = blockIdx.y, half = crop / 2;
-  const float2* row = q + ((size_t)p * N + y) * crop;
-  auto load = [&](int, int r, int idx) {
-    const int c = (r < Plan<N>::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
-    return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
-  };
-  const size_t o = ((size_t)p * N + y) * N;
-  auto use = [&](int, int, int x, float2 v) {
-    if (img) img[o + x] = v.x;
-    iblur[o + x] = v.y;
-    if (printed) printed[o + x] = v.y >= thr ? 1 : 0;
-  };
-  fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, threadIdx.x, load, use);
+  const int p = blockIdx.y, half = crop / 2;
+  for (int y = blockIdx.x * rows_per_cta; y < min(N, (blockIdx.x + 1) * rows_per_cta); ++y) {
+    const float2* row = q + ((size_t)p * N + y) * crop;
+    auto load = [&](int, int r, int idx) {
+      const int c = (r < Plan<N>::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
+      return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
+    };
+    const size_t o = ((size_t)p * N + y) * N;
+    auto use = [&](int, int, int x, float2 v) {
+      if (img) img[o + x] = v.x;
+      iblur[o + x] = v.y;
+      if (printed) printed[o + x] = v.y >= thr ? 1 : 0;
+    };
+    fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, threadIdx.x, load, use);
+  }
+}
+
+// Rows per CTA for the one-row-per-transform kernels: enough CTAs for about
+// eight waves of `per_sm` CTAs per SM, each CTA reusing its twiddle table
+// for its rows.
+inline int rows_per_cta(int rows, int planes, int per_sm) {
+  static int sms = 0;  // the same GPU model throughout a process
+  if (!sms) {
+    int dev = 0, v = 0;
+    sms = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0
+              ? v
+              : 152;
+  }
+  const long long want = 8LL * sms * per_sm;
+  const long long r = std::max<long long>(1, ((long long)rows * planes) / want);
+  return int(std::min<long long>(r, rows));
 }
 
 template <int N>
 cudaError_t band_rows_resist_n(const float2* q, int planes, int crop, const float2* tw, float thr, float* img,
                                float* iblur, uint8_t* printed, cudaStream_t st) {
+  const int rpc = rows_per_cta(N, planes, 2048 / Plan<N>::NT), grid = (N + rpc - 1) / rpc;
   if (2 * crop <= N)
-    k_band_rows_resist<N, true><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed);
+    k_band_rows_resist<N, true><<<dim3(grid, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed,
+                                                                           rpc);
   else
-    k_band_rows_resist<N, false><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed);
+    k_band_rows_resist<N, false><<<dim3(grid, planes), Plan<N>::NT, 0, st>>>(q, crop, tw, thr, img, iblur, printed,
+                                                                            rpc);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t band_rows_real_n(const float2* q, int planes, int crop, float scale, const float2* tw, float* out,
                              cudaStream_t st) {
+  const int rpc = rows_per_cta(N, planes, 2048 / Plan<N>::NT), grid = (N + rpc - 1) / rpc;
   if (2 * crop <= N)
-    k_band_rows_real<N, true><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out);
+    k_band_rows_real<N, true><<<dim3(grid, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out, rpc);
   else
-    k_band_rows_real<N, false><<<dim3(N, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out);
+    k_band_rows_real<N, false><<<dim3(grid, planes), Plan<N>::NT, 0, st>>>(q, crop, scale, tw, out, rpc);
   return cudaGetLastError();
 }
 
@@ -243,7 +274,8 @@ cudaError_t mask_rows_n(const float* m, int b, int crop, const float2* tw, float
   const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
   cudaError_t e = smem_attrs(k_mask_rows<N>, smr);
   if (e != cudaSuccess) return e;
-  k_mask_rows<N><<<dim3(N / 2, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf);
+  const int ppc = rows_per_cta(N / 2, b, 2048 / Plan<N>::NT);
+  k_mask_rows<N><<<dim3((N / 2 + ppc - 1) / ppc, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf, ppc);
   return cudaGetLastError();
 }
 
@@ -253,7 +285,8 @@ cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, f
   const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
   cudaError_t e = smem_attrs(k_mask_rows<N>, smr);
   if (e != cudaSuccess) return e;
-  k_mask_rows<N><<<dim3(N / 2, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf);
+  const int ppc = rows_per_cta(N / 2, b, 2048 / Plan<N>::NT);
+  k_mask_rows<N><<<dim3((N / 2 + ppc - 1) / ppc, b), Plan<N>::NT, smr, st>>>(m, crop, tw, rowbuf, ppc);
   const size_t sm = col_smem_bytes<N>();
   e = smem_attrs(k_mask_cols<N>, sm);
   if (e != cudaSuccess) return e;
