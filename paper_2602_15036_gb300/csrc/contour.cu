@@ -225,89 +225,188 @@ __global__ void __launch_bounds__(kRowThreads) k_ms_emit(const float* __restrict
   }
 }
 
-// Rows whose length is a multiple of 128: each warp owns a chunk of 128
-// cells of one row (lane l: cells 4l .. 4l + 3, one 16-byte load per pixel row,
-// the fifth corner from the next lane).  The count pass writes one count per
-// chunk (warp reduction), a per-plane scan turns them into offsets, and the
-// emit pass places each lane's segments with a warp scan: no block barrier in
-// either pass; grid y = plane, warps over the plane's (row, chunk) units in a
-// grid-stride loop.
-struct Cells4 {
-  Cell c[4];
+// Rows whose length is a multiple of 128: a warp walks one row of cells in
+// chunks of 128 (lane l: cells 4l .. 4l + 3, one 16-byte load per pixel row;
+// the fifth corner comes from the next lane, for lane 31 from the next
+// chunk's lane 0, and after the last chunk from the row's first pixel),
+// loading the next chunk while it works on the current one.  The count pass
+// writes one count per chunk (warp reduction), a per-plane scan turns them
+// into offsets, and the emit pass places each lane's segments with a warp
+// scan: no block barrier in either pass; grid y = plane, warps over the
+// plane's rows in a grid-stride loop.
+struct RowWalk {
+  const float* ra;  // row i, this lane's first pixel
+  const float* rb;  // row i + 1 (periodic)
+  float4 a, b;      // current chunk
+  float a_first, b_first;  // pixel 0 of the two rows
 };
 
-__device__ __forceinline__ Cells4 load_cells4(const float* __restrict__ plane, int n, int i, int j0) {
-  const int i1 = i + 1 == n ? 0 : i + 1, lane = threadIdx.x & 31, j = j0 + 4 * lane;
-  const float4 a = __ldg(reinterpret_cast<const float4*>(plane + (size_t)i * n + j));
-  const float4 b = __ldg(reinterpret_cast<const float4*>(plane + (size_t)i1 * n + j));
-  float a4 = __shfl_down_sync(0xffffffffu, a.x, 1), b4 = __shfl_down_sync(0xffffffffu, b.x, 1);
-  if (lane == 31) {  // the next chunk's first pixels, or the row's start
-    const int j4 = j + 4 == n ? 0 : j + 4;
-    a4 = __ldg(plane + (size_t)i * n + j4);
-    b4 = __ldg(plane + (size_t)i1 * n + j4);
-  }
-  Cells4 r;
-  r.c[0] = Cell{a.x, a.y, b.y, b.x};
-  r.c[1] = Cell{a.y, a.z, b.z, b.y};
-  r.c[2] = Cell{a.z, a.w, b.w, b.z};
-  r.c[3] = Cell{a.w, a4, b4, b.w};
-  return r;
+__device__ __forceinline__ RowWalk row_walk_begin(const float* __restrict__ plane, int n, int i, int lane) {
+  const int i1 = i + 1 == n ? 0 : i + 1;
+  RowWalk w;
+  w.ra = plane + (size_t)i * n + 4 * lane;
+  w.rb = plane + (size_t)i1 * n + 4 * lane;
+  w.a = __ldg(reinterpret_cast<const float4*>(w.ra));
+  w.b = __ldg(reinterpret_cast<const float4*>(w.rb));
+  w.a_first = __shfl_sync(0xffffffffu, w.a.x, 0);
+  w.b_first = __shfl_sync(0xffffffffu, w.b.x, 0);
+  return w;
 }
 
-__global__ void __launch_bounds__(256) k_ms_count4(const float* __restrict__ img, int n, int planes, float thr,
+// Chunk c + 1 of the row (its loads in flight while chunk c is worked on);
+// past the last chunk, values that only supply the wrap-around corner.
+struct Chunk2 {
+  float4 a, b;
+};
+
+__device__ __forceinline__ Chunk2 row_walk_next(const RowWalk& w, int c, int chunks) {
+  if (c + 1 < chunks)
+    return Chunk2{__ldg(reinterpret_cast<const float4*>(w.ra + 128 * (c + 1))),
+                  __ldg(reinterpret_cast<const float4*>(w.rb + 128 * (c + 1)))};
+  return Chunk2{make_float4(w.a_first, 0.f, 0.f, 0.f), make_float4(w.b_first, 0.f, 0.f, 0.f)};
+}
+
+// The fifth corner of each lane (pixel 4l + 4 of the chunk): from lane l + 1,
+// for lane 31 the next chunk's first pixel.
+__device__ __forceinline__ void fifth_corner(const float4& a, const float4& b, const float4& na, const float4& nb,
+                                             int lane, float* a4, float* b4) {
+  *a4 = __shfl_sync(0xffffffffu, lane == 0 ? na.x : a.x, (lane + 1) & 31);
+  *b4 = __shfl_sync(0xffffffffu, lane == 0 ? nb.x : b.x, (lane + 1) & 31);
+}
+
+// Inside bits of five consecutive pixels (bit k: pixel k >= T).
+__device__ __forceinline__ unsigned inside5(const float4& v, float v4, float thr) {
+  return unsigned(v.x >= thr) | unsigned(v.y >= thr) << 1 | unsigned(v.z >= thr) << 2 | unsigned(v.w >= thr) << 3 |
+         unsigned(v4 >= thr) << 4;
+}
+
+// Segments of the lane's four cells from the inside bits of their top and
+// bottom pixel rows: a cell's crossed edges number 0, 2 or 4 and it has half
+// as many segments, so the four cells have half their total crossings (top
+// edges, bottom edges, left edges, right edges).
+__device__ __forceinline__ int segments4(unsigned top, unsigned bot) {
+  const unsigned v = top ^ bot;
+  return (__popc((top ^ (top >> 1)) & 15u) + __popc((bot ^ (bot >> 1)) & 15u) + __popc(v & 15u) + __popc(v & 30u)) >>
+         1;
+}
+
+__global__ void __launch_bounds__(256, 4) k_ms_count4(const float* __restrict__ img, int n, int planes, float thr,
                                                    int* __restrict__ chunk_count) {
-  const int chunks = n / 128, per_plane = n * chunks, p = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < per_plane; r += (gridDim.x * blockDim.x) >> 5) {
-    const size_t w = (size_t)p * per_plane + r;
-    const int i = r / chunks, j0 = (r - i * chunks) * 128;
-    const Cells4 cs = load_cells4(img + (size_t)p * n * n, n, i, j0);
-    int cnt = 0;
+  const int chunks = n / 128, p = blockIdx.y, lane = threadIdx.x & 31;
+  const float* plane = img + (size_t)p * n * n;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    RowWalk w = row_walk_begin(plane, n, i, lane);
+    int* out = chunk_count + ((size_t)p * n + i) * chunks;
+    for (int c = 0; c < chunks; ++c) {
+      const Chunk2 nx = row_walk_next(w, c, chunks);
+      const float4 na = nx.a, nb = nx.b;
+      float a4, b4;
+      fifth_corner(w.a, w.b, na, nb, lane, &a4, &b4);
+      int cnt = segments4(inside5(w.a, a4, thr), inside5(w.b, b4, thr));
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cnt += case_segments(cell_case(cs.c[k], thr));
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-    if (lane == 0) chunk_count[w] = cnt;
+      for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+      if (lane == 0) out[c] = cnt;
+      w.a = na;
+      w.b = nb;
+    }
   }
 }
 
-__global__ void __launch_bounds__(256) k_ms_emit4(const float* __restrict__ img, int n, int planes, float thr,
-                                                  const long long* __restrict__ chunk_start,
-                                                  const long long* __restrict__ plane_start, long long capacity,
-                                                  float4* __restrict__ seg, int* __restrict__ cell_id) {
+// Crossing point of edge e (0 top, 1 right, 2 bottom, 3 left) of the cell with
+// corners tl, tr, br, bl, in cell-local (x, y); the same interpolation as
+// edge_point, without branches.
+__device__ __forceinline__ float2 edge_point_sel(float tl, float tr, float br, float bl, int e, float thr) {
+  const float va = e == 1 ? tr : e == 2 ? bl : tl;
+  const float vb = e == 0 ? tr : e == 3 ? bl : br;
+  const float da = va - thr, db = vb - thr;
+  const float t = da / (da - db);
+  const float ax = e == 1 ? 1.f : 0.f, ay = e == 2 ? 1.f : 0.f;
+  const bool horiz = (e & 1) == 0;
+  return make_float2(ax + (horiz ? t : 0.f), ay + (horiz ? 0.f : t));
+}
+
+// Emit: the warp's segments of a chunk are handed out one per lane in
+// rounds of 32 (most chunks need one): segment s belongs to the first lane
+// whose inclusive count exceeds s (a binary search over the warp scan), and
+// that lane's pixels are read from its slot in shared memory.
+constexpr int kEmitWarps = 8;
+
+__global__ void __launch_bounds__(32 * kEmitWarps, 4) k_ms_emit4(const float* __restrict__ img, int n, int planes,
+                                                                 float thr, const long long* __restrict__ chunk_start,
+                                                                 const long long* __restrict__ plane_start,
+                                                                 long long capacity, float4* __restrict__ seg,
+                                                                 int* __restrict__ cell_id) {
   __shared__ uint16_t tab[32];
+  // per lane: row i pixels 4l .. 4l + 4 at [0, 5), row i + 1 at [8, 13)
+  __shared__ __align__(16) float px[kEmitWarps][32][16];
   if (threadIdx.x < 32) tab[threadIdx.x] = kSegTable[threadIdx.x];
   __syncthreads();
-  const int chunks = n / 128, per_plane = n * chunks, p = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  for (int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < per_plane; r += (gridDim.x * blockDim.x) >> 5) {
-    const size_t w = (size_t)p * per_plane + r;
-    const int i = r / chunks, j0 = (r - i * chunks) * 128;
-    const Cells4 cs = load_cells4(img + (size_t)p * n * n, n, i, j0);
-    uint16_t ent[4];
-    int cnt = 0;
+  const int chunks = n / 128, p = blockIdx.y, lane = threadIdx.x & 31;
+  float(*mine)[16] = px[threadIdx.x >> 5];
+  const float* plane = img + (size_t)p * n * n;
+  const long long p0 = plane_start[p];
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
+    RowWalk w = row_walk_begin(plane, n, i, lane);
+    const long long* starts = chunk_start + ((size_t)p * n + i) * chunks;
+    for (int c = 0; c < chunks; ++c) {
+      const Chunk2 nx = row_walk_next(w, c, chunks);
+      const long long cbase = p0 + __ldg(starts + c);
+      float a4, b4;
+      fifth_corner(w.a, w.b, nx.a, nx.b, lane, &a4, &b4);
+      const unsigned top = inside5(w.a, a4, thr), bot = inside5(w.b, b4, thr);
+      const int cnt = segments4(top, bot);
+      int x = cnt;  // inclusive warp scan
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      ent[k] = cell_entry(cs.c[k], thr, tab);
-      cnt += ent[k] >> 8;
-    }
-    int x = cnt;  // inclusive warp scan
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    long long o = plane_start[p] + chunk_start[w] + (x - cnt);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int ns = ent[k] >> 8, j = j0 + 4 * lane + k;
-      for (int q = 0; q < ns; ++q, ++o) {
-        if (o >= capacity) continue;
-        const int s0 = (ent[k] >> (4 * q)) & 3, e0 = (ent[k] >> (4 * q + 2)) & 3;
-        const float2 a = edge_point(cs.c[k], s0, thr), b = edge_point(cs.c[k], e0, thr);
-        seg[o] = make_float4(j + a.x, i + a.y, j + b.x, i + b.y);
-        if (cell_id) cell_id[o] = i * n + j;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
+      const int total = __shfl_sync(0xffffffffu, x, 31);
+      if (total > 0) {  // uniform
+        *reinterpret_cast<float4*>(&mine[lane][0]) = w.a;
+        mine[lane][4] = a4;
+        *reinterpret_cast<float4*>(&mine[lane][8]) = w.b;
+        mine[lane][12] = b4;
+        __syncwarp();
+        for (int s0 = 0; s0 < total; s0 += 32) {
+          const int s = min(s0 + lane, total - 1);
+          int L = 0;  // owner lane: the number of lanes whose inclusive count is <= s
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1)
+            if (__shfl_sync(0xffffffffu, x, L + step - 1) <= s) L += step;
+          const int excl = __shfl_sync(0xffffffffu, x - cnt, L);
+          const unsigned tb = __shfl_sync(0xffffffffu, top | bot << 5, L);
+          if (s0 + lane < total) {
+            const unsigned t5 = tb & 31u, b5 = tb >> 5, v = t5 ^ b5;
+            const unsigned h = (t5 ^ (t5 >> 1)) + ((b5 ^ (b5 >> 1)) << 8) + (v << 16) + ((v >> 1) << 24);
+            int q = s - excl, k = 0;  // the owner's cell k and its segment q
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+              const int ck = int(((h >> kk) & 1u) + ((h >> (kk + 8)) & 1u) + ((h >> (kk + 16)) & 1u) +
+                                 ((h >> (kk + 24)) & 1u)) >> 1;
+              if (k == kk && q >= ck) {
+                q -= ck;
+                k = kk + 1;
+              }
+            }
+            const float* ra = mine[L];
+            const Cell cl{ra[k], ra[k + 1], ra[8 + k + 1], ra[8 + k]};
+            const uint16_t ent = tab[cell_case(cl, thr)];
+            const int s_e = (ent >> (4 * q)) & 3, e_e = (ent >> (4 * q + 2)) & 3;
+            const float2 pa = edge_point_sel(cl.tl, cl.tr, cl.br, cl.bl, s_e, thr);
+            const float2 pb = edge_point_sel(cl.tl, cl.tr, cl.br, cl.bl, e_e, thr);
+            const long long o = cbase + s;
+            const int j = c * 128 + 4 * L + k;
+            if (o < capacity) {
+              seg[o] = make_float4(j + pa.x, i + pa.y, j + pb.x, i + pb.y);
+              if (cell_id) cell_id[o] = i * n + j;
+            }
+          }
+        }
+        __syncwarp();  // slots reusable
+      }
+      w.a = nx.a;
+      w.b = nx.b;
     }
   }
 }
@@ -382,7 +481,7 @@ cudaError_t launch_contours(const float* img, int planes, int n, float thr, floa
   long long* plane_total = reinterpret_cast<long long*>(w + (sized * sizeof(int) + 255) / 256 * 256 +
                                                         (sized * sizeof(long long) + 255) / 256 * 256);
   if (vec) {
-    const int blocks = std::max(1, std::min(152 * 8 / std::max(1, planes / 8), n * (n / 128) / 8));
+    const int blocks = (n + 7) / 8;  // a warp per row of cells
     k_ms_count4<<<dim3(blocks, planes), 256, 0, st>>>(img, n, planes, thr, count);
     k_ms_scan<<<planes, 1024, 0, st>>>(count, int(per_plane), start, plane_total);
     k_ms_planes<<<1, 1, 0, st>>>(plane_total, planes, plane_start);
