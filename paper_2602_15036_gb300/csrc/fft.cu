@@ -149,6 +149,12 @@ __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const
   for (int p = 0; p < PERL; ++p)
 #pragma unroll
     for (int q = 0; q < RL; ++q) acc[p][q] = 0.f;
+  // middle-pass twiddles in registers: measured faster for 2048-point rows,
+  // slower for 1024 (where the registers they take cost more than the
+  // shared-memory reads they save)
+  constexpr bool kMid = MidTwiddles<N, +1>::kUsable && N >= 2048;
+  MidTwiddles<N, +1> mid;
+  if constexpr (kMid) mid.load(tw, t);
   for (int j = 0; j < nk; ++j) {
     const float l = __ldg(lp + j);
     if (l == 0.f) continue;  // uniform across the block
@@ -158,7 +164,10 @@ __global__ void __launch_bounds__(Plan<N>::NT, 512 / Plan<N>::NT) k_stage2(const
       return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
     };
     auto use = [&](int p, int q, int, float2 v) { acc[p][q] = fmaf(l, fmaf(v.x, v.x, v.y * v.y), acc[p][q]); };
-    fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, t, load, use);
+    if constexpr (kMid)
+      fft_load_use_mid<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, t, load, use, mid);
+    else
+      fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, t, load, use);
   }
   float* out = img + plane * img_plane + (size_t)y * N;
 #pragma unroll

@@ -217,6 +217,29 @@ __device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2*
   dft_reg<R, SIGN, BANDED>(v);
 }
 
+// Stockham output of one pass: butterfly j's R values to their places in
+// shared memory (no barrier).
+template <int N, int NT, int R, int NS>
+__device__ __forceinline__ void store_pass(float2* buf, int t, const float2 (&v)[PassShape<N, NT, R>::PER][R]) {
+  using S = PassShape<N, NT, R>;
+#pragma unroll
+  for (int p = 0; p < S::PER; ++p) {
+    const int j = t + p * NT;
+    if (j < S::NB) {
+      const int base = (j / NS) * NS * R + (j % NS);
+      if constexpr (NS == 1 && 16 % R == 0) {
+        // base is a multiple of R, which divides 16: base + r stays in one run of 16
+        float2* wb = buf + pad16(base);
+#pragma unroll
+        for (int r = 0; r < R; ++r) wb[r] = v[p][r];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[pad16_step<NS>(base, r)] = v[p][r];
+      }
+    }
+  }
+}
+
 // One pass whose inputs come from `load(index)` (or shared memory when
 // FROM_SMEM) and whose outputs go to shared memory.  Ends with a barrier.
 // A loader that also takes (p, r, index) gets the butterfly slot p and the
@@ -250,22 +273,7 @@ __device__ __forceinline__ void pass_to_smem(float2* buf, const float2* tw, int 
     }
   }
   __syncthreads();
-#pragma unroll
-  for (int p = 0; p < S::PER; ++p) {
-    const int j = t + p * NT;
-    if (j < S::NB) {
-      const int base = (j / NS) * NS * R + (j % NS);
-      if constexpr (NS == 1 && 16 % R == 0) {
-        // base is a multiple of R, which divides 16: base + r stays in one run of 16
-        float2* wb = buf + pad16(base);
-#pragma unroll
-        for (int r = 0; r < R; ++r) wb[r] = v[p][r];
-      } else {
-#pragma unroll
-        for (int r = 0; r < R; ++r) buf[pad16_step<NS>(base, r)] = v[p][r];
-      }
-    }
-  }
+  store_pass<N, NT, R, NS>(buf, t, v);
   __syncthreads();
 }
 
@@ -312,6 +320,55 @@ __device__ __forceinline__ void fft_load_use(float2* buf, const float2* tw, int 
     pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
     pass_last<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, TwOff<N>::p2>(buf, tw, t, use);
   }
+}
+
+// Twiddles of the middle pass of a three-pass plan, held in registers.
+// When the plan's thread count is a multiple of that pass's stride, all
+// butterflies of a thread use the same R - 1 twiddles, so a thread that runs
+// many transforms loads them once.
+template <int N, int SIGN>
+struct MidTwiddles {
+  using PL = Plan<N>;
+  static constexpr int R = PL::R[1], NS = PL::R[0];
+  static constexpr bool kUsable = PL::P == 3 && PL::NT % NS == 0;
+  float2 w[R - 1];
+  __device__ __forceinline__ void load(const float2* tw, int t) {
+    const int k = t % NS;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 x = tw[TwOff<N>::p1 + (r - 1) * NS + k];
+      if (SIGN > 0) x.y = -x.y;
+      w[r - 1] = x;
+    }
+  }
+};
+
+// fft_load_use with the middle pass's twiddles from `mid` (same result).
+template <int N, int SIGN, class Load, class Use, bool BANDED = false>
+__device__ __forceinline__ void fft_load_use_mid(float2* buf, const float2* tw, int t, Load& load, Use& use,
+                                                 const MidTwiddles<N, SIGN>& mid) {
+  using PL = Plan<N>;
+  using M = MidTwiddles<N, SIGN>;
+  static_assert(M::kUsable, "middle-pass twiddles are per thread only when NT is a multiple of the stride");
+  constexpr int NT = PL::NT, R = M::R, NS = M::NS;
+  using S = PassShape<N, NT, R>;
+  pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false, Load, BANDED>(buf, tw, t, load);
+  float2 v[S::PER][R];
+#pragma unroll
+  for (int p = 0; p < S::PER; ++p) {
+    const int j = t + p * NT;
+    if (j < S::NB) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[p][r] = buf[pad16_step<S::NB>(j, r)];
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], mid.w[r - 1]);
+      dft_reg<R, SIGN, false>(v[p]);
+    }
+  }
+  __syncthreads();
+  store_pass<N, NT, R, NS>(buf, t, v);
+  __syncthreads();
+  pass_last<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, TwOff<N>::p2>(buf, tw, t, use);
 }
 
 // Full transform in place in shared memory (padded layout on entry and on
