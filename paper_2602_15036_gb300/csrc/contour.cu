@@ -337,12 +337,14 @@ __global__ void __launch_bounds__(32 * kEmitWarps, 4) k_ms_emit4(const float* __
                                                                  long long capacity, float4* __restrict__ seg,
                                                                  int* __restrict__ cell_id) {
   __shared__ uint16_t tab[32];
-  // per lane: row i pixels 4l .. 4l + 4 at [0, 5), row i + 1 at [8, 13)
-  __shared__ __align__(16) float px[kEmitWarps][32][16];
+  // per warp: value v of lane l at [v][l] (row i pixels 4l .. 4l + 4 as
+  // v = 0..4, row i + 1 as v = 5..9); the odd row length keeps the reads of
+  // different lanes and values on different banks
+  __shared__ float px[kEmitWarps][10][33];
   if (threadIdx.x < 32) tab[threadIdx.x] = kSegTable[threadIdx.x];
   __syncthreads();
   const int chunks = n / 128, p = blockIdx.y, lane = threadIdx.x & 31;
-  float(*mine)[16] = px[threadIdx.x >> 5];
+  float(*mine)[33] = px[threadIdx.x >> 5];
   const float* plane = img + (size_t)p * n * n;
   const long long p0 = plane_start[p];
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += (gridDim.x * blockDim.x) >> 5) {
@@ -363,10 +365,16 @@ __global__ void __launch_bounds__(32 * kEmitWarps, 4) k_ms_emit4(const float* __
       }
       const int total = __shfl_sync(0xffffffffu, x, 31);
       if (total > 0) {  // uniform
-        *reinterpret_cast<float4*>(&mine[lane][0]) = w.a;
-        mine[lane][4] = a4;
-        *reinterpret_cast<float4*>(&mine[lane][8]) = w.b;
-        mine[lane][12] = b4;
+        mine[0][lane] = w.a.x;
+        mine[1][lane] = w.a.y;
+        mine[2][lane] = w.a.z;
+        mine[3][lane] = w.a.w;
+        mine[4][lane] = a4;
+        mine[5][lane] = w.b.x;
+        mine[6][lane] = w.b.y;
+        mine[7][lane] = w.b.z;
+        mine[8][lane] = w.b.w;
+        mine[9][lane] = b4;
         __syncwarp();
         for (int s0 = 0; s0 < total; s0 += 32) {
           const int s = min(s0 + lane, total - 1);
@@ -389,8 +397,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps, 4) k_ms_emit4(const float* __
                 k = kk + 1;
               }
             }
-            const float* ra = mine[L];
-            const Cell cl{ra[k], ra[k + 1], ra[8 + k + 1], ra[8 + k]};
+            const Cell cl{mine[k][L], mine[k + 1][L], mine[5 + k + 1][L], mine[5 + k][L]};
             const uint16_t ent = tab[cell_case(cl, thr)];
             const int s_e = (ent >> (4 * q)) & 3, e_e = (ent >> (4 * q + 2)) & 3;
             const float2 pa = edge_point_sel(cl.tl, cl.tr, cl.br, cl.bl, s_e, thr);

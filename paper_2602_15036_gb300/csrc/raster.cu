@@ -24,7 +24,10 @@ namespace litho {
 
 namespace {
 
-constexpr int kTile = 16, kTileThreads = kTile * kTile, kTileCache = 1024;
+constexpr int kTile = 16, kTileThreads = kTile * kTile;
+// tile kernel: 64 threads, 4 pixels each, and a 256-piece cache (larger
+// lists are read from global memory), so that 32 tiles fit on an SM
+constexpr int kRastThreads = 64, kRastPix = kTile * kTile / kRastThreads, kTileCache = 256;
 
 // Pieces of rectangle r (x0, y0, x1, y1) after the shift into [0, n) and the
 // split at n; calls f(piece) for each nonempty one.
@@ -117,8 +120,9 @@ __global__ void k_rast_base(const int* __restrict__ total, int b, long long* __r
   clip_base[b] = run;
 }
 
-// Union area of the pieces within the unit pixel at (px, py).
-__device__ float pixel_coverage(const float4* pcs, int np, float px, float py) {
+// 1 when one piece covers the unit pixel at (px, py), 0 when none reaches
+// into it, else -1 (a grey pixel: pixel_area measures it).
+__device__ __forceinline__ float pixel_class(const float4* pcs, int np, float px, float py) {
   const float X1 = px + 1.f, Y1 = py + 1.f;
   bool any = false;
   for (int k = 0; k < np; ++k) {
@@ -126,7 +130,12 @@ __device__ float pixel_coverage(const float4* pcs, int np, float px, float py) {
     if (p.x <= px && p.z >= X1 && p.y <= py && p.w >= Y1) return 1.f;
     any |= p.x < X1 && p.z > px && p.y < Y1 && p.w > py;
   }
-  if (!any) return 0.f;
+  return any ? -1.f : 0.f;
+}
+
+// Union area of the pieces within the unit pixel at (px, py).
+__device__ float pixel_area(const float4* pcs, int np, float px, float py) {
+  const float X1 = px + 1.f, Y1 = py + 1.f;
   float area = 0.f, xa = px;
   while (xa < X1) {
     float xb = X1;  // next piece edge above xa
@@ -159,28 +168,53 @@ __device__ float pixel_coverage(const float4* pcs, int np, float px, float py) {
   return area;
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_rast_tiles(const float4* __restrict__ list, const int* __restrict__ count,
+__global__ void __launch_bounds__(kRastThreads) k_rast_tiles(const float4* __restrict__ list, const int* __restrict__ count,
                                                              const int* __restrict__ tile_start,
                                                              const long long* __restrict__ clip_base,
                                                              const int* __restrict__ bad, int n,
                                                              float* __restrict__ mask) {
   __shared__ float4 cache[kTileCache];
+  __shared__ int grey[kTile * kTile];
+  __shared__ int n_grey;
   const int tiles = n / kTile, c = blockIdx.y, t = blockIdx.x;
   const size_t ti = (size_t)c * tiles * tiles + t;
   const int ty = t / tiles, tx = t % tiles;
-  const int i = ty * kTile + threadIdx.x / kTile, j = tx * kTile + threadIdx.x % kTile;
+  // pixel q = threadIdx.x + r * kRastThreads of the tile (row q / 16, column q % 16)
+  auto at = [&](int q) -> float* { return mask + ((size_t)c * n + ty * kTile + q / kTile) * n + tx * kTile + q % kTile; };
   if (bad[c]) {  // uniform across the block
-    mask[((size_t)c * n + i) * n + j] = __int_as_float(0x7fc00000);
+#pragma unroll
+    for (int r = 0; r < kRastPix; ++r) *at(threadIdx.x + r * kRastThreads) = __int_as_float(0x7fc00000);
     return;
   }
   const int np = count[ti];
   const float4* pcs = list + clip_base[c] + tile_start[ti];
+  if (threadIdx.x == 0) n_grey = 0;
   if (np <= kTileCache) {
-    for (int k = threadIdx.x; k < np; k += kTileThreads) cache[k] = pcs[k];
-    __syncthreads();
+    for (int k = threadIdx.x; k < np; k += kRastThreads) cache[k] = pcs[k];
     pcs = cache;
   }
-  mask[((size_t)c * n + i) * n + j] = pixel_coverage(pcs, np, float(j), float(i));
+  __syncthreads();
+  // empty and fully covered pixels at once; the grey ones are gathered so
+  // that whole warps run their sweeps
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int r = 0; r < kRastPix; ++r) {
+    const int q = threadIdx.x + r * kRastThreads;
+    const float cls = pixel_class(pcs, np, float(tx * kTile + q % kTile), float(ty * kTile + q / kTile));
+    const unsigned m = __ballot_sync(0xffffffffu, cls < 0.f);
+    int slot = 0;
+    if (lane == 0 && m) slot = atomicAdd(&n_grey, __popc(m));
+    slot = __shfl_sync(0xffffffffu, slot, 0) + __popc(m & ((1u << lane) - 1u));
+    if (cls < 0.f)
+      grey[slot] = q;
+    else
+      *at(q) = cls;
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < n_grey; g += kRastThreads) {
+    const int q = grey[g];
+    *at(q) = pixel_area(pcs, np, float(tx * kTile + q % kTile), float(ty * kTile + q / kTile));
+  }
 }
 
 // Workspace: per-tile counts, starts and cursors, the clips' flags, totals and
@@ -249,7 +283,7 @@ cudaError_t launch_raster(const float4* rects, const long long* rect_start, int 
     k_rast_bin<true><<<grid, 256, 0, st>>>(rects, rect_start, n, max_rects, float(max_side), L.count, L.tile_start,
                                            L.clip_base, L.cursor, L.list, L.bad);
   }
-  k_rast_tiles<<<dim3(unsigned(tiles2), b), kTileThreads, 0, st>>>(L.list, L.count, L.tile_start, L.clip_base, L.bad,
+  k_rast_tiles<<<dim3(unsigned(tiles2), b), kRastThreads, 0, st>>>(L.list, L.count, L.tile_start, L.clip_base, L.bad,
                                                                    n, mask);
   return cudaGetLastError();
 }
