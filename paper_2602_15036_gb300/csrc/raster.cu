@@ -181,13 +181,15 @@ __global__ void __launch_bounds__(kRastThreads) k_rast_tiles(const float4* __res
   const int ty = t / tiles, tx = t % tiles;
   // pixel q = threadIdx.x + r * kRastThreads of the tile (row q / 16, column q % 16)
   auto at = [&](int q) -> float* { return mask + ((size_t)c * n + ty * kTile + q / kTile) * n + tx * kTile + q % kTile; };
-  if (bad[c]) {  // uniform across the block
+  // the flag and the tile's list are fetched together (a flagged clip's
+  // counts are read but its list is not)
+  const int flagged = bad[c], np = count[ti];
+  const float4* pcs = list + clip_base[c] + tile_start[ti];
+  if (flagged) {  // uniform across the block
 #pragma unroll
     for (int r = 0; r < kRastPix; ++r) *at(threadIdx.x + r * kRastThreads) = __int_as_float(0x7fc00000);
     return;
   }
-  const int np = count[ti];
-  const float4* pcs = list + clip_base[c] + tile_start[ti];
   if (threadIdx.x == 0) n_grey = 0;
   if (np <= kTileCache) {
     for (int k = threadIdx.x; k < np; k += kRastThreads) cache[k] = pcs[k];
