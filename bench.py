@@ -465,11 +465,13 @@ def run_aerial(args):
 
 def run_ilt(args):
     """16 clips of 1024^2, annular 21x21, K=16, 5 focus planes; one step = litho_ilt_grad on all clips
-    plus the gradient-descent update theta -= 0.5 g / max|g| (torch, outside the library)."""
+    plus the gradient-descent update theta -= 0.5 g / max|g| (torch, outside the library).  --precision
+    fft32/coarse (default) evaluates fields and adjoint on the 512-point coarse grid, fft32 on 1024."""
     import paper_2602_15036_gb300 as P
     from paper_2602_15036_gb300 import litho as L
     ctx = Ctx(args)
     torch = ctx.torch
+    prec = args.precision if args.precision in ("fft32", "fft32/coarse") else "fft32/coarse"
     n, pixel, k, focus, clips = 1024, 8.0, 16, [-60.0, -30.0, 0.0, 30.0, 60.0], 16
     optics = dict(wavelength_nm=193.0, na=1.35, n_medium=1.44, kind="annular", src_grid=21, sigma_in=0.6,
                   sigma_out=0.9)
@@ -483,7 +485,8 @@ def run_ilt(args):
     losses = []
 
     def step():
-        _, loss = P.litho_ilt_grad(kern, theta, target, grad=grad, workspace=ws, want_loss=True, stream=stream)
+        _, loss = P.litho_ilt_grad(kern, theta, target, grad=grad, workspace=ws, want_loss=True, precision=prec,
+                                   stream=stream)
         losses.append(float(loss.sum()))
         theta.sub_(0.5 * grad / grad.abs().amax(dim=(1, 2), keepdim=True).clamp_min(1e-30))
 
@@ -497,7 +500,8 @@ def run_ilt(args):
             "value": whole_job_rate(clips * n * n * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
             "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
             "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "ilt 16x1024^2@8nm annular21 K=16 focus(-60..60 step 30)", "clips_per_gpu": clips},
+            "config": {"workload": "ilt 16x1024^2@8nm annular21 K=16 focus(-60..60 step 30)", "clips_per_gpu": clips,
+                       "precision": prec, "grid": kern.grid(prec) if prec.endswith("/coarse") else n},
             "loss_first_last": [losses[0], losses[-1]],
             "stages_ms_per_step": {kk: v[0] / (args.steps + args.warmup) for kk, v in prof.items()},
             "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}
@@ -770,7 +774,7 @@ def run_serve(args):
             "requests": total, "arrival_rate_rps": sweep[0.8]["arrival_rate_rps"], "saturated_rps": sat_rps,
             "p50_ms": sweep[0.8]["p50_ms"], "p99_ms": sweep[0.8]["p99_ms"], "load_sweep": sweep,
             "higher_is_better": True, "dtype": "f32",
-            "data": "synthetic", "config": {"precision": "fft32/coarse (images), fft32 (ILT)", "slots": 8},
+            "data": "synthetic", "config": {"precision": "fft32/coarse (images and ILT steps)", "slots": 8},
             "stats": {k: s[k] for k in ("submitted", "completed", "rejected", "cancelled", "hbm_high_water",
                                          "kernel_sets_cached")},
             "status_counts": statuses, "first_error": first_err[0] if first_err else None}

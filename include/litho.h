@@ -359,7 +359,14 @@ litho_status litho_ilt_workspace_size(const litho_kernels* h, int b, size_t* ful
  * loss_host (may be NULL): b doubles, reduced in FP64 on the device; when
  * given, the call waits for the stream.  A workspace between min_bytes and
  * full_bytes selects recomputation of the forward fields; below min_bytes is
- * ENOMEM.  Only LITHO_PREC_FFT32 is implemented (else EUNSUPPORTED). */
+ * ENOMEM.  prec: LITHO_PREC_FFT32 (else EUNSUPPORTED), optionally with
+ * LITHO_GRID_COARSE: the fields, the image and the adjoint transforms are
+ * evaluated on the coarse grid of litho_kernels_grid (when it is below n),
+ * the image is interpolated exactly to n for the resist and the loss, and
+ * d loss / dI is low-passed to the image band (2C) and sampled on that grid
+ * before the adjoint; the products with the fields are cropped to the field
+ * band, where nothing aliases on a grid of at least 2C points, so the
+ * gradient is the full-grid one up to FP32 rounding. */
 litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, const float* target_dev, int b,
                             double dose, double mask_steep, double resist_steep, double threshold, double sigma_nm,
                             litho_precision prec, float* grad_dev, double* loss_host, void* workspace_dev,

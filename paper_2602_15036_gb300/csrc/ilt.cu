@@ -280,6 +280,11 @@ struct IltLayout {
   float2 *rowbuf, *mhat, *t1, *u, *sk, *s, *qf;
   float *img, *blur;
   double *partial, *loss;
+  // coarse grid (nc x nc, band 2C of the image): coarse images and the coarse
+  // samples of the low-passed dL/dI (ic), row spectra on nc (mid), band rows
+  // on N (big), image spectra (spec)
+  float* ic;
+  float2 *mid, *big, *spec;
   size_t bytes;
 };
 
@@ -306,6 +311,13 @@ IltLayout ilt_layout(const litho_kernels* h, int b, int P, void* base) {
   L.blur = reinterpret_cast<float*>(take(P * N * N * 4));
   L.partial = reinterpret_cast<double*>(take(kPartials * 8));
   L.loss = reinterpret_cast<double*>(take(size_t(b) * 8));
+  const size_t NC = h->nc, C2 = 2 * C;
+  if (NC > 0) {
+    L.ic = reinterpret_cast<float*>(take(P * NC * NC * 4));
+    L.mid = reinterpret_cast<float2*>(take(P * NC * C2 * 8));
+    L.big = reinterpret_cast<float2*>(take(P * N * C2 * 8));
+    L.spec = reinterpret_cast<float2*>(take(P * C2 * C2 * 8));
+  }
   L.bytes = off;
   return L;
 }
@@ -341,8 +353,8 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
     set_error("null argument or b < 1");
     return LITHO_EINVAL;
   }
-  if (prec != LITHO_PREC_FFT32) {
-    set_error("litho_ilt_grad implements the FP32 FFT path only (LITHO_PREC_FFT32)");
+  if ((int(prec) & ~LITHO_GRID_COARSE) != LITHO_PREC_FFT32) {
+    set_error("litho_ilt_grad implements the FP32 FFT path only (LITHO_PREC_FFT32, optionally | LITHO_GRID_COARSE)");
     return LITHO_EUNSUPPORTED;
   }
   if (!std::isfinite(dose) || !std::isfinite(mask_steep) || !std::isfinite(resist_steep) ||
@@ -379,6 +391,17 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nn = size_t(N) * N;
   const float scale = float(2.0 * dose / (double(N) * double(N)));
+  // Coarse grid: the fields, the image and the adjoint transforms run on
+  // nc >= 2C.  The image is interpolated exactly to N for the resist and the
+  // loss; dL/dI enters the adjoint only through its frequencies below C in
+  // magnitude (the products with the fields are cropped to the field band),
+  // so it is low-passed to the 2C band and sampled on nc, times (N/nc)^2 for
+  // the sums over nc^2 instead of N^2 points.  No product frequency aliases
+  // into the field band on nc >= 2C, so the result is the full-grid one.
+  const bool coarse = (int(prec) & LITHO_GRID_COARSE) && h->nc > 0 && interp_cols_supported(h->nc, N);
+  const int NE = coarse ? h->nc : N, C2 = 2 * C;
+  const float2* twe = coarse ? h->d_twc : h->d_tw;
+  const float lp_scale = float((double(N) / NE) * (double(N) / NE));
   for (int clip = 0; clip < b; ++clip) {
     {
       ProfScope ps(kStageIltForward, st, 3);
@@ -387,11 +410,18 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
       LITHO_TRY_CUDA(launch_mask_spectrum(L.m, 1, N, C, h->d_tw, L.rowbuf, L.mhat, st));
     }
     for (int f0 = 0; f0 < F; f0 += P) {
+      const float2* phi = h->d_phi + size_t(f0) * K * C * C;
+      const float* lam = h->d_lambda + size_t(f0) * K;
       {
-        ProfScope ps(kStageIltForward, st, 5);
-        LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, P * K, N, C, h->d_tw, L.t1, st));
-        LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda + size_t(f0) * K, K, N, C, float(dose), h->d_tw, L.img,
-                                         P, (long long)K * N * C, (long long)nn, st));
+        ProfScope ps(kStageIltForward, st, coarse ? 8 : 5);
+        LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, P * K, NE, C, twe, L.t1, st));
+        LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, P,
+                                         (long long)K * NE * C, (long long)NE * NE, st));
+        if (coarse) {
+          LITHO_TRY_CUDA(launch_mask_rows(L.ic, P, NE, C2, twe, L.mid, st));
+          LITHO_TRY_CUDA(launch_interp_cols(L.mid, P, NE, N, C2, twe, h->d_tw, nullptr, L.big, st));
+          LITHO_TRY_CUDA(launch_band_rows_real(L.big, P, N, C2, 1.0f, h->d_tw, L.img, st));
+        }
         LITHO_TRY_CUDA(launch_resist(L.img, P, N, taps, float(threshold), L.blur, nullptr, st));
         k_resist_grad<<<kPartials, 256, 0, st>>>(L.blur, target_dev + clip * nn, nn, P, float(resist_steep),
                                                  float(threshold), L.img, L.partial);
@@ -400,11 +430,17 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
         LITHO_TRY_CUDA(cudaGetLastError());
       }
       {
-        ProfScope ps(kStageIltBackward, st, 4);
+        ProfScope ps(kStageIltBackward, st, coarse ? 7 : 4);
         LITHO_TRY_CUDA(launch_resist(L.img, P, N, taps, float(threshold), L.blur, nullptr, st));
-        LITHO_TRY_CUDA(launch_adj_rows(N, L.t1, h->d_lambda + size_t(f0) * K, K, C, L.blur, h->d_tw, L.u, P, st));
-        LITHO_TRY_CUDA(launch_adj_cols(N, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
-                                       h->d_tw, L.sk, P * K, st));
+        const float* gsrc = L.blur;
+        if (coarse) {
+          LITHO_TRY_CUDA(launch_mask_spectrum(L.blur, P, N, C2, h->d_tw, L.big, L.spec, st));
+          LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, P, NE, C2, twe, L.mid, st));
+          LITHO_TRY_CUDA(launch_band_rows_real(L.mid, P, NE, C2, lp_scale, twe, L.ic, st));
+          gsrc = L.ic;
+        }
+        LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, gsrc, twe, L.u, P, st));
+        LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, P * K, st));
         k_sum_planes<<<256, 256, 0, st>>>(L.sk, P * K, size_t(C) * C, L.s, f0 > 0 ? 1 : 0);
         LITHO_TRY_CUDA(cudaGetLastError());
       }

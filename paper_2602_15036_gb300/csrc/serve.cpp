@@ -241,7 +241,8 @@ litho_status launch(litho_server* s, Req* q, litho_kernels* h, std::string* err)
   }
   if (ilt) {
     st = litho_ilt_grad(h, d_in, d_tg, 1, r.dose, r.mask_steep, r.resist_steep, r.threshold, r.sigma_nm,
-                        LITHO_PREC_FFT32, d_out, nullptr, ws, ws_bytes, sl.stream);
+                        static_cast<litho_precision>(LITHO_PREC_FFT32 | LITHO_GRID_COARSE), d_out, nullptr, ws,
+                        ws_bytes, sl.stream);
   } else {
     st = litho_aerial(h, d_in, 1, r.dose, static_cast<litho_precision>(r.precision), d_out, ws, ws_bytes, sl.stream);
   }

@@ -23,11 +23,11 @@ def _oracle(theta, target, lam, phi, pixel):
                             sigma_nm=PARAMS["sigma_nm"], pixel_nm=pixel)
 
 
-def _gpu(litho_lib, cuda, kern, thetas, targets, workspace=None):
+def _gpu(litho_lib, cuda, kern, thetas, targets, workspace=None, precision="fft32"):
     import torch
     th = torch.from_numpy(np.ascontiguousarray(thetas, dtype=np.float32)).to(cuda)
     tg = torch.from_numpy(np.ascontiguousarray(targets, dtype=np.float32)).to(cuda)
-    g, loss = litho_lib.litho_ilt_grad(kern, th, tg, workspace=workspace, **PARAMS)
+    g, loss = litho_lib.litho_ilt_grad(kern, th, tg, workspace=workspace, precision=precision, **PARAMS)
     return g.cpu().numpy().astype(np.float64), loss
 
 
@@ -38,15 +38,18 @@ def _check(g, ref, pts):
     return rel, per
 
 
+@pytest.mark.parametrize("precision", ["fft32", "fft32/coarse"])
 @pytest.mark.parametrize("n,pixel,k,focus,b", [(128, 8.0, 6, [-60.0, -30.0, 0.0, 30.0, 60.0], 2),
                                                (256, 8.0, 8, [0.0, 40.0], 1)])
-def test_ilt_gradient_matches_oracle(litho_lib, cuda, n, pixel, k, focus, b):
+def test_ilt_gradient_matches_oracle(litho_lib, cuda, n, pixel, k, focus, b, precision):
     lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, focus, k)
     kern = litho_lib.litho_upload_kernels(n, pixel, lam, phi)
+    if precision.endswith("/coarse"):
+        assert 0 < kern.grid(precision) < n  # the coarse grid is in use
     clips = [synth.ilt_clip(n, pixel, seed=500 + i) for i in range(b)]
     thetas = np.stack([c[0] for c in clips])
     targets = np.stack([c[1] for c in clips])
-    g, loss = _gpu(litho_lib, cuda, kern, thetas, targets)
+    g, loss = _gpu(litho_lib, cuda, kern, thetas, targets, precision=precision)
     st = synth.Stream(64)
     pts = list(zip(st.integers(0, n - 1, 64), st.integers(0, n - 1, 64)))
     for i in range(b):
@@ -57,7 +60,8 @@ def test_ilt_gradient_matches_oracle(litho_lib, cuda, n, pixel, k, focus, b):
         assert rel <= 1e-4 and per <= 1e-4
 
 
-def test_ilt_recompute_mode_equals_full_mode(litho_lib, cuda):
+@pytest.mark.parametrize("precision", ["fft32", "fft32/coarse"])
+def test_ilt_recompute_mode_equals_full_mode(litho_lib, cuda, precision):
     import torch
     n, pixel = 128, 8.0
     lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, [-40.0, 0.0, 40.0], 6)
@@ -65,15 +69,35 @@ def test_ilt_recompute_mode_equals_full_mode(litho_lib, cuda):
     theta, target = synth.ilt_clip(n, pixel, seed=9)
     full, mn = litho_lib.litho_ilt_workspace_size(kern, 1)
     assert mn < full
-    g_full, l_full = _gpu(litho_lib, cuda, kern, theta[None], target[None])
+    g_full, l_full = _gpu(litho_lib, cuda, kern, theta[None], target[None], precision=precision)
     ws = torch.empty(mn, dtype=torch.uint8, device=cuda)
-    g_min, l_min = _gpu(litho_lib, cuda, kern, theta[None], target[None], workspace=ws)
+    g_min, l_min = _gpu(litho_lib, cuda, kern, theta[None], target[None], workspace=ws, precision=precision)
     assert abs(l_full[0] - l_min[0]) <= 1e-12 * l_full[0]
     assert np.abs(g_full - g_min).max() <= 1e-6 * np.abs(g_full).max()
     small = torch.empty(mn - 256, dtype=torch.uint8, device=cuda)
     with pytest.raises(litho_lib.LithoError) as e:
-        _gpu(litho_lib, cuda, kern, theta[None], target[None], workspace=small)
+        _gpu(litho_lib, cuda, kern, theta[None], target[None], workspace=small, precision=precision)
     assert e.value.status == litho_lib.ENOMEM
+
+
+def test_ilt_coarse_grid_equals_full_grid(litho_lib, cuda):
+    """The coarse-grid adjoint is exact (no product frequency aliases into the
+    field band on nc >= 2C), so it agrees with the full-grid gradient to FP32
+    rounding: 1e-5 relative, ten times inside the oracle bar."""
+    n, pixel = 256, 8.0
+    lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, [-50.0, 0.0, 50.0], 8)
+    kern = litho_lib.litho_upload_kernels(n, pixel, lam, phi)
+    assert 0 < kern.grid("fft32/coarse") < n
+    clips = [synth.ilt_clip(n, pixel, seed=700 + i) for i in range(2)]
+    thetas = np.stack([c[0] for c in clips])
+    targets = np.stack([c[1] for c in clips])
+    g_f, l_f = _gpu(litho_lib, cuda, kern, thetas, targets)
+    g_c, l_c = _gpu(litho_lib, cuda, kern, thetas, targets, precision="fft32/coarse")
+    for i in range(2):
+        assert abs(l_c[i] - l_f[i]) <= 1e-5 * l_f[i]
+        rel = np.linalg.norm(g_c[i] - g_f[i]) / np.linalg.norm(g_f[i])
+        print(f"clip {i}: coarse vs full grid, loss {l_c[i]:.6f} / {l_f[i]:.6f}, grad rel l2 {rel:.2e}")
+        assert rel <= 1e-5
 
 
 def test_ilt_fp32_finite_differences(litho_lib, cuda):
