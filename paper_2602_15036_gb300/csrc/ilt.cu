@@ -25,6 +25,7 @@
 //                    real part, chain factor -> dL/dtheta
 // The fields E are never stored: each backward row recomputes E_fk from the
 // stage-1 field T_fk (C values per row) that the forward pass kept.
+#include <algorithm>
 #include <cmath>
 
 #include "fft_common.cuh"
@@ -43,9 +44,16 @@ __global__ void k_sigmoid(const float* __restrict__ theta, float alpha, float* _
     m[i] = 1.0f / (1.0f + expf(-alpha * theta[i]));
 }
 
+// Clip blockIdx.y: its `planes` planes of ib and q, its target, its
+// kPartials partial sums (the same partition for every group size).
 __global__ void __launch_bounds__(256) k_resist_grad(const float* __restrict__ ib, const float* __restrict__ target,
                                                      size_t nn, int planes, float beta, float thr,
                                                      float* __restrict__ q, double* __restrict__ partial) {
+  const size_t clip = blockIdx.y;
+  ib += clip * planes * nn;
+  q += clip * planes * nn;
+  target += clip * nn;
+  partial += clip * gridDim.x;
   double acc = 0.0;
   const size_t total = nn * planes;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
@@ -65,9 +73,12 @@ __global__ void __launch_bounds__(256) k_resist_grad(const float* __restrict__ i
   }
 }
 
+// Clip blockIdx.x: out[clip] (+)= the fixed-order sum of its `count` partials.
 __global__ void __launch_bounds__(1024) k_reduce_loss(const double* __restrict__ partial, int count,
                                                       double* __restrict__ out, int accumulate) {
   __shared__ double s[1024];
+  partial += (size_t)blockIdx.x * count;
+  out += blockIdx.x;
   double a = 0.0;
   for (int i = threadIdx.x; i < count; i += 1024) a += partial[i];
   s[threadIdx.x] = a;
@@ -81,10 +92,12 @@ __global__ void __launch_bounds__(1024) k_reduce_loss(const double* __restrict__
 
 // Backward rows: for every kernel of the plane, E = inverse FFT of the band row
 // T[y][:], P = G[y][:] E, U[y][c] = forward FFT of P on the crop columns.
+// Plane p takes lam[(p mod lam_period) nk ...] (clips of a group repeat the focus planes).
 template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restrict__ t1, const float* __restrict__ lam,
                                                           int nk, int crop, const float* __restrict__ g,
-                                                          const float2* __restrict__ tw_g, float2* __restrict__ u) {
+                                                          const float2* __restrict__ tw_g, float2* __restrict__ u,
+                                                          int lam_period) {
   using PL = Plan<N>;
   constexpr int NT = PL::NT, RL = PL::R[PL::P - 1];
   constexpr int PERL = PassShape<N, NT, RL>::PER;
@@ -105,7 +118,7 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restri
     }
   __syncthreads();
   for (int k = 0; k < nk; ++k) {
-    if (lam[plane * nk + k] == 0.f) continue;
+    if (lam[(plane % lam_period) * nk + k] == 0.f) continue;
     const size_t rowoff = (((size_t)plane * nk + k) * N + y) * crop;
     const float2* row = t1 + rowoff;
     auto load_band = [&](int idx) {
@@ -129,19 +142,20 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restri
 
 template <int N> struct AdjW { static constexpr int W = ColW<N>::W; };
 
-// Backward columns: forward FFT over y of U_j[:, c], crop rows, times lam_j conj(Phi_j).
+// Backward columns: forward FFT over y of U_j[:, c], crop rows, times lam_j conj(Phi_j);
+// field j uses kernel j mod period.
 template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const float2* __restrict__ u,
                                                                         const float2* __restrict__ phi,
                                                                         const float* __restrict__ lam, int crop,
                                                                         const float2* __restrict__ tw_g,
-                                                                        float2* __restrict__ sk) {
+                                                                        float2* __restrict__ sk, int period) {
   constexpr int W = AdjW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
-  const int j = blockIdx.y, c0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
-  const float l = lam[j];
+  const int j = blockIdx.y, jk = j % period, c0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
+  const float l = lam[jk];
   float2* dst = sk + (size_t)j * crop * crop + c0;
   if (l == 0.f) {  // uniform across the block
     for (int i = tid; i < crop * W; i += blockDim.x) dst[(size_t)(i / W) * crop + i % W] = make_float2(0.f, 0.f);
@@ -155,7 +169,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
   }
   __syncthreads();
   fft_smem<N, -1>(buf + (tid / NT) * LD, tw, tid % NT);
-  const float2* ph = phi + (size_t)j * crop * crop + c0;
+  const float2* ph = phi + (size_t)jk * crop * crop + c0;
   for (int i = tid; i < crop * W; i += blockDim.x) {
     const int cv = i / W, w = i % W;
     const float2 h = buf[w * LD + pad16((cv - half + N) % N)];
@@ -169,8 +183,11 @@ __global__ void k_fill(float* __restrict__ p, float v, size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
+// s[clip] (+)= sum over the clip's `planes` planes of sk, in order (clip = blockIdx.y).
 __global__ void k_sum_planes(const float2* __restrict__ sk, int planes, size_t cc, float2* __restrict__ s,
                              int accumulate) {
+  sk += (size_t)blockIdx.y * planes * cc;
+  s += (size_t)blockIdx.y * cc;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cc; i += (size_t)gridDim.x * blockDim.x) {
     float2 a = accumulate ? s[i] : make_float2(0.f, 0.f);
     for (int j = 0; j < planes; ++j) {
@@ -193,6 +210,10 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_grad_rows(const float2* __restr
   load_twiddles<N>(tw, tw_g);
   __syncthreads();
   const int y = blockIdx.x, t = threadIdx.x, half = crop / 2;
+  const size_t clip = blockIdx.y;  // clip of the group: its band rows, mask and gradient
+  qf += clip * N * crop;
+  if (m) m += clip * N * N;
+  grad += clip * N * N;
   const float2* row = qf + (size_t)y * crop;
   auto load = [&](int idx) {
     const int c = freq_of_idx(idx, N) + half;
@@ -213,32 +234,32 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_grad_rows(const float2* __restr
 
 template <int N>
 cudaError_t adj_rows_n(const float2* t1, const float* lam, int nk, int crop, const float* g, const float2* tw,
-                       float2* u, int planes, cudaStream_t st) {
+                       float2* u, int planes, int lam_period, cudaStream_t st) {
   const size_t sm = sizeof(float2) * (N + 2 * PadLen<N>::value);
   cudaError_t e = cudaFuncSetAttribute(k_adj_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_adj_rows<N><<<dim3(N, planes), Plan<N>::NT, sm, st>>>(t1, lam, nk, crop, g, tw, u);
+  k_adj_rows<N><<<dim3(N, planes), Plan<N>::NT, sm, st>>>(t1, lam, nk, crop, g, tw, u, lam_period);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t adj_cols_n(const float2* u, const float2* phi, const float* lam, int crop, const float2* tw, float2* sk,
-                       int planes, cudaStream_t st) {
+                       int planes, int period, cudaStream_t st) {
   constexpr int W = AdjW<N>::W;
   const size_t sm = sizeof(float2) * (N + W * ColLD<N>::value);
   cudaError_t e = smem_attrs(k_adj_cols<N>, sm);
   if (e != cudaSuccess) return e;
-  k_adj_cols<N><<<dim3(crop / W, planes), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, sk);
+  k_adj_cols<N><<<dim3(crop / W, planes), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, sk, period);
   return cudaGetLastError();
 }
 
 template <int N>
 cudaError_t grad_rows_n(const float2* qf, int crop, float scale, const float* m, float alpha, const float2* tw,
-                        float* grad, cudaStream_t st) {
+                        float* grad, int clips, cudaStream_t st) {
   const size_t sm = sizeof(float2) * (N + PadLen<N>::value);
   cudaError_t e = cudaFuncSetAttribute(k_grad_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_grad_rows<N><<<N, Plan<N>::NT, sm, st>>>(qf, crop, scale, m, alpha, tw, grad);
+  k_grad_rows<N><<<dim3(N, clips), Plan<N>::NT, sm, st>>>(qf, crop, scale, m, alpha, tw, grad);
   return cudaGetLastError();
 }
 
@@ -255,20 +276,20 @@ cudaError_t grad_rows_n(const float2* qf, int crop, float scale, const float* m,
   }
 
 cudaError_t launch_adj_rows(int n, const float2* t1, const float* lam, int nk, int crop, const float* g,
-                            const float2* tw, float2* u, int planes, cudaStream_t st) {
-#define CALL(N) adj_rows_n<N>(t1, lam, nk, crop, g, tw, u, planes, st)
+                            const float2* tw, float2* u, int planes, int lam_period, cudaStream_t st) {
+#define CALL(N) adj_rows_n<N>(t1, lam, nk, crop, g, tw, u, planes, lam_period, st)
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
 cudaError_t launch_adj_cols(int n, const float2* u, const float2* phi, const float* lam, int crop, const float2* tw,
-                            float2* sk, int planes, cudaStream_t st) {
-#define CALL(N) adj_cols_n<N>(u, phi, lam, crop, tw, sk, planes, st)
+                            float2* sk, int planes, int period, cudaStream_t st) {
+#define CALL(N) adj_cols_n<N>(u, phi, lam, crop, tw, sk, planes, period, st)
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
 cudaError_t launch_grad_rows(int n, const float2* qf, int crop, float scale, const float* m, float alpha,
-                             const float2* tw, float* grad, cudaStream_t st) {
-#define CALL(N) grad_rows_n<N>(qf, crop, scale, m, alpha, tw, grad, st)
+                             const float2* tw, float* grad, int clips, cudaStream_t st) {
+#define CALL(N) grad_rows_n<N>(qf, crop, scale, m, alpha, tw, grad, clips, st)
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
@@ -288,9 +309,20 @@ struct IltLayout {
   size_t bytes;
 };
 
-// Carves the workspace for P focus planes per group (P = n_focus or 1).
-IltLayout ilt_layout(const litho_kernels* h, int b, int P, void* base) {
-  const size_t N = h->n, C = h->crop, K = h->k;
+// Clips per group: the group's stage-1 fields at the full grid within 2 GiB,
+// and groups of equal size.
+int ilt_group(const litho_kernels* h, int b) {
+  const size_t per_clip = size_t(h->n_focus) * h->k * h->n * h->crop * sizeof(float2);
+  const size_t cap = std::max<size_t>(1, std::min<size_t>(size_t(b), (size_t(2) << 30) / per_clip));
+  const size_t groups = (size_t(b) + cap - 1) / cap;
+  return int((size_t(b) + groups - 1) / groups);
+}
+
+// Carves the workspace for groups of G clips and P focus planes at a time
+// (P = all planes with G = ilt_group, or P = 1 with G = 1).  The b FP64
+// losses come first, so their address does not depend on P or G.
+IltLayout ilt_layout(const litho_kernels* h, int b, int P, int G, void* base) {
+  const size_t N = h->n, C = h->crop, K = h->k, g = size_t(G), PG = size_t(P) * G;
   IltLayout L{};
   size_t off = 0;
   char* p = static_cast<char*>(base);
@@ -299,34 +331,49 @@ IltLayout ilt_layout(const litho_kernels* h, int b, int P, void* base) {
     off += up256(bytes);
     return r;
   };
-  L.m = reinterpret_cast<float*>(take(N * N * 4));
-  L.rowbuf = reinterpret_cast<float2*>(take(N * C * 8));
-  L.mhat = reinterpret_cast<float2*>(take(C * C * 8));
-  L.t1 = reinterpret_cast<float2*>(take(P * K * N * C * 8));
-  L.u = reinterpret_cast<float2*>(take(P * K * N * C * 8));
-  L.sk = reinterpret_cast<float2*>(take(P * K * C * C * 8));
-  L.s = reinterpret_cast<float2*>(take(C * C * 8));
-  L.qf = reinterpret_cast<float2*>(take(N * C * 8));
-  L.img = reinterpret_cast<float*>(take(P * N * N * 4));
-  L.blur = reinterpret_cast<float*>(take(P * N * N * 4));
-  L.partial = reinterpret_cast<double*>(take(kPartials * 8));
   L.loss = reinterpret_cast<double*>(take(size_t(b) * 8));
+  L.m = reinterpret_cast<float*>(take(g * N * N * 4));
+  L.rowbuf = reinterpret_cast<float2*>(take(g * N * C * 8));
+  L.mhat = reinterpret_cast<float2*>(take(g * C * C * 8));
+  L.t1 = reinterpret_cast<float2*>(take(PG * K * N * C * 8));
+  L.u = reinterpret_cast<float2*>(take(PG * K * N * C * 8));
+  L.sk = reinterpret_cast<float2*>(take(PG * K * C * C * 8));
+  L.s = reinterpret_cast<float2*>(take(g * C * C * 8));
+  L.qf = reinterpret_cast<float2*>(take(g * N * C * 8));
+  L.img = reinterpret_cast<float*>(take(PG * N * N * 4));
+  L.blur = reinterpret_cast<float*>(take(PG * N * N * 4));
+  L.partial = reinterpret_cast<double*>(take(g * kPartials * 8));
   const size_t NC = h->nc, C2 = 2 * C;
   if (NC > 0) {
-    L.ic = reinterpret_cast<float*>(take(P * NC * NC * 4));
-    L.mid = reinterpret_cast<float2*>(take(P * NC * C2 * 8));
-    L.big = reinterpret_cast<float2*>(take(P * N * C2 * 8));
-    L.spec = reinterpret_cast<float2*>(take(P * C2 * C2 * 8));
+    L.ic = reinterpret_cast<float*>(take(PG * NC * NC * 4));
+    L.mid = reinterpret_cast<float2*>(take(PG * NC * C2 * 8));
+    L.big = reinterpret_cast<float2*>(take(PG * N * C2 * 8));
+    L.spec = reinterpret_cast<float2*>(take(PG * C2 * C2 * 8));
   }
   L.bytes = off;
   return L;
 }
 
+// Planes and clips per pass for a workspace of `bytes` (false: below the minimum).
+bool ilt_plan(const litho_kernels* h, int b, int planes, size_t bytes, int* P, int* G) {
+  const int g = ilt_group(h, b);
+  if (bytes >= ilt_layout(h, b, planes, g, nullptr).bytes) {
+    *P = planes;
+    *G = g;
+    return true;
+  }
+  *P = 1;  // one focus plane of one clip at a time: its stage-1 fields are rebuilt per plane
+  *G = 1;
+  return bytes >= ilt_layout(h, b, 1, 1, nullptr).bytes;
+}
+
 }  // namespace
 
 double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes) {
-  const int P = workspace_bytes >= ilt_layout(h, b, h->n_focus, nullptr).bytes ? h->n_focus : 1;
-  return ilt_layout(h, b, P, workspace).loss;
+  (void)h;
+  (void)b;
+  (void)workspace_bytes;
+  return static_cast<double*>(workspace);  // the losses lead every layout
 }
 
 }  // namespace litho
@@ -340,8 +387,8 @@ litho_status litho_ilt_workspace_size(const litho_kernels* h, int b, size_t* ful
     set_error("null handle or b < 1");
     return LITHO_EINVAL;
   }
-  if (full_bytes) *full_bytes = ilt_layout(h, b, h->n_focus, nullptr).bytes;
-  if (min_bytes) *min_bytes = ilt_layout(h, b, 1, nullptr).bytes;
+  if (full_bytes) *full_bytes = ilt_layout(h, b, h->n_focus, ilt_group(h, b), nullptr).bytes;
+  if (min_bytes) *min_bytes = ilt_layout(h, b, 1, 1, nullptr).bytes;
   return LITHO_OK;
 }
 
@@ -377,17 +424,13 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
     return LITHO_EINVAL;
   }
   const int F = h->n_focus, K = h->k, N = h->n, C = h->crop;
-  const size_t full = ilt_layout(h, b, F, nullptr).bytes, mn = ilt_layout(h, b, 1, nullptr).bytes;
-  int P;
-  if (workspace_bytes >= full) {
-    P = F;
-  } else if (workspace_bytes >= mn) {
-    P = 1;  // one focus plane at a time: its stage-1 fields are rebuilt per plane
-  } else {
-    set_error("workspace too small: %zu bytes given, at least %zu needed", workspace_bytes, mn);
+  int P, G;
+  if (!ilt_plan(h, b, F, workspace_bytes, &P, &G)) {
+    set_error("workspace too small: %zu bytes given, at least %zu needed", workspace_bytes,
+              ilt_layout(h, b, 1, 1, nullptr).bytes);
     return LITHO_ENOMEM;
   }
-  IltLayout L = ilt_layout(h, b, P, workspace_dev);
+  IltLayout L = ilt_layout(h, b, P, G, workspace_dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nn = size_t(N) * N;
   const float scale = float(2.0 * dose / (double(N) * double(N)));
@@ -402,52 +445,56 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
   const int NE = coarse ? h->nc : N, C2 = 2 * C;
   const float2* twe = coarse ? h->d_twc : h->d_tw;
   const float lp_scale = float((double(N) / NE) * (double(N) / NE));
-  for (int clip = 0; clip < b; ++clip) {
+  // Groups of g clips: every launch covers the group's g x P planes (plane
+  // i P + p is focus plane f0 + p of clip c0 + i; its fields follow the
+  // plane's K kernels).
+  for (int c0 = 0; c0 < b; c0 += G) {
+    const int g = std::min(G, b - c0), gp = g * P;
     {
       ProfScope ps(kStageIltForward, st, 3);
-      k_sigmoid<<<256, 256, 0, st>>>(theta_dev + clip * nn, float(mask_steep), L.m, nn);
+      k_sigmoid<<<256, 256, 0, st>>>(theta_dev + c0 * nn, float(mask_steep), L.m, size_t(g) * nn);
       LITHO_TRY_CUDA(cudaGetLastError());
-      LITHO_TRY_CUDA(launch_mask_spectrum(L.m, 1, N, C, h->d_tw, L.rowbuf, L.mhat, st));
+      LITHO_TRY_CUDA(launch_mask_spectrum(L.m, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
     }
     for (int f0 = 0; f0 < F; f0 += P) {
       const float2* phi = h->d_phi + size_t(f0) * K * C * C;
       const float* lam = h->d_lambda + size_t(f0) * K;
       {
         ProfScope ps(kStageIltForward, st, coarse ? 8 : 5);
-        LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, P * K, NE, C, twe, L.t1, st));
-        LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, P,
-                                         (long long)K * NE * C, (long long)NE * NE, st));
+        LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, P * K, NE, C, twe, L.t1, st, g));
+        LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, gp,
+                                         (long long)K * NE * C, (long long)NE * NE, st, P));
         if (coarse) {
-          LITHO_TRY_CUDA(launch_mask_rows(L.ic, P, NE, C2, twe, L.mid, st));
-          LITHO_TRY_CUDA(launch_interp_cols(L.mid, P, NE, N, C2, twe, h->d_tw, nullptr, L.big, st));
-          LITHO_TRY_CUDA(launch_band_rows_real(L.big, P, N, C2, 1.0f, h->d_tw, L.img, st));
+          LITHO_TRY_CUDA(launch_mask_rows(L.ic, gp, NE, C2, twe, L.mid, st));
+          LITHO_TRY_CUDA(launch_interp_cols(L.mid, gp, NE, N, C2, twe, h->d_tw, nullptr, L.big, st));
+          LITHO_TRY_CUDA(launch_band_rows_real(L.big, gp, N, C2, 1.0f, h->d_tw, L.img, st));
         }
-        LITHO_TRY_CUDA(launch_resist(L.img, P, N, taps, float(threshold), L.blur, nullptr, st));
-        k_resist_grad<<<kPartials, 256, 0, st>>>(L.blur, target_dev + clip * nn, nn, P, float(resist_steep),
-                                                 float(threshold), L.img, L.partial);
+        LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
+        k_resist_grad<<<dim3(kPartials, g), 256, 0, st>>>(L.blur, target_dev + c0 * nn, nn, P, float(resist_steep),
+                                                         float(threshold), L.img, L.partial);
         LITHO_TRY_CUDA(cudaGetLastError());
-        k_reduce_loss<<<1, 1024, 0, st>>>(L.partial, kPartials, L.loss + clip, f0 > 0 ? 1 : 0);
+        k_reduce_loss<<<g, 1024, 0, st>>>(L.partial, kPartials, L.loss + c0, f0 > 0 ? 1 : 0);
         LITHO_TRY_CUDA(cudaGetLastError());
       }
       {
         ProfScope ps(kStageIltBackward, st, coarse ? 7 : 4);
-        LITHO_TRY_CUDA(launch_resist(L.img, P, N, taps, float(threshold), L.blur, nullptr, st));
+        LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
         const float* gsrc = L.blur;
         if (coarse) {
-          LITHO_TRY_CUDA(launch_mask_spectrum(L.blur, P, N, C2, h->d_tw, L.big, L.spec, st));
-          LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, P, NE, C2, twe, L.mid, st));
-          LITHO_TRY_CUDA(launch_band_rows_real(L.mid, P, NE, C2, lp_scale, twe, L.ic, st));
+          LITHO_TRY_CUDA(launch_mask_spectrum(L.blur, gp, N, C2, h->d_tw, L.big, L.spec, st));
+          LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, gp, NE, C2, twe, L.mid, st));
+          LITHO_TRY_CUDA(launch_band_rows_real(L.mid, gp, NE, C2, lp_scale, twe, L.ic, st));
           gsrc = L.ic;
         }
-        LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, gsrc, twe, L.u, P, st));
-        LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, P * K, st));
-        k_sum_planes<<<256, 256, 0, st>>>(L.sk, P * K, size_t(C) * C, L.s, f0 > 0 ? 1 : 0);
+        LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, gsrc, twe, L.u, gp, P, st));
+        LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, gp * K, P * K, st));
+        k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, P * K, size_t(C) * C, L.s, f0 > 0 ? 1 : 0);
         LITHO_TRY_CUDA(cudaGetLastError());
       }
     }
     ProfScope ps(kStageIltBackward, st, 2);
-    LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, 1, N, C, h->d_tw, L.qf, st));
-    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, L.m, float(mask_steep), h->d_tw, grad_dev + clip * nn, st));
+    LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
+    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, L.m, float(mask_steep), h->d_tw, grad_dev + c0 * nn, g, st));
   }
   if (loss_host) {
     LITHO_TRY_CUDA(cudaMemcpyAsync(loss_host, L.loss, size_t(b) * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -476,39 +523,39 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
     return LITHO_EINVAL;
   }
   const int F = h->n_focus, K = h->k, N = h->n, C = h->crop;
-  const size_t full = ilt_layout(h, b, f_count, nullptr).bytes, mn = ilt_layout(h, b, 1, nullptr).bytes;
-  int P;
-  if (workspace_bytes >= full) {
-    P = f_count;
-  } else if (workspace_bytes >= mn) {
-    P = 1;
-  } else {
-    set_error("workspace too small: %zu bytes given, at least %zu needed", workspace_bytes, mn);
+  int P, G;
+  if (!ilt_plan(h, b, f_count, workspace_bytes, &P, &G)) {
+    set_error("workspace too small: %zu bytes given, at least %zu needed", workspace_bytes,
+              ilt_layout(h, b, 1, 1, nullptr).bytes);
     return LITHO_ENOMEM;
   }
-  IltLayout L = ilt_layout(h, b, P, workspace_dev);
+  // clips are grouped when their upstream planes follow one another: all
+  // focus planes of each clip, or no upstream (ones)
+  if (upstream_dev && !(P == F && f_first == 0)) G = 1;
+  IltLayout L = ilt_layout(h, b, P, G, workspace_dev);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nn = size_t(N) * N;
   const float scale = float(2.0 * dose / (double(N) * double(N)));
   ProfScope ps(kStageIltBackward, st, 1);
   if (!upstream_dev) {  // dL/dI = 1 on every pixel of the selected planes
-    k_fill<<<256, 256, 0, st>>>(L.img, 1.0f, size_t(P) * nn);
+    k_fill<<<256, 256, 0, st>>>(L.img, 1.0f, size_t(G) * P * nn);
     LITHO_TRY_CUDA(cudaGetLastError());
   }
-  for (int clip = 0; clip < b; ++clip) {
-    LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev + clip * nn, 1, N, C, h->d_tw, L.rowbuf, L.mhat, st));
+  for (int c0 = 0; c0 < b; c0 += G) {
+    const int g = std::min(G, b - c0);
+    LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev + c0 * nn, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
     for (int f0 = f_first; f0 < f_first + f_count; f0 += P) {
       const int p = std::min(P, f_first + f_count - f0);
-      const float* g = upstream_dev ? upstream_dev + (size_t(clip) * F + f0) * nn : L.img;
-      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, p * K, N, C, h->d_tw, L.t1, st));
-      LITHO_TRY_CUDA(launch_adj_rows(N, L.t1, h->d_lambda + size_t(f0) * K, K, C, g, h->d_tw, L.u, p, st));
+      const float* up = upstream_dev ? upstream_dev + (size_t(c0) * F + f0) * nn : L.img;
+      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, p * K, N, C, h->d_tw, L.t1, st, g));
+      LITHO_TRY_CUDA(launch_adj_rows(N, L.t1, h->d_lambda + size_t(f0) * K, K, C, up, h->d_tw, L.u, g * p, p, st));
       LITHO_TRY_CUDA(launch_adj_cols(N, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
-                                     h->d_tw, L.sk, p * K, st));
-      k_sum_planes<<<256, 256, 0, st>>>(L.sk, p * K, size_t(C) * C, L.s, f0 > f_first ? 1 : 0);
+                                     h->d_tw, L.sk, g * p * K, p * K, st));
+      k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, p * K, size_t(C) * C, L.s, f0 > f_first ? 1 : 0);
       LITHO_TRY_CUDA(cudaGetLastError());
     }
-    LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, 1, N, C, h->d_tw, L.qf, st));
-    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, dm_dev + clip * nn, st));
+    LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
+    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, dm_dev + c0 * nn, g, st));
   }
   return LITHO_OK;
 }

@@ -80,6 +80,24 @@ def test_ilt_recompute_mode_equals_full_mode(litho_lib, cuda, precision):
     assert e.value.status == litho_lib.ENOMEM
 
 
+@pytest.mark.parametrize("precision", ["fft32", "fft32/coarse"])
+def test_ilt_clip_groups_equal_clips_alone(litho_lib, cuda, precision):
+    """One call images its clips in groups (a launch covers every clip of a
+    group); each clip's gradient is bit-identical and its FP64 loss equal to
+    the same clip run alone."""
+    n, pixel, b = 128, 8.0, 3
+    lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, [-40.0, 0.0, 40.0], 6)
+    kern = litho_lib.litho_upload_kernels(n, pixel, lam, phi)
+    clips = [synth.ilt_clip(n, pixel, seed=800 + i) for i in range(b)]
+    thetas = np.stack([c[0] for c in clips])
+    targets = np.stack([c[1] for c in clips])
+    g_all, l_all = _gpu(litho_lib, cuda, kern, thetas, targets, precision=precision)
+    for i in range(b):
+        g_i, l_i = _gpu(litho_lib, cuda, kern, thetas[i:i + 1], targets[i:i + 1], precision=precision)
+        assert np.array_equal(g_all[i], g_i[0])
+        assert l_all[i] == l_i[0]
+
+
 def test_ilt_coarse_grid_equals_full_grid(litho_lib, cuda):
     """The coarse-grid adjoint is exact (no product frequency aliases into the
     field band on nc >= 2C), so it agrees with the full-grid gradient to FP32
