@@ -646,10 +646,13 @@ def run_ai(args):
     targets = torch.from_numpy(np.stack([synth.manhattan_mask(N, seed=s) for s in clip_seeds(ctx.rank, clips)])).to(
         ctx.dev)
     stream = torch.cuda.current_stream()
+    prec = args.precision if args.precision in ("fft32", "fft32/coarse") else "fft32/coarse"
+    ws = torch.empty(L.litho_ai_inputs_workspace_size(kern, clips), dtype=torch.uint8, device=ctx.dev)
+    xbuf = torch.empty((clips, 3, N, N), dtype=torch.float32, device=ctx.dev)
     out = {}
 
     def step():
-        x = P.litho_ai_inputs(kern, targets, focus=0, stream=stream)
+        x = P.litho_ai_inputs(kern, targets, focus=0, precision=prec, out=xbuf, workspace=ws, stream=stream)
         out["x"] = x
         out["p"] = P.litho_print_images(targets, x[:, 1].contiguous(), PIXEL, 20.0, 0.5, 0.3, stream=stream)
 
@@ -667,7 +670,8 @@ def run_ai(args):
             "value": whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
             "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
             "higher_is_better": True, "scaling": "weak", "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"ai inputs {clips}x2048^2 quadrupole41 K=24 nominal focus", "clips_per_gpu": clips},
+            "config": {"workload": f"ai inputs {clips}x2048^2 quadrupole41 K=24 nominal focus", "clips_per_gpu": clips,
+                       "precision": prec},
             "litho_loss_first_clips": [int(v) for v in out["p"][2][:4].cpu().tolist()],
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}

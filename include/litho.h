@@ -260,11 +260,17 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
  * the aerial image of the target at plane `focus`, x[c][2] = (g - min g) /
  * (max g - min g) with g the gradient of that plane's total intensity with
  * respect to the mask (litho_intensity_vjp of ones), the extremes taken over
- * the batch (a constant channel becomes 0).  x is f32 [b][3][n][n].  Workspace:
- * litho_ai_inputs_workspace_size bytes, 256-byte aligned.  Async. */
-litho_status litho_ai_inputs_workspace_size(const litho_kernels* h, size_t* bytes);
+ * the batch (a constant channel becomes 0).  x is f32 [b][3][n][n], 1 <= b <=
+ * 65535.  Workspace: litho_ai_inputs_workspace_size(h, b) bytes, 256-byte
+ * aligned.  prec:
+ * LITHO_PREC_FFT32 (else EUNSUPPORTED), optionally | LITHO_GRID_COARSE (fields
+ * and adjoint on the coarse grid, the image interpolated exactly: the same
+ * channels up to FP32 rounding).  Both channels come from one evaluation of
+ * the stage-1 fields per group of clips.  Async. */
+litho_status litho_ai_inputs_workspace_size(const litho_kernels* h, int b, size_t* bytes);
 litho_status litho_ai_inputs(const litho_kernels* h, const float* target_dev, int b, double dose, int focus,
-                             float* x_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
+                             litho_precision prec, float* x_dev, void* workspace_dev, size_t workspace_bytes,
+                             void* stream);
 
 /* Eqs. (15)-(17): z_round = [G (x) Z_t >= tau_round] with G the periodic,
  * normalised Gaussian of sigma_round_nm truncated at 4 sigma (as

@@ -4,8 +4,9 @@
 // Eq. (9), as read here: X[c] = (Z_t, I0 / max I0, (dI/dM - min) / (max - min))
 // with I0 the aerial image of the target at one focus plane, dI/dM the
 // gradient of the plane's total intensity with respect to the mask pixels
-// (the adjoint of Eq. (4) applied to ones, litho_intensity_vjp) and the
-// extremes taken over the whole batch (a constant channel maps to 0).
+// (the adjoint of Eq. (4) applied to ones, as litho_intensity_vjp computes
+// it; both channels come from one set of stage-1 fields, see ai_channels)
+// and the extremes taken over the whole batch (a constant channel maps to 0).
 // Eqs. (15)-(17): Z_round = [G (x) Z_t >= tau_round] with the resist's
 // periodic Gaussian, Z_print = [I >= tau_print], L_litho = sum |Z_print -
 // Z_round| per clip (an integer count, reduced in a fixed order).
@@ -22,16 +23,27 @@ namespace {
 
 constexpr int kReduceBlocks = 304, kReduceThreads = 256;
 
-// Per-block minimum and maximum of channel `ch` of X[b][3][nn].
+// Per-block minimum and maximum of channel `ch` of X[b][3][nn]: block
+// (x, clip) scans its share of the clip's channel (16-byte loads when nn is a
+// multiple of 4); partials [b][gridDim.x].
 __global__ void __launch_bounds__(kReduceThreads) k_minmax(const float* __restrict__ x, int b, size_t nn, int ch,
                                                            float2* __restrict__ part) {
   __shared__ float smin[kReduceThreads], smax[kReduceThreads];
   float lo = FLT_MAX, hi = -FLT_MAX;
-  const size_t total = size_t(b) * nn;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const float v = x[(i / nn) * 3 * nn + size_t(ch) * nn + i % nn];
-    lo = fminf(lo, v);
-    hi = fmaxf(hi, v);
+  const float* src = x + (size_t(blockIdx.y) * 3 + ch) * nn;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  if (nn % 4 == 0) {
+    const float4* s4 = reinterpret_cast<const float4*>(src);
+    for (size_t i = t0; i < nn / 4; i += stride) {
+      const float4 v = s4[i];
+      lo = fminf(lo, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
+      hi = fmaxf(hi, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+    }
+  } else {
+    for (size_t i = t0; i < nn; i += stride) {
+      lo = fminf(lo, src[i]);
+      hi = fmaxf(hi, src[i]);
+    }
   }
   smin[threadIdx.x] = lo;
   smax[threadIdx.x] = hi;
@@ -43,31 +55,47 @@ __global__ void __launch_bounds__(kReduceThreads) k_minmax(const float* __restri
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) part[blockIdx.x] = make_float2(smin[0], smax[0]);
+  if (threadIdx.x == 0) part[size_t(blockIdx.y) * gridDim.x + blockIdx.x] = make_float2(smin[0], smax[0]);
 }
 
-// Channel ch of every clip: v -> (v - lo) * s, with lo and s from the block
-// partials (mode 0: lo = 0, s = 1/max; mode 1: lo = min, s = 1/(max - min);
-// s = 0 when the range is empty).
+// Channel ch of every clip: v -> (v - lo) * s, with lo and s from the
+// `nparts` block partials (mode 0: lo = 0, s = 1/max; mode 1: lo = min,
+// s = 1/(max - min); s = 0 when the range is empty).  Block (x, clip).
 __global__ void k_normalize(float* __restrict__ x, int b, size_t nn, int ch, const float2* __restrict__ part,
                             int nparts, int mode) {
-  __shared__ float lo_s, s_s;
-  if (threadIdx.x == 0) {
-    float lo = FLT_MAX, hi = -FLT_MAX;
-    for (int k = 0; k < nparts; ++k) {
-      lo = fminf(lo, part[k].x);
-      hi = fmaxf(hi, part[k].y);
-    }
-    if (mode == 0) lo = 0.f;
-    lo_s = lo;
-    s_s = hi > lo ? 1.0f / (hi - lo) : 0.f;
+  __shared__ float smin[kReduceThreads], smax[kReduceThreads];
+  float lo = FLT_MAX, hi = -FLT_MAX;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+    lo = fminf(lo, part[k].x);
+    hi = fmaxf(hi, part[k].y);
   }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
   __syncthreads();
-  const float lo = lo_s, s = s_s;
-  const size_t total = size_t(b) * nn;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    float* p = x + (i / nn) * 3 * nn + size_t(ch) * nn + i % nn;
-    *p = (*p - lo) * s;
+  for (int o = kReduceThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smin[threadIdx.x] = fminf(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmaxf(smax[threadIdx.x], smax[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  lo = mode == 0 ? 0.f : smin[0];
+  hi = smax[0];
+  const float s = hi > lo ? 1.0f / (hi - lo) : 0.f;
+  float* dst = x + (size_t(blockIdx.y) * 3 + ch) * nn;
+  const size_t t0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, stride = (size_t)gridDim.x * blockDim.x;
+  if (nn % 4 == 0) {
+    float4* d4 = reinterpret_cast<float4*>(dst);
+    for (size_t i = t0; i < nn / 4; i += stride) {
+      float4 v = d4[i];
+      v.x = (v.x - lo) * s;
+      v.y = (v.y - lo) * s;
+      v.z = (v.z - lo) * s;
+      v.w = (v.w - lo) * s;
+      d4[i] = v;
+    }
+  } else {
+    for (size_t i = t0; i < nn; i += stride) dst[i] = (dst[i] - lo) * s;
   }
 }
 
@@ -107,12 +135,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_l1_count(const uint4* __rest
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Forward scratch of one clip at one plane: row spectrum, crop spectrum, stage-1 fields.
-size_t ai_forward_bytes(const litho_kernels* h) {
-  const size_t N = h->n, C = h->crop, K = h->k;
-  return up256(N * C * 8) + up256(C * C * 8) + up256(K * N * C * 8);
-}
-
 }  // namespace
 
 }  // namespace litho
@@ -121,64 +143,53 @@ using namespace litho;
 
 extern "C" {
 
-litho_status litho_ai_inputs_workspace_size(const litho_kernels* h, size_t* bytes) {
-  if (!h || !bytes) {
-    set_error("null argument");
+litho_status litho_ai_inputs_workspace_size(const litho_kernels* h, int b, size_t* bytes) {
+  if (!h || !bytes || b < 1) {
+    set_error("null argument or b < 1");
     return LITHO_EINVAL;
   }
-  size_t vjp_min = 0;
-  litho_status s = litho_intensity_vjp_workspace_size(h, 1, nullptr, &vjp_min);
-  if (s != LITHO_OK) return s;
-  *bytes = std::max(ai_forward_bytes(h), vjp_min) + up256(kReduceBlocks * sizeof(float2));
+  *bytes = up256(ai_channels_bytes(h, b)) + up256(size_t(std::max(kReduceBlocks, b)) * sizeof(float2));
   return LITHO_OK;
 }
 
 litho_status litho_ai_inputs(const litho_kernels* h, const float* target_dev, int b, double dose, int focus,
-                             float* x_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
-  if (!h || !target_dev || !x_dev || !workspace_dev || b < 1) {
-    set_error("null argument or b < 1");
+                             litho_precision prec, float* x_dev, void* workspace_dev, size_t workspace_bytes,
+                             void* stream) {
+  if (!h || !target_dev || !x_dev || !workspace_dev || b < 1 || b > 65535) {
+    set_error("null argument or b outside [1, 65535]");
     return LITHO_EINVAL;
   }
   if (focus < 0 || focus >= h->n_focus || !std::isfinite(dose)) {
     set_error("focus must index a plane of the kernel set; dose finite");
     return LITHO_EINVAL;
   }
+  if ((int(prec) & ~LITHO_GRID_COARSE) != LITHO_PREC_FFT32) {
+    set_error("litho_ai_inputs implements the FP32 FFT path only (LITHO_PREC_FFT32, optionally | LITHO_GRID_COARSE)");
+    return LITHO_EUNSUPPORTED;
+  }
   size_t need = 0;
-  litho_status s = litho_ai_inputs_workspace_size(h, &need);
+  litho_status s = litho_ai_inputs_workspace_size(h, b, &need);
   if (s != LITHO_OK) return s;
   if (workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace_dev) & 255) != 0) {
     set_error("workspace must be 256-byte aligned and hold %zu bytes (%zu given)", need, workspace_bytes);
     return workspace_bytes < need ? LITHO_ENOMEM : LITHO_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int N = h->n, C = h->crop, K = h->k;
-  const size_t nn = size_t(N) * N;
-  char* w = static_cast<char*>(workspace_dev);
-  float2* part = reinterpret_cast<float2*>(w + (need - up256(kReduceBlocks * sizeof(float2))));
-  float2* rowbuf = reinterpret_cast<float2*>(w);
-  float2* mhat = reinterpret_cast<float2*>(w + up256(size_t(N) * C * 8));
-  float2* t1 = reinterpret_cast<float2*>(w + up256(size_t(N) * C * 8) + up256(size_t(C) * C * 8));
+  const size_t nn = size_t(h->n) * h->n;
+  float2* part = reinterpret_cast<float2*>(static_cast<char*>(workspace_dev) + up256(ai_channels_bytes(h, b)));
   {
-    ProfScope ps(kStageIltForward, st, 1 + 4 * b);
+    ProfScope ps(kStageIltForward, st, 1);
     k_copy_channel<<<512, 256, 0, st>>>(target_dev, x_dev, b, nn, 0);
     LITHO_TRY_CUDA(cudaGetLastError());
-    for (int c = 0; c < b; ++c) {  // channel 1: the aerial image of the target at plane `focus`
-      LITHO_TRY_CUDA(launch_mask_spectrum(target_dev + c * nn, 1, N, C, h->d_tw, rowbuf, mhat, st));
-      LITHO_TRY_CUDA(launch_stage1_fft(mhat, h->d_phi + size_t(focus) * K * C * C, K, N, C, h->d_tw, t1, st));
-      LITHO_TRY_CUDA(launch_stage2_fft(t1, h->d_lambda + size_t(focus) * K, K, N, C, float(dose), h->d_tw,
-                                       x_dev + (size_t(c) * 3 + 1) * nn, 1, (long long)K * N * C, (long long)nn,
-                                       st));
-    }
   }
-  for (int c = 0; c < b; ++c) {  // channel 2: the gradient of the plane's total intensity
-    s = litho_intensity_vjp(h, target_dev + c * nn, 1, dose, focus, 1, nullptr, x_dev + (size_t(c) * 3 + 2) * nn,
-                            workspace_dev, need - up256(kReduceBlocks * sizeof(float2)), stream);
-    if (s != LITHO_OK) return s;
-  }
+  s = ai_channels(h, target_dev, b, dose, focus, (int(prec) & LITHO_GRID_COARSE) != 0, x_dev, workspace_dev, st);
+  if (s != LITHO_OK) return s;
   ProfScope ps(kStageIltReduce, st, 4);
+  const int per_clip = std::max(1, kReduceBlocks / b);  // partials per clip: at most kReduceBlocks in all
   for (int ch = 1; ch <= 2; ++ch) {
-    k_minmax<<<kReduceBlocks, kReduceThreads, 0, st>>>(x_dev, b, nn, ch, part);
-    k_normalize<<<512, 256, 0, st>>>(x_dev, b, nn, ch, part, kReduceBlocks, ch == 1 ? 0 : 1);
+    k_minmax<<<dim3(per_clip, b), kReduceThreads, 0, st>>>(x_dev, b, nn, ch, part);
+    k_normalize<<<dim3(std::max(1, 1216 / b), b), kReduceThreads, 0, st>>>(x_dev, b, nn, ch, part, per_clip * b,
+                                                                          ch == 1 ? 0 : 1);
   }
   LITHO_TRY_CUDA(cudaGetLastError());
   return LITHO_OK;

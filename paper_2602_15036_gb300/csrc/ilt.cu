@@ -179,6 +179,13 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
   }
 }
 
+// x[i][ch] = img[i] for the planes i of a group (x: [.][3][nn]).
+__global__ void k_to_channel(const float* __restrict__ img, float* __restrict__ x, int planes, size_t nn, int ch) {
+  const size_t total = size_t(planes) * nn;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x)
+    x[(i / nn) * 3 * nn + size_t(ch) * nn + i % nn] = img[i];
+}
+
 __global__ void k_fill(float* __restrict__ p, float v, size_t count) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -203,7 +210,8 @@ __global__ void k_sum_planes(const float2* __restrict__ sk, int planes, size_t c
 template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT) k_grad_rows(const float2* __restrict__ qf, int crop, float scale,
                                                            const float* __restrict__ m, float alpha,
-                                                           const float2* __restrict__ tw_g, float* __restrict__ grad) {
+                                                           const float2* __restrict__ tw_g, float* __restrict__ grad,
+                                                           long long grad_stride) {
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_grad_rows(const float2* __restr
   const size_t clip = blockIdx.y;  // clip of the group: its band rows, mask and gradient
   qf += clip * N * crop;
   if (m) m += clip * N * N;
-  grad += clip * N * N;
+  grad += clip * grad_stride;
   const float2* row = qf + (size_t)y * crop;
   auto load = [&](int idx) {
     const int c = freq_of_idx(idx, N) + half;
@@ -255,11 +263,11 @@ cudaError_t adj_cols_n(const float2* u, const float2* phi, const float* lam, int
 
 template <int N>
 cudaError_t grad_rows_n(const float2* qf, int crop, float scale, const float* m, float alpha, const float2* tw,
-                        float* grad, int clips, cudaStream_t st) {
+                        float* grad, int clips, long long grad_stride, cudaStream_t st) {
   const size_t sm = sizeof(float2) * (N + PadLen<N>::value);
   cudaError_t e = cudaFuncSetAttribute(k_grad_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_grad_rows<N><<<dim3(N, clips), Plan<N>::NT, sm, st>>>(qf, crop, scale, m, alpha, tw, grad);
+  k_grad_rows<N><<<dim3(N, clips), Plan<N>::NT, sm, st>>>(qf, crop, scale, m, alpha, tw, grad, grad_stride);
   return cudaGetLastError();
 }
 
@@ -287,9 +295,10 @@ cudaError_t launch_adj_cols(int n, const float2* u, const float2* phi, const flo
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
+// Clip i of `clips` writes grad + i grad_stride.
 cudaError_t launch_grad_rows(int n, const float2* qf, int crop, float scale, const float* m, float alpha,
-                             const float2* tw, float* grad, int clips, cudaStream_t st) {
-#define CALL(N) grad_rows_n<N>(qf, crop, scale, m, alpha, tw, grad, clips, st)
+                             const float2* tw, float* grad, int clips, long long grad_stride, cudaStream_t st) {
+#define CALL(N) grad_rows_n<N>(qf, crop, scale, m, alpha, tw, grad, clips, grad_stride, st)
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
@@ -374,6 +383,53 @@ double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t w
   (void)b;
   (void)workspace_bytes;
   return static_cast<double*>(workspace);  // the losses lead every layout
+}
+
+size_t ai_channels_bytes(const litho_kernels* h, int b) { return ilt_layout(h, b, 1, ilt_group(h, b), nullptr).bytes; }
+
+litho_status ai_channels(const litho_kernels* h, const float* target, int b, double dose, int focus, bool coarse,
+                         float* x, void* workspace, cudaStream_t st) {
+  const int G = ilt_group(h, b), K = h->k, N = h->n, C = h->crop;
+  IltLayout L = ilt_layout(h, b, 1, G, workspace);
+  const size_t nn = size_t(N) * N;
+  coarse = coarse && h->nc > 0 && interp_cols_supported(h->nc, N);
+  const int NE = coarse ? h->nc : N, C2 = 2 * C;
+  const float2* twe = coarse ? h->d_twc : h->d_tw;
+  const float2* phi = h->d_phi + size_t(focus) * K * C * C;
+  const float* lam = h->d_lambda + size_t(focus) * K;
+  const float scale = float(2.0 * dose / (double(N) * double(N)));
+  for (int c0 = 0; c0 < b; c0 += G) {
+    const int g = std::min(G, b - c0);
+    {  // channel 1: the aerial image of the targets (interpolated from the coarse grid)
+      ProfScope ps(kStageIltForward, st, coarse ? 7 : 4);
+      LITHO_TRY_CUDA(launch_mask_spectrum(target + c0 * nn, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
+      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, K, NE, C, twe, L.t1, st, g));
+      LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, g,
+                                       (long long)K * NE * C, (long long)NE * NE, st, 1));
+      if (coarse) {
+        LITHO_TRY_CUDA(launch_mask_rows(L.ic, g, NE, C2, twe, L.mid, st));
+        LITHO_TRY_CUDA(launch_interp_cols(L.mid, g, NE, N, C2, twe, h->d_tw, nullptr, L.big, st));
+        LITHO_TRY_CUDA(launch_band_rows_real(L.big, g, N, C2, 1.0f, h->d_tw, L.img, st));
+      }
+      k_to_channel<<<512, 256, 0, st>>>(L.img, x + size_t(c0) * 3 * nn, g, nn, 1);
+      LITHO_TRY_CUDA(cudaGetLastError());
+    }
+    {  // channel 2: the adjoint of the same fields applied to dL/dI = 1; on the
+       // coarse grid the low-passed ones are the constant (N/nc)^2 (only the DC term)
+      ProfScope ps(kStageIltBackward, st, 6);
+      float* ones = coarse ? L.ic : L.img;
+      k_fill<<<256, 256, 0, st>>>(ones, float((double(N) / NE) * (double(N) / NE)), size_t(g) * NE * NE);
+      LITHO_TRY_CUDA(cudaGetLastError());
+      LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, ones, twe, L.u, g, 1, st));
+      LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, g * K, K, st));
+      k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, K, size_t(C) * C, L.s, 0);
+      LITHO_TRY_CUDA(cudaGetLastError());
+      LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
+      LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, x + (size_t(c0) * 3 + 2) * nn, g,
+                                      (long long)3 * nn, st));
+    }
+  }
+  return LITHO_OK;
 }
 
 }  // namespace litho
@@ -494,7 +550,8 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
     }
     ProfScope ps(kStageIltBackward, st, 2);
     LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
-    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, L.m, float(mask_steep), h->d_tw, grad_dev + c0 * nn, g, st));
+    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, L.m, float(mask_steep), h->d_tw, grad_dev + c0 * nn, g,
+                                    (long long)nn, st));
   }
   if (loss_host) {
     LITHO_TRY_CUDA(cudaMemcpyAsync(loss_host, L.loss, size_t(b) * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -555,7 +612,8 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
       LITHO_TRY_CUDA(cudaGetLastError());
     }
     LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
-    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, dm_dev + c0 * nn, g, st));
+    LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, dm_dev + c0 * nn, g, (long long)nn,
+                                    st));
   }
   return LITHO_OK;
 }

@@ -150,6 +150,15 @@ cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n,
 // Device address of the per-clip FP64 losses inside an ILT workspace (ilt.cu).
 double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes);
 
+// Channels 1 and 2 of Eq. (9) before normalisation (ilt.cu): for b targets
+// at focus plane `focus`, x[c][1] = the aerial image and x[c][2] = the
+// gradient of the plane's total intensity with respect to the mask pixels
+// (x: [b][3][n][n]), in groups of clips; `coarse` evaluates the fields and
+// the adjoint on the coarse grid.  Workspace: ai_channels_bytes(h, b).
+size_t ai_channels_bytes(const litho_kernels* h, int b);
+litho_status ai_channels(const litho_kernels* h, const float* target, int b, double dose, int focus, bool coarse,
+                         float* x, void* workspace, cudaStream_t st);
+
 // out[p][y][x] = scale Re(sum_c q[p][y][c] e^{+2 pi i u_c x/N}) for band rows q[p][N][C].
 cudaError_t launch_band_rows_real(const float2* q, int planes, int n, int crop, float scale, const float2* tw,
                                   float* out, cudaStream_t st);

@@ -89,8 +89,9 @@ _SIGS = {
     "litho_intensity_vjp_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
     "litho_intensity_vjp": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p, c_void_p, c_void_p,
                                     c_size_t, c_void_p]),
-    "litho_ai_inputs_workspace_size": (c_int, [c_void_p, POINTER(c_size_t)]),
-    "litho_ai_inputs": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_size_t, c_void_p]),
+    "litho_ai_inputs_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t)]),
+    "litho_ai_inputs": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p, c_void_p, c_size_t,
+                                c_void_p]),
     "litho_print_images": (c_int, [c_void_p, c_void_p, c_int, c_int, c_double, c_double, c_double, c_double, c_void_p,
                                    c_void_p, c_void_p, c_void_p, c_void_p]),
     "litho_rasterize_workspace_size": (c_int, [c_int, c_int, ctypes.c_int64, c_int, POINTER(c_size_t)]),
@@ -398,16 +399,23 @@ def litho_intensity_vjp(kern: Kernels, mask, upstream=None, f_first=0, f_count=N
     return dm
 
 
-def litho_ai_inputs(kern: Kernels, targets, focus=0, dose=1.0, stream=None):
+def litho_ai_inputs_workspace_size(kern: Kernels, b: int) -> int:
+    sz = c_size_t()
+    _check(lib().litho_ai_inputs_workspace_size(kern.handle, b, byref(sz)))
+    return sz.value
+
+
+def litho_ai_inputs(kern: Kernels, targets, focus=0, dose=1.0, precision="fft32", out=None, workspace=None,
+                    stream=None):
     """targets: CUDA float32 [b][n][n] (0/1) -> X [b][3][n][n] (Eq. (9) channels)."""
     import torch
     b, n = targets.shape[0], targets.shape[-1]
-    sz = c_size_t()
-    _check(lib().litho_ai_inputs_workspace_size(kern.handle, byref(sz)))
-    ws = torch.empty(sz.value, dtype=torch.uint8, device=targets.device)
-    x = torch.empty((b, 3, n, n), dtype=torch.float32, device=targets.device)
-    _check(lib().litho_ai_inputs(kern.handle, c_void_p(targets.data_ptr()), b, dose, focus, c_void_p(x.data_ptr()),
-                                 c_void_p(ws.data_ptr()), ws.numel(), _stream_ptr(stream)))
+    if workspace is None:
+        workspace = torch.empty(litho_ai_inputs_workspace_size(kern, b), dtype=torch.uint8, device=targets.device)
+    x = out if out is not None else torch.empty((b, 3, n, n), dtype=torch.float32, device=targets.device)
+    _check(lib().litho_ai_inputs(kern.handle, c_void_p(targets.data_ptr()), b, dose, focus, prec_code(precision),
+                                 c_void_p(x.data_ptr()), c_void_p(workspace.data_ptr()), workspace.numel(),
+                                 _stream_ptr(stream)))
     return x
 
 

@@ -42,13 +42,16 @@ def test_intensity_vjp_matches_oracle(litho_lib, cuda):
         assert np.abs(ones[c] - ref1).max() <= 1e-4 * np.abs(ref1).max()
 
 
-def test_ai_inputs_match_oracle(litho_lib, cuda):
+@pytest.mark.parametrize("precision", ["fft32", "fft32/coarse"])
+def test_ai_inputs_match_oracle(litho_lib, cuda, precision):
     import torch
     L = litho_lib
     n = 256
     lam, phi, targets = _setup(n, b=3)
     kern = L.litho_upload_kernels(n, 8.0, lam, phi)
-    x = L.litho_ai_inputs(kern, torch.from_numpy(targets).to(cuda), focus=1).cpu().numpy()
+    if precision.endswith("/coarse"):
+        assert 0 < kern.grid(precision) < n
+    x = L.litho_ai_inputs(kern, torch.from_numpy(targets).to(cuda), focus=1, precision=precision).cpu().numpy()
     ref, _, _ = OA.ai_channels(targets, lam[1], phi[1])
     assert np.array_equal(x[:, 0], targets)
     assert np.abs(x[:, 1] - ref[:, 1]).max() <= 1e-5
