@@ -71,7 +71,7 @@ template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const float2* __restrict__ rowbuf, int crop,
                                                                          const float2* __restrict__ tw_g,
                                                                          const float* __restrict__ gain,
-                                                                         float2* __restrict__ mhat) {
+                                                                         float2* __restrict__ mhat, int gain_real) {
   constexpr int W = ColW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
   extern __shared__ float2 smem[];
   float2* tw = smem;
@@ -95,7 +95,8 @@ __global__ void __launch_bounds__(Plan<N>::NT * ColW<N>::W) k_mask_cols(const fl
     v = make_float2(v.x * scale, v.y * scale);
     if (gain) {
       const float g = __ldg(gain + cv) * __ldg(gain + u0 + w);
-      v = make_float2(fmaf(-g, v.y, v.x), fmaf(g, v.x, v.y));
+      v = gain_real ? make_float2(g * v.x, g * v.y)  // the blurred plane's spectrum
+                    : make_float2(fmaf(-g, v.y, v.x), fmaf(g, v.x, v.y));  // the plane + i its blur
     }
     dst[(size_t)cv * crop + w] = v;
   }
@@ -290,7 +291,7 @@ cudaError_t mask_rows_n(const float* m, int b, int crop, const float2* tw, float
 
 template <int N>
 cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, float2* rowbuf, float2* mhat,
-                            const float* gain, cudaStream_t st) {
+                            const float* gain, bool gain_real, cudaStream_t st) {
   const size_t smr = sizeof(float2) * (2 * N + PadLen<N>::value + 1);
   cudaError_t e = smem_attrs(k_mask_rows<N>, smr);
   if (e != cudaSuccess) return e;
@@ -299,7 +300,8 @@ cudaError_t mask_spectrum_n(const float* m, int b, int crop, const float2* tw, f
   const size_t sm = col_smem_bytes<N>();
   e = smem_attrs(k_mask_cols<N>, sm);
   if (e != cudaSuccess) return e;
-  k_mask_cols<N><<<dim3(crop / ColW<N>::W, b), Plan<N>::NT * ColW<N>::W, sm, st>>>(rowbuf, crop, tw, gain, mhat);
+  k_mask_cols<N><<<dim3(crop / ColW<N>::W, b), Plan<N>::NT * ColW<N>::W, sm, st>>>(rowbuf, crop, tw, gain, mhat,
+                                                                                   gain_real ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -365,8 +367,8 @@ bool fft_twiddle_table(int n, float2* out) {
 }
 
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
-                                 float2* mhat, cudaStream_t st, const float* gain) {
-#define CALL(N) mask_spectrum_n<N>(m, b, crop, tw, rowbuf, mhat, gain, st)
+                                 float2* mhat, cudaStream_t st, const float* gain, bool gain_real) {
+#define CALL(N) mask_spectrum_n<N>(m, b, crop, tw, rowbuf, mhat, gain, gain_real, st)
   LITHO_DISPATCH_NC(n, CALL)
 #undef CALL
 }

@@ -93,7 +93,8 @@ __global__ void __launch_bounds__(1024) k_reduce_loss(const double* __restrict__
 // Backward rows: for every kernel of the plane, E = inverse FFT of the band row
 // T[y][:], P = G[y][:] E, U[y][c] = forward FFT of P on the crop columns.
 // Plane p takes lam[(p mod lam_period) nk ...] (clips of a group repeat the focus planes).
-template <int N>
+// BANDED (2 crop <= N): the band row's zero half is skipped in the first pass.
+template <int N, bool BANDED>
 __global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restrict__ t1, const float* __restrict__ lam,
                                                           int nk, int crop, const float* __restrict__ g,
                                                           const float2* __restrict__ tw_g, float2* __restrict__ u,
@@ -121,14 +122,14 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restri
     if (lam[(plane % lam_period) * nk + k] == 0.f) continue;
     const size_t rowoff = (((size_t)plane * nk + k) * N + y) * crop;
     const float2* row = t1 + rowoff;
-    auto load_band = [&](int idx) {
-      const int c = freq_of_idx(idx, N) + half;
+    auto load_band = [&](int, int r, int idx) {
+      const int c = (r < PL::R[0] / 2 ? idx : idx - N) + half;  // first pass: idx < N/2 exactly when r < R/2
       return (c >= 0 && c < crop) ? __ldg(row + c) : make_float2(0.f, 0.f);
     };
     auto times_g = [&](int p, int q, int idx, float2 v) {
       bufb[pad16(idx)] = make_float2(v.x * gv[p][q], v.y * gv[p][q]);
     };
-    fft_load_use<N, +1>(bufa, tw, t, load_band, times_g);
+    fft_load_use<N, +1, decltype(load_band), decltype(times_g), BANDED>(bufa, tw, t, load_band, times_g);
     __syncthreads();
     auto load_prod = [&](int idx) { return bufb[pad16(idx)]; };
     float2* urow = u + rowoff;
@@ -244,9 +245,10 @@ template <int N>
 cudaError_t adj_rows_n(const float2* t1, const float* lam, int nk, int crop, const float* g, const float2* tw,
                        float2* u, int planes, int lam_period, cudaStream_t st) {
   const size_t sm = sizeof(float2) * (N + 2 * PadLen<N>::value);
-  cudaError_t e = cudaFuncSetAttribute(k_adj_rows<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  auto kern = 2 * crop <= N ? k_adj_rows<N, true> : k_adj_rows<N, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  k_adj_rows<N><<<dim3(N, planes), Plan<N>::NT, sm, st>>>(t1, lam, nk, crop, g, tw, u, lam_period);
+  kern<<<dim3(N, planes), Plan<N>::NT, sm, st>>>(t1, lam, nk, crop, g, tw, u, lam_period);
   return cudaGetLastError();
 }
 
@@ -315,6 +317,7 @@ struct IltLayout {
   // on N (big), image spectra (spec)
   float* ic;
   float2 *mid, *big, *spec;
+  float* gain;  // the resist blur's transfer function on the 2C band
   size_t bytes;
 };
 
@@ -358,6 +361,7 @@ IltLayout ilt_layout(const litho_kernels* h, int b, int P, int G, void* base) {
     L.mid = reinterpret_cast<float2*>(take(PG * NC * C2 * 8));
     L.big = reinterpret_cast<float2*>(take(PG * N * C2 * 8));
     L.spec = reinterpret_cast<float2*>(take(PG * C2 * C2 * 8));
+    L.gain = reinterpret_cast<float*>(take(C2 * 4));
   }
   L.bytes = off;
   return L;
@@ -501,6 +505,7 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
   const int NE = coarse ? h->nc : N, C2 = 2 * C;
   const float2* twe = coarse ? h->d_twc : h->d_tw;
   const float lp_scale = float((double(N) / NE) * (double(N) / NE));
+  if (coarse) LITHO_TRY_CUDA(launch_blur_gain(taps, N, C2, L.gain, st));
   // Groups of g clips: every launch covers the group's g x P planes (plane
   // i P + p is focus plane f0 + p of clip c0 + i; its fields follow the
   // plane's K kernels).
@@ -516,16 +521,18 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
       const float2* phi = h->d_phi + size_t(f0) * K * C * C;
       const float* lam = h->d_lambda + size_t(f0) * K;
       {
-        ProfScope ps(kStageIltForward, st, coarse ? 8 : 5);
+        ProfScope ps(kStageIltForward, st, 5);
         LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, P * K, NE, C, twe, L.t1, st, g));
         LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, gp,
                                          (long long)K * NE * C, (long long)NE * NE, st, P));
-        if (coarse) {
+        if (coarse) {  // the blurred image straight from the interpolation (blur applied to the spectrum)
           LITHO_TRY_CUDA(launch_mask_rows(L.ic, gp, NE, C2, twe, L.mid, st));
-          LITHO_TRY_CUDA(launch_interp_cols(L.mid, gp, NE, N, C2, twe, h->d_tw, nullptr, L.big, st));
-          LITHO_TRY_CUDA(launch_band_rows_real(L.big, gp, N, C2, 1.0f, h->d_tw, L.img, st));
+          LITHO_TRY_CUDA(launch_interp_cols(L.mid, gp, NE, N, C2, twe, h->d_tw, L.gain, L.big, st));
+          LITHO_TRY_CUDA(launch_band_rows_resist(L.big, gp, N, C2, h->d_tw, float(threshold), nullptr, L.blur,
+                                                 nullptr, st));
+        } else {
+          LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
         }
-        LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
         k_resist_grad<<<dim3(kPartials, g), 256, 0, st>>>(L.blur, target_dev + c0 * nn, nn, P, float(resist_steep),
                                                          float(threshold), L.img, L.partial);
         LITHO_TRY_CUDA(cudaGetLastError());
@@ -533,14 +540,15 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
         LITHO_TRY_CUDA(cudaGetLastError());
       }
       {
-        ProfScope ps(kStageIltBackward, st, coarse ? 7 : 4);
-        LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
+        ProfScope ps(kStageIltBackward, st, coarse ? 6 : 4);
         const float* gsrc = L.blur;
-        if (coarse) {
-          LITHO_TRY_CUDA(launch_mask_spectrum(L.blur, gp, N, C2, h->d_tw, L.big, L.spec, st));
+        if (coarse) {  // low-pass of g (x) q: the spectrum of q on the 2C band times the blur's transfer function
+          LITHO_TRY_CUDA(launch_mask_spectrum(L.img, gp, N, C2, h->d_tw, L.big, L.spec, st, L.gain, true));
           LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, gp, NE, C2, twe, L.mid, st));
           LITHO_TRY_CUDA(launch_band_rows_real(L.mid, gp, NE, C2, lp_scale, twe, L.ic, st));
           gsrc = L.ic;
+        } else {
+          LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
         }
         LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, gsrc, twe, L.u, gp, P, st));
         LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, gp * K, P * K, st));

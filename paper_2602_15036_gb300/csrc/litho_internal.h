@@ -122,9 +122,10 @@ inline const float2* coarse_tw(const litho_kernels* h, litho_precision p) {
 // The N-entry per-pass twiddle table the FFT kernels expect (false if n unsupported).
 bool fft_twiddle_table(int n, float2* out);
 // Mask spectrum: m[b][n][n] -> mhat[b][C][C] = N^-2 DFT(m) on the crop.  rowbuf: [b][n][C].
-// With `gain` [C] the stored value is mhat (1 + i gain[v] gain[u]) (blur channel, see fft.cu).
+// With `gain` [C] the stored value is mhat (1 + i gain[v] gain[u]) (blur channel, see fft.cu),
+// or with gain_real mhat gain[v] gain[u] (the spectrum of the blurred plane).
 cudaError_t launch_mask_spectrum(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf,
-                                 float2* mhat, cudaStream_t st, const float* gain = nullptr);
+                                 float2* mhat, cudaStream_t st, const float* gain = nullptr, bool gain_real = false);
 // Row pass of the mask spectrum alone: rowbuf[b][n][C] = row DFT of m, crop columns kept.
 cudaError_t launch_mask_rows(const float* m, int b, int n, int crop, const float2* tw, float2* rowbuf, cudaStream_t st);
 // Column pass of the interpolation from an nc grid to an n grid (interp.cu):
