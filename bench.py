@@ -193,6 +193,31 @@ def stage_models(prec: str, clips: int, n: int, crop: int, n_focus: int, k_eff: 
     return m
 
 
+def ilt_models(clips: int, n: int, ne: int, crop: int, n_focus: int, k: int, coarse: bool, group: int,
+               resist_taps: int = 11) -> dict:
+    """stage -> (flops per step, algorithmic DRAM bytes per step) of litho_ilt_grad, counted as in
+    stage_models (5 m log2 m per m-point transform): the forward pass (mask spectrum, stage 1 and 2
+    per kernel, interpolation with the blur channel or the direct blur, resist gradient) and the
+    backward pass (low-pass of the blurred dL/dI or the direct blur, adjoint rows: inverse and
+    forward transform per kernel and row, adjoint columns, the band-to-full gradient).  Bytes:
+    theta, target and the kernels Phi (once per clip group) in, the gradient out."""
+    fft = lambda m: 5.0 * m * math.log2(m)  # noqa: E731
+    c2 = 2 * crop
+    fwd_plane = k * (crop * fft(ne) + 6.0 * crop * crop + ne * (fft(ne) + 4.0 * ne)) + n * n * 10.0
+    bwd_plane = k * (ne * (2 * fft(ne) + 8.0 * ne) + crop * fft(ne) + 6.0 * crop * crop)
+    if coarse:
+        fwd_plane += ne / 2 * fft(ne) + c2 * fft(ne) + c2 * fft(n) + n * fft(n) + 6.0 * c2 * c2
+        bwd_plane += n / 2 * fft(n) + c2 * fft(n) + c2 * fft(ne) + ne * fft(ne)
+    else:
+        fwd_plane += n * n * 4.0 * resist_taps
+        bwd_plane += n * n * 4.0 * resist_taps
+    fwd = clips * (n / 2 * fft(n) + crop * fft(n) + n_focus * fwd_plane)
+    bwd = clips * (crop * fft(n) + n * fft(n) + n_focus * bwd_plane)
+    groups = -(-clips // group)
+    phi_bytes = groups * n_focus * k * crop * crop * 8.0
+    return {"ilt_forward": (fwd, clips * n * n * 8.0 + phi_bytes), "ilt_backward": (bwd, clips * n * n * 4.0)}
+
+
 # Sources whose kernels each stage runs: a DRAM-traffic figure taken with ncu
 # holds only while they are unchanged.
 STAGE_SOURCES = {
@@ -496,6 +521,16 @@ def run_ilt(args):
     prof = L.litho_profile_read()
     L.litho_profile_enable(False)
     total = ctx.max_over_ranks(sum(step_ms))
+    peaks, peak_src = _peaks()
+    ne = kern.grid(prec) if prec.endswith("/coarse") else n
+    per_clip = len(focus) * k * n * kern.crop * 8.0  # the library's clip groups: stage-1 fields within 2 GiB
+    cap = max(1, min(clips, int((2 << 30) // per_clip)))
+    group = -(-clips // -(-clips // cap))
+    roofs = rooflines(prof, args.steps + args.warmup,
+                      ilt_models(clips, n, ne or n, kern.crop, len(focus), k, bool(ne) and ne < n, group), peaks)
+    dominant = max(roofs.items(), key=lambda kv: kv[1]["ms_per_step"])
+    roof = dict(dominant[1], kernel=dominant[0], traffic=None,
+                peak_source=f"derived ALU peak; {peak_src} HBM copy bandwidth")
     line = {"metric": "ILT gradient Mpx/s (1024² clips, K=16, 5 focus)", "workload": "ilt",
             "value": whole_job_rate(clips * n * n * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
             "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
@@ -504,6 +539,7 @@ def run_ilt(args):
                        "precision": prec, "grid": kern.grid(prec) if prec.endswith("/coarse") else n},
             "loss_first_last": [losses[0], losses[-1]],
             "stages_ms_per_step": {kk: v[0] / (args.steps + args.warmup) for kk, v in prof.items()},
+            "roofline": roof, "stage_rooflines": {kk: {x: v[x] for x in ("bound", "frac")} for kk, v in roofs.items()},
             "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}
     if ctx.rank == 0:
         print(json.dumps(line), flush=True)
