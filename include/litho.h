@@ -435,7 +435,10 @@ litho_status litho_serve_stats_reset(litho_server* s);
 void litho_serve_destroy(litho_server* s);
 /* Host-side fault injection for tests: bit 0 makes the next admitted
  * request's device allocation fail (the request ends with LITHO_ENOMEM and
- * the server carries on).  No GPU fault is involved. */
+ * the server carries on); bit 1 makes the next admitted request slow (a
+ * fixed 200 ms device delay on its slot's stream before its work: one thread
+ * spinning on the SM clock, which always ends), so that requests on the
+ * other slots can be seen to complete meanwhile.  No GPU fault is involved. */
 litho_status litho_serve_inject_fault(litho_server* s, int fault_mask);
 
 /* ---- tracing ------------------------------------------------------------------------------------- */
@@ -443,7 +446,10 @@ litho_status litho_serve_inject_fault(litho_server* s, int fault_mask);
 /* Per-stage device timing.  While enabled, every stage the library enqueues is
  * bracketed by CUDA events on its stream (stages: mask_spectrum, stage1_fft,
  * stage2_fft, stage1_gemm_operands, stage2_gemm, resist, ilt_forward,
- * ilt_backward, ilt_reduce).  litho_profile_read waits for the recorded events
+ * ilt_backward, ilt_reduce, upsample, upsample_resist, contours, epe,
+ * raster).  Every stage also opens an NVTX range of the same name on the
+ * calling host thread, enabled or not (free unless an NVTX tool is attached).
+ * litho_profile_read waits for the recorded events
  * and reports, for up to max_stages stages that ran since the last reset,
  * the name (32-byte slots in `names`), the summed device milliseconds and the
  * number of kernel launches; *count receives how many were written. */

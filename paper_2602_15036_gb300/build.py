@@ -72,7 +72,7 @@ def build(verbose: bool = False) -> str:
                 print(log, file=sys.stderr)
     if not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         tmp = LIB + ".tmp"
-        cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-lpthread"]
+        cmd = [_nvcc(), "-shared"] + ARCH + ["-o", tmp] + objs + ["-lpthread", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

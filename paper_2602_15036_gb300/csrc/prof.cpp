@@ -1,6 +1,9 @@
 // Per-stage device timing: CUDA events recorded on the launching stream around
 // each stage while profiling is enabled, resolved into per-stage totals when
-// read.  Off by default; when off, a scope costs one relaxed atomic load.
+// read.  Off by default; when off, a scope costs one relaxed atomic load and
+// an NVTX range named after the stage (a no-op unless a tool is attached).
+#include <nvtx3/nvToolsExt.h>
+
 #include <atomic>
 #include <cstring>
 #include <mutex>
@@ -55,6 +58,7 @@ void resolve_locked() {
 }  // namespace
 
 ProfScope::ProfScope(int stage, cudaStream_t st, int launches) : stage_(stage), st_(st), launches_(launches) {
+  nvtxRangePushA(kStageNames[stage]);
   if (!g_on.load(std::memory_order_relaxed)) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t a = get_event();
@@ -66,6 +70,7 @@ ProfScope::ProfScope(int stage, cudaStream_t st, int launches) : stage_(stage), 
 }
 
 ProfScope::~ProfScope() {
+  nvtxRangePop();
   if (!a_) return;
   std::lock_guard<std::mutex> lk(g_mu);
   cudaEvent_t b = get_event();

@@ -182,6 +182,8 @@ void CUDART_CB on_done(void* arg) {
   finish_locked(s, q, kDone, LITHO_OK, nullptr);
 }
 
+constexpr double kInjectedDelayMs = 200.0;  // the injected slow request's device delay
+
 // Enqueues an admitted request on its slot's stream (called without the lock).
 litho_status launch(litho_server* s, Req* q, litho_kernels* h, std::string* err) {
   Slot& sl = s->slots[q->slot];
@@ -214,6 +216,13 @@ litho_status launch(litho_server* s, Req* q, litho_kernels* h, std::string* err)
     s->fault_mask.fetch_and(~1);
     *err = "injected device allocation failure";
     return LITHO_ENOMEM;
+  }
+  if (s->fault_mask.load() & 2) {  // a slow request: a fixed device delay before its work
+    s->fault_mask.fetch_and(~2);
+    if (launch_delay(sl.stream, kInjectedDelayMs) != cudaSuccess) {
+      *err = "delay launch failed";
+      return LITHO_ECUDA;
+    }
   }
   if (cudaMallocAsync(&d, dev_bytes, sl.stream) != cudaSuccess) {
     cudaGetLastError();

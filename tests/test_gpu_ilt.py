@@ -169,3 +169,25 @@ def test_autograd_function(litho_lib, cuda):
     g, _ = litho_lib.litho_ilt_grad(kern, th.detach(), tg, **PARAMS)
     w = torch.tensor([2.0, 3.0], device=cuda).view(2, 1, 1)
     assert torch.allclose(th.grad, g * w, rtol=0, atol=1e-6 * g.abs().max().item())
+
+
+def test_ilt_run_resumes_from_checkpoint(litho_lib, cuda, tmp_path):
+    """A gradient-descent run through litho_ilt_grad stopped after 3 steps and
+    resumed from its checkpoint files equals the run that never stopped."""
+    import torch
+    from paper_2602_15036_gb300.iltrun import IltRun
+    n, pixel = 128, 8.0
+    lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, [-40.0, 0.0, 40.0], 6)
+    kern = litho_lib.litho_upload_kernels(n, pixel, lam, phi)
+    clips = [synth.ilt_clip(n, pixel, seed=900 + i) for i in range(2)]
+    theta = torch.from_numpy(np.stack([c[0] for c in clips])).to(cuda)
+    target = torch.from_numpy(np.stack([c[1] for c in clips])).to(cuda)
+    fn = IltRun.litho_grad_fn(kern, precision="fft32/coarse", **PARAMS)
+    full = IltRun(theta.clone(), target, fn)
+    full.run(6)
+    prefix = str(tmp_path / "ilt")
+    IltRun(theta.clone(), target, fn).run(3, checkpoint_prefix=prefix)
+    again = IltRun.load(prefix, target, fn, device=cuda)
+    again.run(3)
+    assert torch.equal(again.theta, full.theta) and again.losses == full.losses
+    assert full.losses[-1] < full.losses[0]

@@ -155,3 +155,25 @@ def test_small_requests_overtake_a_large_one(litho_lib, cuda):
     assert all(v == L.OK for v in st.values())
     assert order.index(tb) >= 3, order
     srv.close()
+
+
+def test_injected_slow_request_does_not_hold_the_others(litho_lib, cuda):
+    """A request made slow on its own slot (a fixed device delay) finishes
+    last while the requests submitted after it complete on the other slots,
+    all with the same result as the request run alone."""
+    L = litho_lib
+    srv = L.Server(16 << 30, max_slots=4, max_queue=64)
+    opt = L.make_optics(**DUV)
+    m = synth.random_rect_mask(256, seed=7)
+    ref = np.zeros_like(m)
+    t, _ = srv.submit("image", opt, 256, 8.0, 0.0, 8, m, ref)    # builds and warms the kernel set
+    assert srv.poll(t, 60000) == L.OK
+    srv.inject_fault(2)
+    outs = [np.zeros_like(m) for _ in range(4)]
+    tickets = [srv.submit("image", opt, 256, 8.0, 0.0, 8, m, outs[i])[0] for i in range(4)]
+    status, order = _wait_all(srv, L, tickets, timeout_s=120)
+    assert all(status[t] == L.OK for t in tickets), status
+    assert order[-1] == tickets[0], order
+    for o in outs:
+        assert np.array_equal(o, ref)
+    srv.close()
