@@ -2,12 +2,16 @@
 // normalised Gaussian g[j] ~ exp(-(j p)^2 / (2 s^2)), |j| <= R = ceil(4 s / p),
 // then printed = [I_blur >= T] (ties print, as the ">=" of Eqs. (16)-(17)).
 //
-// One pass over HBM: each CTA loads a (32 + 2R) x (32 + 2R) tile with a
-// periodic halo into shared memory, blurs rows into a second tile, blurs
-// columns from it and writes I_blur (f32) and printed (u8) once.  For the
-// common radii (R <= 12) the radius is a template parameter: the taps live in
-// registers, the tap loops unroll and each thread blurs four consecutive
-// column outputs from a register window; larger radii take a loop version.
+// One pass over HBM, by strips: a CTA takes 32 columns by SH rows (128 when
+// n allows, else 32).  Its threads load the strip and its periodic halo into
+// shared memory together, the warps blur its rows horizontally into a
+// shared strip of SH + 2R rows; then each thread
+// blurs its column over a register window of SH/8 + 2R rows and writes
+// I_blur (f32) and printed (u8), a warp writing whole 128-byte rows.  Reads
+// are 1 + 2R/32 horizontal and 1 + 2R/SH vertical per pixel (the halos of
+// neighbouring strips, which run side by side, mostly hit L2).  For the
+// common radii (R <= 12) the radius is a template parameter (taps in
+// registers, unrolled loops); larger radii take a loop version.
 #include <cmath>
 
 #include "litho_internal.h"
@@ -16,89 +20,94 @@ namespace litho {
 
 namespace {
 
-constexpr int TX = 32, TY = 32, BY = 8, RPT = TY / BY;  // RPT: column outputs per thread
+constexpr int SW = 32, SWARPS = 8;  // strip width, warps per CTA
 
-template <int R>  // R >= 0: compile-time radius; R < 0: taps.radius at run time
-__global__ void __launch_bounds__(TX * BY) k_resist(const float* __restrict__ img, int n, ResistTaps taps, float thr,
-                                                    float* __restrict__ iblur, uint8_t* __restrict__ printed) {
+template <int R, int SH>  // R >= 0: compile-time radius; R < 0: taps.radius at run time
+__global__ void __launch_bounds__(32 * SWARPS) k_resist(const float* __restrict__ img, int n, ResistTaps taps,
+                                                        float thr, float* __restrict__ iblur,
+                                                        uint8_t* __restrict__ printed) {
+  constexpr int PER = SH / SWARPS;  // output rows per thread
   extern __shared__ float sm[];
   const int r = R >= 0 ? R : taps.radius;
-  const int hw = TX + 2 * r, hh = TY + 2 * r;
-  float* tile = sm;            // [hh][hw]
-  float* rows = sm + hh * hw;  // [hh][TX]
-  const int plane = blockIdx.z, x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int rows_in = SH + 2 * r, wi = SW + 2 * r;
+  float* tile = sm;                 // [rows_in][wi] the strip and its periodic halo
+  float* hb = sm + rows_in * wi;    // [rows_in][SW] horizontally blurred rows
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int plane = blockIdx.z, x0 = blockIdx.x * SW, y0 = blockIdx.y * SH;
   const float* src = img + (size_t)plane * n * n;
   const bool pow2 = (n & (n - 1)) == 0;
-  for (int ty = threadIdx.y; ty < hh; ty += BY) {
-    int gy = y0 + ty - r;
-    gy = pow2 ? (gy & (n - 1)) : (gy + n) % n;
-    const float* srow = src + (size_t)gy * n;
-    for (int tx = threadIdx.x; tx < hw; tx += TX) {
-      int gx = x0 + tx - r;
-      gx = pow2 ? (gx & (n - 1)) : (gx + n) % n;
-      tile[ty * hw + tx] = __ldg(srow + gx);
-    }
-  }
-  __syncthreads();
-  const int x = threadIdx.x;
-  // rows[ty][x] = sum_a g[a] tile[ty][x + r - a]
+  float g[R >= 0 ? 2 * R + 1 : 1];
   if constexpr (R >= 0) {
-    float g[2 * R + 1];
 #pragma unroll
     for (int a = 0; a <= 2 * R; ++a) g[a] = taps.g[a];
-    for (int ty = threadIdx.y; ty < hh; ty += BY) {
-      const float* t = tile + ty * hw + x + R;
-      float acc = 0.f;
+  }
+  // all threads load the tile at once (consecutive threads, consecutive x)
+  for (int i = threadIdx.x; i < rows_in * wi; i += blockDim.x) {
+    const int ry = i / wi, rx = i - ry * wi;
+    int gy = y0 + ry - r, gx = x0 + rx - r;
+    gy = pow2 ? (gy & (n - 1)) : (gy + n) % n;
+    gx = pow2 ? (gx & (n - 1)) : (gx + n) % n;
+    tile[i] = __ldg(src + (size_t)gy * n + gx);
+  }
+  __syncthreads();
+  // rows: hb[ry][x] = sum_a g[a] I[y0 + ry - r][x0 + x - a]
+  for (int ry = warp; ry < rows_in; ry += SWARPS) {
+    const float* t = tile + ry * wi + lane + r;
+    float acc = 0.f;
+    if constexpr (R >= 0) {
 #pragma unroll
       for (int a = -R; a <= R; ++a) acc = fmaf(g[a + R], t[-a], acc);
-      rows[ty * TX + x] = acc;
+    } else {
+      for (int a = -r; a <= r; ++a) acc = fmaf(taps.g[a + r], t[-a], acc);
     }
-    __syncthreads();
-    const int yy = threadIdx.y * RPT;
-    float win[RPT + 2 * R];
+    hb[ry * SW + lane] = acc;
+  }
+  __syncthreads();
+  // columns: rows y0 + warp PER ... of column x0 + lane
+  const int yy = warp * PER;
+  float* dst = iblur + (size_t)plane * n * n;
+  uint8_t* pr = printed ? printed + (size_t)plane * n * n : nullptr;
+  if constexpr (R >= 0) {
+    float win[PER + 2 * R];
 #pragma unroll
-    for (int j = 0; j < RPT + 2 * R; ++j) win[j] = rows[(yy + j) * TX + x];
-    float* dst = iblur + (size_t)plane * n * n;
-    uint8_t* pr = printed ? printed + (size_t)plane * n * n : nullptr;
+    for (int j = 0; j < PER + 2 * R; ++j) win[j] = hb[(yy + j) * SW + lane];
 #pragma unroll
-    for (int i = 0; i < RPT; ++i) {
+    for (int i = 0; i < PER; ++i) {
       float acc = 0.f;
 #pragma unroll
       for (int a = -R; a <= R; ++a) acc = fmaf(g[a + R], win[i + R - a], acc);
-      const size_t o = (size_t)(y0 + yy + i) * n + x0 + x;
+      const size_t o = (size_t)(y0 + yy + i) * n + x0 + lane;
       dst[o] = acc;
       if (pr) pr[o] = acc >= thr ? 1 : 0;
     }
   } else {
-    for (int ty = threadIdx.y; ty < hh; ty += BY) {
-      const float* t = tile + ty * hw + x + r;
+    for (int i = 0; i < PER; ++i) {
+      const float* c = hb + (yy + i + r) * SW + lane;
       float acc = 0.f;
-      for (int a = -r; a <= r; ++a) acc = fmaf(taps.g[a + r], t[-a], acc);
-      rows[ty * TX + x] = acc;
-    }
-    __syncthreads();
-    float* dst = iblur + (size_t)plane * n * n;
-    uint8_t* pr = printed ? printed + (size_t)plane * n * n : nullptr;
-    for (int yy = threadIdx.y; yy < TY; yy += BY) {
-      const float* c = rows + (yy + r) * TX + x;
-      float acc = 0.f;
-      for (int a = -r; a <= r; ++a) acc = fmaf(taps.g[a + r], c[-a * TX], acc);
-      const size_t o = (size_t)(y0 + yy) * n + x0 + x;
+      for (int a = -r; a <= r; ++a) acc = fmaf(taps.g[a + r], c[-a * SW], acc);
+      const size_t o = (size_t)(y0 + yy + i) * n + x0 + lane;
       dst[o] = acc;
       if (pr) pr[o] = acc >= thr ? 1 : 0;
     }
   }
 }
 
+template <int R, int SH>
+cudaError_t launch_rs(const float* img, int planes, int n, const ResistTaps& taps, float thr, float* iblur,
+                      uint8_t* printed, cudaStream_t st) {
+  const int r = taps.radius;
+  const size_t sm = sizeof(float) * ((SH + 2 * r) * (SW + 2 * r) + (SH + 2 * r) * SW);
+  cudaError_t e = cudaFuncSetAttribute(k_resist<R, SH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  k_resist<R, SH><<<dim3(n / SW, n / SH, planes), 32 * SWARPS, sm, st>>>(img, n, taps, thr, iblur, printed);
+  return cudaGetLastError();
+}
+
 template <int R>
 cudaError_t launch_r(const float* img, int planes, int n, const ResistTaps& taps, float thr, float* iblur,
                      uint8_t* printed, cudaStream_t st) {
-  const int r = taps.radius;
-  const size_t sm = sizeof(float) * ((TY + 2 * r) * (TX + 2 * r) + (TY + 2 * r) * TX);
-  cudaError_t e = cudaFuncSetAttribute(k_resist<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  k_resist<R><<<dim3(n / TX, n / TY, planes), dim3(TX, BY), sm, st>>>(img, n, taps, thr, iblur, printed);
-  return cudaGetLastError();
+  return n % 128 == 0 ? launch_rs<R, 128>(img, planes, n, taps, thr, iblur, printed, st)
+                      : launch_rs<R, 32>(img, planes, n, taps, thr, iblur, printed, st);
 }
 
 }  // namespace
@@ -125,7 +134,7 @@ bool resist_taps(double sigma_nm, double pixel_nm, ResistTaps* t, std::string* w
 
 cudaError_t launch_resist(const float* img, int planes, int n, const ResistTaps& taps, float threshold, float* iblur,
                           uint8_t* printed, cudaStream_t st) {
-  if (n % TX != 0 || n % TY != 0 || 2 * taps.radius >= n) return cudaErrorInvalidValue;
+  if (n % SW != 0 || 2 * taps.radius >= n) return cudaErrorInvalidValue;
   switch (taps.radius) {
 #define R_CASE(R) \
   case R: return launch_r<R>(img, planes, n, taps, threshold, iblur, printed, st);
