@@ -71,3 +71,21 @@ def test_stage_models_are_consistent():
     r = bench.rooflines({"stage1_fft": (10.0, 8), "stage2_fft": (10.0, 8)}, 1, m3, peaks)
     assert r["stage1_fft"]["bound"] == "hbm" and r["stage2_fft"]["bound"] == "alu"
     assert r["stage1_fft"]["achieved"] == pytest.approx(m3["stage1_fft"][1] / 1e-2 / 1e9)
+
+
+def test_ilt_models_count_the_adjoint_transforms():
+    """The ILT work model: per (clip, plane, kernel) the adjoint rows take two
+    transforms per row and the columns one per crop column, so the coarse grid
+    (512 for 1024^2) cuts the per-kernel work about fourfold; bytes count theta,
+    target and the kernels in, the gradient out."""
+    import math
+    fft = lambda m: 5.0 * m * math.log2(m)  # noqa: E731
+    full = bench.ilt_models(16, 1024, 1024, 224, 5, 16, False, 8)
+    coarse = bench.ilt_models(16, 1024, 512, 224, 5, 16, True, 8)
+    per_kernel_bwd = 1024 * (2 * fft(1024) + 8.0 * 1024) + 224 * fft(1024) + 6.0 * 224 ** 2
+    per_plane_bwd = 16 * per_kernel_bwd + 1024 ** 2 * 4.0 * 11
+    assert full["ilt_backward"][0] == pytest.approx(16 * (224 * fft(1024) + 1024 * fft(1024) + 5 * per_plane_bwd))
+    assert full["ilt_backward"][1] == pytest.approx(16 * 1024 ** 2 * 4.0)
+    assert full["ilt_forward"][1] == pytest.approx(16 * 1024 ** 2 * 8.0 + 2 * 5 * 16 * 224 ** 2 * 8.0)
+    ratio = full["ilt_backward"][0] / coarse["ilt_backward"][0]
+    assert 2.5 < ratio < 4.5
