@@ -218,6 +218,27 @@ def ilt_models(clips: int, n: int, ne: int, crop: int, n_focus: int, k: int, coa
     return {"ilt_forward": (fwd, clips * n * n * 8.0 + phi_bytes), "ilt_backward": (bwd, clips * n * n * 4.0)}
 
 
+def ai_models(clips: int, n: int, ne: int, crop: int, k: int, coarse: bool, round_taps: int) -> dict:
+    """stage -> (flops per step, algorithmic DRAM bytes per step) of the AI-input step
+    (litho_ai_inputs + litho_print_images), counted as in stage_models: ilt_forward = the image
+    channel (mask spectrum, stage 1 and 2 per kernel, interpolation), ilt_backward = the adjoint of
+    ones (adjoint rows and columns per kernel, the band-to-full gradient), ilt_reduce = the two
+    channel normalisations (read, then read and write), resist = the print images (blur of the
+    targets, two thresholds, the L1 count).  Bytes: targets in, the three channels out."""
+    fft = lambda m: 5.0 * m * math.log2(m)  # noqa: E731
+    c2 = 2 * crop
+    fwd = clips * (n / 2 * fft(n) + crop * fft(n) +
+                   k * (crop * fft(ne) + 6.0 * crop * crop + ne * (fft(ne) + 4.0 * ne)))
+    if coarse:
+        fwd += clips * (ne / 2 * fft(ne) + c2 * fft(ne) + c2 * fft(n) + n * fft(n))
+    bwd = clips * (k * (ne * (2 * fft(ne) + 8.0 * ne) + crop * fft(ne) + 6.0 * crop * crop) +
+                   crop * fft(n) + n * fft(n))
+    px = clips * n * n
+    return {"ilt_forward": (fwd, px * 4.0 + px * 8.0), "ilt_backward": (bwd, px * 4.0),
+            "ilt_reduce": (px * 2 * 3.0, px * 2 * 12.0),
+            "resist": (px * 4.0 * round_taps, px * (4.0 + 4.0 + 4.0 + 1.0 + 1.0))}
+
+
 # Sources whose kernels each stage runs: a DRAM-traffic figure taken with ncu
 # holds only while they are unchanged.
 STAGE_SOURCES = {
@@ -702,6 +723,14 @@ def run_ai(args):
     prof = L.litho_profile_read()
     L.litho_profile_enable(False)
     total = ctx.max_over_ranks(sum(step_ms))
+    peaks, peak_src = _peaks()
+    ne = kern.grid(prec) if prec.endswith("/coarse") else N
+    round_taps = 2 * math.ceil(4 * 20.0 / PIXEL) + 1
+    roofs = rooflines(prof, args.steps, ai_models(clips, N, ne or N, kern.crop, K, bool(ne) and ne < N, round_taps),
+                      peaks)
+    dominant = max(roofs.items(), key=lambda kv: kv[1]["ms_per_step"])
+    roof = dict(dominant[1], kernel=dominant[0], traffic=None,
+                peak_source=f"derived ALU peak; {peak_src} HBM copy bandwidth")
     line = {"metric": "AI-input channels + print images Mpx/s (2048² targets, K=24)", "workload": "ai",
             "value": whole_job_rate(clips * N * N * args.steps / 1e6, ctx.world, [total * 1e-3]), "unit": "Mpx/s",
             "n_gpus": ctx.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
@@ -710,6 +739,7 @@ def run_ai(args):
                        "precision": prec},
             "litho_loss_first_clips": [int(v) for v in out["p"][2][:4].cpu().tolist()],
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "roofline": roof, "stage_rooflines": {kk: {x: v[x] for x in ("bound", "frac")} for kk, v in roofs.items()},
             "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}
     if ctx.rank == 0:
         print(json.dumps(line), flush=True)
