@@ -249,11 +249,14 @@ litho_status litho_resist(const float* intensity_dev, int planes, int n, double 
  * every pixel (the gradient of the total intensity).  The same adjoint as
  * litho_ilt_grad without the resist and sigmoid factors: 2 D N^-2 Re IDFT of
  * sum_k lam_k conj(Phi_k) DFT_crop(q E_k).  Workspace as litho_ilt_workspace_size
- * (the smaller size evaluates one plane at a time).  FP32 FFT path.  Async. */
+ * (the smaller size evaluates one plane of one clip at a time).  prec:
+ * LITHO_PREC_FFT32 (else EUNSUPPORTED), optionally | LITHO_GRID_COARSE (the
+ * fields and the adjoint on the coarse grid, q low-passed to the image band
+ * and sampled there: the full-grid result up to FP32 rounding).  Async. */
 litho_status litho_intensity_vjp_workspace_size(const litho_kernels* h, int b, size_t* full_bytes, size_t* min_bytes);
-litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, int b, double dose, int f_first,
-                                 int f_count, const float* upstream_dev, float* dm_dev, void* workspace_dev,
-                                 size_t workspace_bytes, void* stream);
+litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, int b, double dose,
+                                 litho_precision prec, int f_first, int f_count, const float* upstream_dev,
+                                 float* dm_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* Eq. (9): the three input channels of the AI initialiser for binary targets
  * Z_t = target[b][n][n] (0/1 f32): x[c][0] = Z_t, x[c][1] = I0 / max I0 with I0

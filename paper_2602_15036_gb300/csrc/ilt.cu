@@ -572,9 +572,9 @@ litho_status litho_intensity_vjp_workspace_size(const litho_kernels* h, int b, s
   return litho_ilt_workspace_size(h, b, full_bytes, min_bytes);
 }
 
-litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, int b, double dose, int f_first,
-                                 int f_count, const float* upstream_dev, float* dm_dev, void* workspace_dev,
-                                 size_t workspace_bytes, void* stream) {
+litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, int b, double dose,
+                                 litho_precision prec, int f_first, int f_count, const float* upstream_dev,
+                                 float* dm_dev, void* workspace_dev, size_t workspace_bytes, void* stream) {
   if (!h || !mask_dev || !dm_dev || !workspace_dev || b < 1) {
     set_error("null argument or b < 1");
     return LITHO_EINVAL;
@@ -582,6 +582,11 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
   if (f_first < 0 || f_count < 1 || f_first + f_count > h->n_focus || !std::isfinite(dose)) {
     set_error("focus planes [f_first, f_first + f_count) must lie in [0, n_focus); dose finite");
     return LITHO_EINVAL;
+  }
+  if ((int(prec) & ~LITHO_GRID_COARSE) != LITHO_PREC_FFT32) {
+    set_error("litho_intensity_vjp implements the FP32 FFT path only (LITHO_PREC_FFT32, optionally | "
+              "LITHO_GRID_COARSE)");
+    return LITHO_EUNSUPPORTED;
   }
   if ((reinterpret_cast<uintptr_t>(workspace_dev) & 255) != 0) {
     set_error("workspace must be 256-byte aligned");
@@ -601,9 +606,16 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nn = size_t(N) * N;
   const float scale = float(2.0 * dose / (double(N) * double(N)));
+  // coarse grid as in litho_ilt_grad: the upstream low-passed to the 2C band
+  // and sampled on nc (ones: only the DC term, the constant (N/nc)^2)
+  const bool coarse = (int(prec) & LITHO_GRID_COARSE) && h->nc > 0 && interp_cols_supported(h->nc, N);
+  const int NE = coarse ? h->nc : N, C2 = 2 * C;
+  const float2* twe = coarse ? h->d_twc : h->d_tw;
+  const float lp_scale = float((double(N) / NE) * (double(N) / NE));
   ProfScope ps(kStageIltBackward, st, 1);
+  float* ones = coarse ? L.ic : L.img;
   if (!upstream_dev) {  // dL/dI = 1 on every pixel of the selected planes
-    k_fill<<<256, 256, 0, st>>>(L.img, 1.0f, size_t(G) * P * nn);
+    k_fill<<<256, 256, 0, st>>>(ones, coarse ? lp_scale : 1.0f, size_t(G) * P * NE * NE);
     LITHO_TRY_CUDA(cudaGetLastError());
   }
   for (int c0 = 0; c0 < b; c0 += G) {
@@ -611,11 +623,20 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
     LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev + c0 * nn, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
     for (int f0 = f_first; f0 < f_first + f_count; f0 += P) {
       const int p = std::min(P, f_first + f_count - f0);
-      const float* up = upstream_dev ? upstream_dev + (size_t(c0) * F + f0) * nn : L.img;
-      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, p * K, N, C, h->d_tw, L.t1, st, g));
-      LITHO_TRY_CUDA(launch_adj_rows(N, L.t1, h->d_lambda + size_t(f0) * K, K, C, up, h->d_tw, L.u, g * p, p, st));
-      LITHO_TRY_CUDA(launch_adj_cols(N, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
-                                     h->d_tw, L.sk, g * p * K, p * K, st));
+      const float* up = ones;
+      if (upstream_dev) {
+        up = upstream_dev + (size_t(c0) * F + f0) * nn;
+        if (coarse) {
+          LITHO_TRY_CUDA(launch_mask_spectrum(up, g * p, N, C2, h->d_tw, L.big, L.spec, st));
+          LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, g * p, NE, C2, twe, L.mid, st));
+          LITHO_TRY_CUDA(launch_band_rows_real(L.mid, g * p, NE, C2, lp_scale, twe, L.ic, st));
+          up = L.ic;
+        }
+      }
+      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, p * K, NE, C, twe, L.t1, st, g));
+      LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, h->d_lambda + size_t(f0) * K, K, C, up, twe, L.u, g * p, p, st));
+      LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
+                                     twe, L.sk, g * p * K, p * K, st));
       k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, p * K, size_t(C) * C, L.s, f0 > f_first ? 1 : 0);
       LITHO_TRY_CUDA(cudaGetLastError());
     }

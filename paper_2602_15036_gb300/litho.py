@@ -87,8 +87,8 @@ _SIGS = {
     "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
     "litho_intensity_vjp_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
-    "litho_intensity_vjp": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p, c_void_p, c_void_p,
-                                    c_size_t, c_void_p]),
+    "litho_intensity_vjp": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_int, c_void_p, c_void_p,
+                                    c_void_p, c_size_t, c_void_p]),
     "litho_ai_inputs_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t)]),
     "litho_ai_inputs": (c_int, [c_void_p, c_void_p, c_int, c_double, c_int, c_int, c_void_p, c_void_p, c_size_t,
                                 c_void_p]),
@@ -382,7 +382,8 @@ def litho_contours(iblur, threshold=0.3, capacity=None, with_cells=True, stream=
     return seg[:kept], (cell[:kept] if cell is not None else None), st
 
 
-def litho_intensity_vjp(kern: Kernels, mask, upstream=None, f_first=0, f_count=None, dose=1.0, stream=None):
+def litho_intensity_vjp(kern: Kernels, mask, upstream=None, f_first=0, f_count=None, dose=1.0, precision="fft32",
+                        stream=None):
     """mask: CUDA float32 [b][n][n]; upstream: CUDA float32 [b][n_focus][n][n] or None (ones) ->
     dm [b][n][n] = sum over planes [f_first, f_first + f_count) of J_f^T upstream_f."""
     import torch
@@ -392,7 +393,8 @@ def litho_intensity_vjp(kern: Kernels, mask, upstream=None, f_first=0, f_count=N
     _check(lib().litho_intensity_vjp_workspace_size(kern.handle, b, byref(full), byref(mn)))
     ws = torch.empty(full.value, dtype=torch.uint8, device=mask.device)
     dm = torch.empty_like(mask)
-    _check(lib().litho_intensity_vjp(kern.handle, c_void_p(mask.data_ptr()), b, dose, f_first, f_count,
+    _check(lib().litho_intensity_vjp(kern.handle, c_void_p(mask.data_ptr()), b, dose, prec_code(precision), f_first,
+                                     f_count,
                                      c_void_p(upstream.data_ptr()) if upstream is not None else None,
                                      c_void_p(dm.data_ptr()), c_void_p(ws.data_ptr()), ws.numel(),
                                      _stream_ptr(stream)))

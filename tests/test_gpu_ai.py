@@ -23,16 +23,20 @@ def _setup(n=256, focus=(0.0, 50.0), k=8, b=2):
     return lam, phi, targets
 
 
-def test_intensity_vjp_matches_oracle(litho_lib, cuda):
+@pytest.mark.parametrize("precision", ["fft32", "fft32/coarse"])
+def test_intensity_vjp_matches_oracle(litho_lib, cuda, precision):
     import torch
     L = litho_lib
     n = 256
     lam, phi, targets = _setup(n)
     kern = L.litho_upload_kernels(n, 8.0, lam, phi)
+    if precision.endswith("/coarse"):
+        assert 0 < kern.grid(precision) < n
     up = synth.random_field((2, 2, n, n), seed=7).astype(np.float32)
     dm = L.litho_intensity_vjp(kern, torch.from_numpy(targets).to(cuda), torch.from_numpy(up).to(cuda),
-                               dose=1.3).cpu().numpy()
-    ones = L.litho_intensity_vjp(kern, torch.from_numpy(targets).to(cuda), None, f_first=1, f_count=1).cpu().numpy()
+                               dose=1.3, precision=precision).cpu().numpy()
+    ones = L.litho_intensity_vjp(kern, torch.from_numpy(targets).to(cuda), None, f_first=1, f_count=1,
+                                 precision=precision).cpu().numpy()
     for c in range(2):
         m = targets[c].astype(np.float64)
         ref = OIL.intensity_vjp(m, list(zip(lam, phi)), [up[c, 0].astype(np.float64), up[c, 1].astype(np.float64)],
