@@ -582,8 +582,11 @@ def run_contour(args):
     stream = torch.cuda.current_stream()
     _, iblur, _ = P.litho_aerial_resist(kern, torch.from_numpy(masks_np).to(ctx.dev), precision=HEADLINE,
                                         sigma_nm=SIGMA_NM, threshold=THRESH, stream=stream)
-    pts = [torch.from_numpy(synth.edge_sites(m).astype(np.float32)).to(ctx.dev) for m in masks_np]
-    n_pts = sum(int(p.shape[0]) for p in pts)
+    pts_np = [synth.edge_sites(m).astype(np.float32) for m in masks_np]
+    n_pts = sum(len(p) for p in pts_np)
+    pts = torch.from_numpy(np.concatenate(pts_np)).to(ctx.dev)          # all clips' edge sites
+    pt_start = torch.from_numpy(np.concatenate([[0], np.cumsum([len(p) for p in pts_np])]).astype(np.int64)).to(
+        ctx.dev)
     planes = clips * F
     ws = torch.empty(L.contours_workspace_size(planes, N), dtype=torch.uint8, device=ctx.dev)
     starts = torch.empty(planes + 1, dtype=torch.int64, device=ctx.dev)
@@ -591,15 +594,14 @@ def run_contour(args):
     capacity = int(st0[-1]) + 1024
     seg = torch.empty((capacity, 4), dtype=torch.float32, device=ctx.dev)
     cell = torch.empty(capacity, dtype=torch.int32, device=ctx.dev)
-    epe = [torch.empty((F, int(p.shape[0])), dtype=torch.float32, device=ctx.dev) for p in pts]
-    avg = [torch.empty(int(p.shape[0]), dtype=torch.float32, device=ctx.dev) for p in pts]
-    eff = [torch.empty(int(p.shape[0]), dtype=torch.float32, device=ctx.dev) for p in pts]
+    epe = torch.empty((F, n_pts), dtype=torch.float32, device=ctx.dev)
+    avg = torch.empty(n_pts, dtype=torch.float32, device=ctx.dev)
+    eff = torch.empty(n_pts, dtype=torch.float32, device=ctx.dev)
 
     def step():
         L.contours_into(iblur, planes, N, THRESH, seg, cell, capacity, starts, ws, stream)
-        for c in range(clips):
-            P.litho_epe(iblur[c], pts[c], PIXEL, THRESH, out=epe[c], stream=stream)
-            L.epe_through_focus_into(epe[c], 1, 2, 0, -1.0, 1.0, avg[c], eff[c], stream)
+        P.litho_epe_batch(iblur, pts, pt_start, PIXEL, THRESH, out=epe, stream=stream)
+        L.epe_through_focus_into(epe, 1, 2, 0, -1.0, 1.0, avg, eff, stream)
 
     L.litho_profile_enable(True)
     L.litho_profile_reset()

@@ -346,6 +346,18 @@ litho_status litho_contours(const float* iblur_dev, int planes, int n, double th
 litho_status litho_epe(const float* iblur_dev, int planes, int n, double pixel_nm, double threshold,
                        const float* points_dev, int m, float* epe_dev, void* stream);
 
+/* litho_epe for a batch of clips in one launch: the points of clip c are
+ * points[start[c] .. start[c+1]) (start_dev: clips + 1 int64 on the device,
+ * start[0] = 0, non-decreasing, start[clips] = m_total; empty clips allowed)
+ * and are evaluated on that clip's planes iblur[c][0 .. planes) (f32
+ * [clips][planes][n][n]); epe[p][k] for all m_total points, plane-major, so
+ * that one litho_epe_through_focus call covers the batch.  Each value equals
+ * litho_epe on the clip alone.  A start array that breaks these rules gives
+ * wrong values but no access outside the buffers.  Asynchronous. */
+litho_status litho_epe_batch(const float* iblur_dev, int clips, int planes, int n, double pixel_nm, double threshold,
+                             const float* points_dev, const int64_t* start_dev, int64_t m_total, float* epe_dev,
+                             void* stream);
+
 /* Eqs. (7)-(8) from epe[planes][m]: avg[k] = mean of the on-focus plane f0 and
  * the defocused planes fp and fn; eff[k] = e0 - tol_pos if e0 > tol_pos,
  * e0 - tol_neg if e0 < tol_neg, else avg[k] (e0 = epe[f0][k]; a value equal to

@@ -728,6 +728,23 @@ litho_status litho_epe(const float* iblur_dev, int planes, int n, double pixel_n
   return LITHO_OK;
 }
 
+litho_status litho_epe_batch(const float* iblur_dev, int clips, int planes, int n, double pixel_nm, double threshold,
+                             const float* points_dev, const int64_t* start_dev, int64_t m_total, float* epe_dev,
+                             void* stream) {
+  LITHO_REQUIRE(iblur_dev && points_dev && start_dev && epe_dev, "null argument");
+  LITHO_REQUIRE(clips >= 1 && planes >= 1 && n >= 2 && m_total >= 0, "clips >= 1, planes >= 1, n >= 2, m_total >= 0");
+  LITHO_REQUIRE(pixel_nm > 0 && std::isfinite(threshold), "pixel_nm > 0 and a finite threshold required");
+  LITHO_REQUIRE((reinterpret_cast<uintptr_t>(points_dev) & 7) == 0 && (reinterpret_cast<uintptr_t>(start_dev) & 7) == 0,
+                "points_dev and start_dev must be 8-byte aligned");
+  if (m_total == 0) return LITHO_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ProfScope ps(kStageEpe, st, 1);
+  LITHO_TRY_CUDA(launch_epe_batch(iblur_dev, clips, planes, n, float(pixel_nm), float(threshold),
+                                  reinterpret_cast<const float2*>(points_dev),
+                                  reinterpret_cast<const long long*>(start_dev), m_total, epe_dev, st));
+  return LITHO_OK;
+}
+
 litho_status litho_epe_through_focus(const float* epe_dev, int planes, int m, int f0, int fp, int fn, double tol_neg,
                                      double tol_pos, float* avg_dev, float* eff_dev, void* stream) {
   LITHO_REQUIRE(epe_dev && (avg_dev || eff_dev), "null argument");

@@ -423,14 +423,8 @@ __device__ __forceinline__ float bilin(float a, float b, float c, float d, float
   return (1.f - fy) * ((1.f - fx) * a + fx * b) + fy * ((1.f - fx) * c + fx * d);
 }
 
-// One thread per control point, every plane in turn.
-__global__ void k_epe(const float* __restrict__ img, int planes, int n, int m, float inv_pixel, float thr,
-                      const float2* __restrict__ pts, float* __restrict__ epe) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m) return;
-  const float2 r = pts[k];
-  for (int p = 0; p < planes; ++p) {
-  const float* I = img + (size_t)p * n * n;
+// Eq. (6) at point r (pixels) of plane I.
+__device__ __forceinline__ float epe_at(const float* __restrict__ I, int n, float2 r, float inv_pixel, float thr) {
   const float fj = floorf(r.x), fi = floorf(r.y);
   const float fx = r.x - fj, fy = r.y - fi;
   auto wrap = [&](int v) { return ((v % n) + n) % n; };
@@ -449,8 +443,37 @@ __global__ void k_epe(const float* __restrict__ img, int planes, int n, int m, f
   const float gy = bilin(0.5f * (v[2][1] - v[0][1]), 0.5f * (v[2][2] - v[0][2]), 0.5f * (v[3][1] - v[1][1]),
                          0.5f * (v[3][2] - v[1][2]), fx, fy);
   const float g = sqrtf(gx * gx + gy * gy) * inv_pixel;
-  epe[(size_t)p * m + k] = g > 0.f ? -(e - thr) / g : __int_as_float(0x7fc00000);
+  return g > 0.f ? -(e - thr) / g : __int_as_float(0x7fc00000);
+}
+
+// One thread per control point, every plane in turn.
+__global__ void k_epe(const float* __restrict__ img, int planes, int n, int m, float inv_pixel, float thr,
+                      const float2* __restrict__ pts, float* __restrict__ epe) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const float2 r = pts[k];
+  for (int p = 0; p < planes; ++p) epe[(size_t)p * m + k] = epe_at(img + (size_t)p * n * n, n, r, inv_pixel, thr);
+}
+
+// All clips' points in one launch: point k belongs to the last clip c with
+// start[c] <= k (empty clips are passed over), whose planes follow one another
+// in img.  Whatever start holds, c stays in [0, clips).
+__global__ void k_epe_batch(const float* __restrict__ img, int clips, int planes, int n, long long m, float inv_pixel,
+                            float thr, const float2* __restrict__ pts, const long long* __restrict__ start,
+                            float* __restrict__ epe) {
+  const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  int lo = 0, hi = clips - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(start + mid) <= k)
+      lo = mid;
+    else
+      hi = mid - 1;
   }
+  const float2 r = pts[k];
+  const float* I = img + (size_t)lo * planes * n * n;
+  for (int p = 0; p < planes; ++p) epe[(size_t)p * m + k] = epe_at(I + (size_t)p * n * n, n, r, inv_pixel, thr);
 }
 
 __global__ void k_epe_focus(const float* __restrict__ epe, int m, int f0, int fp, int fn, float tol_neg,
@@ -505,6 +528,13 @@ cudaError_t launch_contours(const float* img, int planes, int n, float thr, floa
 cudaError_t launch_epe(const float* img, int planes, int n, float pixel_nm, float thr, const float2* pts, int m,
                        float* epe, cudaStream_t st) {
   k_epe<<<(m + 255) / 256, 256, 0, st>>>(img, planes, n, m, 1.0f / pixel_nm, thr, pts, epe);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epe_batch(const float* img, int clips, int planes, int n, float pixel_nm, float thr,
+                             const float2* pts, const long long* start, long long m, float* epe, cudaStream_t st) {
+  k_epe_batch<<<unsigned((m + 255) / 256), 256, 0, st>>>(img, clips, planes, n, m, 1.0f / pixel_nm, thr, pts, start,
+                                                        epe);
   return cudaGetLastError();
 }
 

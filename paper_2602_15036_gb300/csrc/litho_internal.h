@@ -189,6 +189,9 @@ cudaError_t launch_contours(const float* img, int planes, int n, float thr, floa
                             long long capacity, long long* plane_start, void* ws, cudaStream_t st);
 cudaError_t launch_epe(const float* img, int planes, int n, float pixel_nm, float thr, const float2* pts, int m,
                        float* epe, cudaStream_t st);
+// Eq. (6) for all clips' points in one launch (points of clip c at [start[c], start[c+1])).
+cudaError_t launch_epe_batch(const float* img, int clips, int planes, int n, float pixel_nm, float thr,
+                             const float2* pts, const long long* start, long long m, float* epe, cudaStream_t st);
 cudaError_t launch_epe_focus(const float* epe, int m, int f0, int fp, int fn, float tol_neg, float tol_pos,
                              float* avg, float* eff, cudaStream_t st);
 

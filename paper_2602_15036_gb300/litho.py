@@ -101,6 +101,8 @@ _SIGS = {
     "litho_contours": (c_int, [c_void_p, c_int, c_int, c_double, c_void_p, c_void_p, ctypes.c_int64, c_void_p,
                                c_void_p, c_size_t, c_void_p]),
     "litho_epe": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_void_p, c_int, c_void_p, c_void_p]),
+    "litho_epe_batch": (c_int, [c_void_p, c_int, c_int, c_int, c_double, c_double, c_void_p, c_void_p, ctypes.c_int64,
+                                c_void_p, c_void_p]),
     "litho_epe_through_focus": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_double, c_double, c_void_p,
                                         c_void_p, c_void_p]),
     "litho_ilt_workspace_size": (c_int, [c_void_p, c_int, POINTER(c_size_t), POINTER(c_size_t)]),
@@ -506,6 +508,22 @@ def litho_epe(iblur, points, pixel_nm, threshold=0.3, out=None, stream=None):
         out = torch.empty((planes, m), dtype=torch.float32, device=iblur.device)
     _check(lib().litho_epe(c_void_p(iblur.data_ptr()), planes, n, pixel_nm, threshold, c_void_p(points.data_ptr()),
                            m, c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def litho_epe_batch(iblur, points, start, pixel_nm, threshold=0.3, out=None, stream=None):
+    """iblur: CUDA float32 [clips][planes][n][n]; points: CUDA float32 [M][2] (all clips' points);
+    start: CUDA int64 [clips + 1] (clip c's points at start[c] .. start[c+1]) -> EPE [planes][M] in nm."""
+    import torch
+    clips, planes, n = iblur.shape[0], iblur.shape[1], iblur.shape[-1]
+    m = points.shape[0]
+    assert points.is_cuda and points.dtype == torch.float32 and points.is_contiguous()
+    assert start.is_cuda and start.dtype == torch.int64 and start.numel() == clips + 1
+    if out is None:
+        out = torch.empty((planes, m), dtype=torch.float32, device=iblur.device)
+    _check(lib().litho_epe_batch(c_void_p(iblur.data_ptr()), clips, planes, n, pixel_nm, threshold,
+                                 c_void_p(points.data_ptr()), c_void_p(start.data_ptr()), m, c_void_p(out.data_ptr()),
+                                 _stream_ptr(stream)))
     return out
 
 

@@ -140,3 +140,23 @@ def test_epe_flat_image_is_nan_and_errors(litho_lib, cuda):
     with pytest.raises(L.LithoError) as err:
         L.litho_epe_through_focus(e, 0, 1, 2, -1.0, 1.0)           # plane 2 does not exist
     assert err.value.status == L.EINVAL
+
+
+def test_epe_batch_equals_per_clip_calls(litho_lib, cuda):
+    """One launch over several clips' points (one clip with no points) gives
+    each clip's EPE bit-identical to litho_epe on that clip alone."""
+    import torch
+    L = litho_lib
+    n, pixel, thr, planes = 128, 8.0, 0.5, 3
+    imgs = np.stack([np.stack([_blobs(n, 40 + 3 * c + p, count=12) for p in range(planes)]) for c in range(4)])
+    pts = [synth.edge_sites(imgs[c, 0] >= thr).astype(np.float32) for c in range(4)]
+    pts[2] = np.zeros((0, 2), np.float32)
+    start = np.concatenate([[0], np.cumsum([len(p) for p in pts])]).astype(np.int64)
+    d_img = torch.from_numpy(imgs).to(cuda)
+    d_pts = torch.from_numpy(np.concatenate(pts)).to(cuda)
+    got = L.litho_epe_batch(d_img, d_pts, torch.from_numpy(start).to(cuda), pixel, thr).cpu().numpy()
+    for c in range(4):
+        if len(pts[c]) == 0:
+            continue
+        one = L.litho_epe(d_img[c], torch.from_numpy(pts[c]).to(cuda), pixel, thr).cpu().numpy()
+        np.testing.assert_array_equal(got[:, start[c]:start[c + 1]], one)
