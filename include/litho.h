@@ -10,8 +10,14 @@
  *   - marching-squares contours of the resist image and the edge-placement
  *     error at target control points, through focus (Section II.D, Eqs. (6)-(8));
  *   - the ILT mask gradient through the resist and imaging (the adjoint of the
- *     above; pixel-based ILT is the paper's Section I prior art);
+ *     above; pixel-based ILT is the paper's Section I prior art), and the
+ *     intensity vector-Jacobian product on its own;
+ *   - the AI initialiser's input channels and print-consistency images
+ *     (Eqs. (9), (15)-(17));
  *   - a continuous-batching request server over all of it.
+ * The image, its resist, the ILT gradient, the VJP and the AI channels can be
+ * evaluated on a coarse grid of at least 2C points (LITHO_GRID_COARSE) with
+ * an exact Fourier interpolation to N: the same results up to FP32 rounding.
  *
  * Conventions shared by every entry point:
  *   - Grids are N x N, row-major, x fastest; pixel size in nm at the wafer.
