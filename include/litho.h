@@ -231,7 +231,10 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
  * before any stream capture.  All calls share the one array and each call
  * overwrites what the previous one left: calls that can run at the same time
  * on the GPU (different streams, or different host threads) race and corrupt
- * each other's results; serialise them on one stream.  Asynchronous on
+ * each other's results; serialise them on one stream.  The kernel set's
+ * device must be the current device (else EINVAL: the scratch address is
+ * per device).  mask_dev and intensity_dev must be 16-byte aligned and the
+ * dose finite (else EINVAL), as for litho_aerial.  Asynchronous on
  * `stream`. */
 litho_status litho_aerial_noalloc(const litho_kernels* h, const float* mask_dev, int b, double dose,
                                   float* intensity_dev, void* stream);

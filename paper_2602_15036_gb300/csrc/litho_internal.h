@@ -148,7 +148,7 @@ cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
                               long long img_plane_stride, cudaStream_t st, int lam_period = 0);
 
-// A device-side delay of about `ms` milliseconds on `st` (noalloc.cu): one
+// A device-side delay of about `ms` milliseconds on `st` (util.cu): one
 // thread spinning on the SM clock for a fixed number of cycles, which always
 // ends.  The slow request of the serving tests.
 cudaError_t launch_delay(cudaStream_t st, double ms);

@@ -15,6 +15,7 @@
 // library is loaded reserves kScratchBytes for it until the process exits.
 // Host code cannot use the symbol's name as a device address; the device
 // address is looked up once per device with cudaGetSymbolAddress.
+#include <cmath>
 #include <mutex>
 
 #include "litho_internal.h"
@@ -63,30 +64,6 @@ litho_status scratch_address(void** out) {
 
 using namespace litho;
 
-namespace litho {
-
-namespace {
-
-// One thread spinning on the SM clock for a fixed number of cycles: it always
-// ends (no flag or peer is waited on).
-__global__ void k_delay(long long cycles) {
-  const long long t0 = clock64();
-  while (clock64() - t0 < cycles) __nanosleep(1000);
-}
-
-}  // namespace
-
-cudaError_t launch_delay(cudaStream_t st, double ms) {
-  int dev = 0, khz = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
-  if (e != cudaSuccess) return e;
-  k_delay<<<1, 1, 0, st>>>((long long)(ms * double(khz > 0 ? khz : 2000000)));
-  return cudaGetLastError();
-}
-
-}  // namespace litho
-
 extern "C" {
 
 size_t litho_aerial_noalloc_max_bytes(void) { return kScratchBytes; }
@@ -99,6 +76,24 @@ litho_status litho_aerial_noalloc(const litho_kernels* h, const float* mask_dev,
   }
   if (b < 1) {
     set_error("b must be >= 1");
+    return LITHO_EINVAL;
+  }
+  if (!std::isfinite(dose)) {
+    set_error("dose must be finite");
+    return LITHO_EINVAL;
+  }
+  if ((reinterpret_cast<uintptr_t>(mask_dev) & 15) != 0 || (reinterpret_cast<uintptr_t>(intensity_dev) & 15) != 0) {
+    set_error("mask and intensity must be 16-byte aligned");
+    return LITHO_EINVAL;
+  }
+  // The kernel set's tables live on h->device and the scratch address is
+  // looked up on the current device: both must be the same GPU.
+  int cur = 0;
+  LITHO_TRY_CUDA(cudaGetDevice(&cur));
+  if (cur != h->device) {
+    set_error("litho_aerial_noalloc: the current device is %d but the kernel set lives on device %d; make that "
+              "device current first",
+              cur, h->device);
     return LITHO_EINVAL;
   }
   const size_t need = clip_bytes(h);

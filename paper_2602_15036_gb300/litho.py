@@ -327,7 +327,18 @@ def litho_aerial_noalloc(kern: Kernels, mask, out, dose=1.0, stream=None):
     array stands in for the workspace, so `out` must be preallocated
     ([b][F][n][n] float32 on the device).  Calls that may overlap on the GPU
     race on that array; keep them on one stream."""
-    assert mask.is_cuda and out.is_cuda and mask.is_contiguous() and out.is_contiguous()
+    import torch
+    b = mask.shape[0]
+    n, nf = kern.n, kern.n_focus
+    if mask.dtype != torch.float32 or out.dtype != torch.float32:
+        raise ValueError("mask and out must be float32")
+    if tuple(mask.shape) != (b, n, n) or tuple(out.shape) != (b, nf, n, n):
+        raise ValueError(f"need mask [b][{n}][{n}] and out [b][{nf}][{n}][{n}]; got {tuple(mask.shape)} and "
+                         f"{tuple(out.shape)}")
+    if not (mask.is_cuda and out.is_cuda and mask.device == out.device):
+        raise ValueError("mask and out must be on the same CUDA device")
+    if not (mask.is_contiguous() and out.is_contiguous()):
+        raise ValueError("mask and out must be contiguous")
     _check(lib().litho_aerial_noalloc(kern.handle, c_void_p(mask.data_ptr()), mask.shape[0], dose,
                                       c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out

@@ -89,3 +89,72 @@ def test_trace_equals_counted_pupil_overlaps_and_kernels_orthonormal():
     gram = p[:r].conj() @ p[:r].T
     # the weakest modes carry rounding of order eps * lam_1 / lam_k
     assert np.abs(gram - np.eye(r)).max() < 1e-10
+
+
+# ---- the defocus phase, pinned by Talbot self-imaging ------------------------------------------------
+#
+# A grating of period p lit by one on-axis plane wave, with only its orders 0 and +-1
+# passing the pupil, images itself again after a propagation distance z_T at which the
+# first orders have fallen one full cycle behind the zeroth: in a medium of index n the
+# axial wavenumbers are n/lambda (order 0) and sqrt((n/lambda)^2 - 1/p^2) (orders +-1),
+# so z_T = 1 / (n/lambda - sqrt((n/lambda)^2 - 1/p^2)) (the non-paraxial Talbot length).
+# Half-way, the first orders are in antiphase, which is the image shifted by p/2.  These
+# are properties of wave propagation, not of any one way of writing the pupil: a
+# paraxial defocus, a wrong medium index or a missing factor moves z_T and fails them.
+
+ON_AXIS = O.Optics(193.0, 1.35, 1.44, O.ANNULAR, 21, 0.0, 0.0)   # sigma_in = sigma_out = 0: one point
+
+
+def _talbot_length(opt, period_nm):
+    kn = opt.n_medium / opt.wavelength_nm
+    return 1.0 / (kn - np.sqrt(kn * kn - 1.0 / period_nm ** 2))
+
+
+def _line_grating(n, period, width):
+    m = np.zeros((n, n))
+    m[:, (np.arange(n) % period) < width] = 1.0
+    return m
+
+
+@pytest.mark.parametrize("n,period,width", [(208, 26, 10), (256, 32, 11)])
+def test_defocus_phase_reproduces_the_talbot_self_image(n, period, width):
+    from oracle import imaging as I
+    pix = 8.0
+    opt = ON_AXIS
+    sx, sy, _ = O.source_points(opt)
+    assert len(sx) == 1 and sx[0] == 0.0 and sy[0] == 0.0
+    fna = opt.na / opt.wavelength_nm
+    # orders +-1 pass the pupil, +-2 do not
+    assert 1.0 / (period * pix) < fna < 2.0 / (period * pix)
+    m = _line_grating(n, period, width)
+    zt = _talbot_length(opt, period * pix)
+    i0 = I.abbe_image(m, opt, pix, 0.0)
+    assert i0.max() - i0.min() > 0.1                               # a real pattern, not a flat field
+    i_t = I.abbe_image(m, opt, pix, zt)
+    i_h = I.abbe_image(m, opt, pix, zt / 2)
+    i_q = I.abbe_image(m, opt, pix, zt / 4)
+    assert np.abs(i_t - i0).max() < 1e-12
+    assert np.abs(i_h - np.roll(i0, -period // 2, axis=1)).max() < 1e-12
+    assert np.abs(i_q - i0).max() > 1e-2                           # not periodic at a quarter of z_T
+    # the SOCS route (TCC eigen-kernels of Eqs. (2)-(3)) self-images at the same distance
+    lam0, phi0, _ = O.socs_kernels(opt, n, pix, 0.0, 1)
+    lamt, phit, _ = O.socs_kernels(opt, n, pix, zt, 1)
+    assert np.abs(I.socs_image(m, lamt, phit) - I.socs_image(m, lam0, phi0)).max() < 1e-12
+
+
+def test_planted_paraxial_defocus_misses_the_talbot_length(monkeypatch):
+    """A pupil with the paraxial phase -pi lambda z f^2 / n (right sign, right index) puts
+    the self-image at 2 n / (lambda f^2), about 13 % beyond the true z_T at this period."""
+    from oracle import imaging as I
+    n, period, width, pix = 208, 26, 10, 8.0
+    opt = ON_AXIS
+    m = _line_grating(n, period, width)
+    i0 = I.abbe_image(m, opt, pix, 0.0)
+    zt = _talbot_length(opt, period * pix)
+    orig = O.pupil
+
+    def paraxial(fx, fy, o, z):
+        return orig(fx, fy, o, 0.0) * np.exp(-1j * np.pi * o.wavelength_nm * z * (fx * fx + fy * fy) / o.n_medium)
+
+    monkeypatch.setattr(I, "pupil", paraxial)
+    assert np.abs(I.abbe_image(m, opt, pix, zt) - i0).max() > 1e-2

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 import synth
+from oracle import imaging as OI
 from tests.gpu_util import DUV_ANNULAR, DUV_QUAD41, oracle_kernel_set
 
 pytestmark = pytest.mark.gpu
@@ -37,6 +38,12 @@ def test_noalloc_matches_workspace_path_on_consecutive_calls(litho_lib, cuda):
         torch.cuda.synchronize()
         err = (out - ref).abs().max().item()
         assert err <= TOL_FP32, (call, err)
+        got = out.cpu().numpy().astype(np.float64)
+        for i in range(len(masks)):                   # and against the FP64 oracle itself
+            for f in range(lam.shape[0]):
+                want = OI.socs_image(masks[i].astype(np.float64), lam[f], phi[f], 1.2)
+                e = np.abs(got[i, f] - want).max()
+                assert e <= TOL_FP32, (call, i, f, e)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(litho_lib, cuda):
@@ -52,3 +59,20 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(litho_lib, cuda):
     assert e.value.status == L.EINVAL
     assert "fixed scratch array" in str(e.value)
     assert L.litho_aerial_noalloc_max_bytes() == 32 << 20
+
+
+def test_noalloc_checks_its_arguments(litho_lib, cuda):
+    import torch
+    L = litho_lib
+    n, pixel = 64, 8.0
+    lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, [0.0, 40.0], 4)
+    kern = L.litho_upload_kernels(n, pixel, lam, phi)
+    m = torch.zeros((2, n, n), dtype=torch.float32, device=cuda)
+    out = torch.empty((2, 2, n, n), dtype=torch.float32, device=cuda)
+    with pytest.raises(L.LithoError) as e:                       # a NaN dose is refused, as by litho_aerial
+        L.litho_aerial_noalloc(kern, m, out, dose=float("nan"))
+    assert e.value.status == L.EINVAL
+    with pytest.raises(ValueError):                              # an output missing the focus axis
+        L.litho_aerial_noalloc(kern, m, torch.empty((2, n, n), dtype=torch.float32, device=cuda))
+    with pytest.raises(ValueError):
+        L.litho_aerial_noalloc(kern, m.double(), out)
