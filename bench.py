@@ -54,11 +54,35 @@ WORKLOAD = "socs-aerial+resist 2048x2048@8nm quadrupole41 K=24 focus(-50,0,50)"
 METRIC = "aerial-image Mpx/s (2048² clips, K=24) vs plain FFT path at ≤1e-5 err; p99 ms"
 HEADLINE = "fft32/coarse"
 COMPARE = ["fft32", "fp16x3/coarse"]   # the plain FFT path, the split tensor-core path
-ERROR_BOUND = {"fft32": 1e-5, "fft32/coarse": 1e-5, "fp16x3": 1e-5, "fp16x3/coarse": 1e-5, "bf16x3": 5e-5,
-               "bf16x3/coarse": 5e-5, "fp16": 2e-3, "fp16/coarse": 2e-3, "bf16": 4e-3}
+ERROR_BOUND = {"fft32": 1e-5, "fft32/coarse": 1e-5, "fp16x3": 1e-5, "fp16x3/coarse": 1e-5, "bf16x3": 1e-5,
+               "bf16x3/coarse": 1e-5, "fp16": 2e-3, "fp16/coarse": 2e-3, "bf16": 4e-3}
 
-SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-ALU_PEAK_TFLOPS = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP32_LANES_PER_SM = 128
+
+
+def sm_count() -> int:
+    """Streaming multiprocessors of the device in use (152 on a GB300)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+    except Exception:
+        pass
+    return 152
+
+
+def sm_max_mhz() -> float:
+    p, _ = _peaks()
+    return float(p.get("sm_max_mhz") or 2070.0)
+
+
+def alu_peak_tflops() -> float:
+    """FP32 CUDA-core peak: SMs x 128 FP32 lanes x 2 flops (FMA) x maximum SM clock."""
+    return sm_count() * FP32_LANES_PER_SM * 2 * sm_max_mhz() * 1e6 / 1e12
+
+
+def alu_peak_source() -> str:
+    return f"derived: {sm_count()} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flops x {sm_max_mhz():.0f} MHz"
 
 
 def _peaks():
@@ -180,9 +204,12 @@ def stage_models(prec: str, clips: int, n: int, crop: int, n_focus: int, k_eff: 
         "stage2_fft": (clips * fk * ne * (fft(ne) + 4.0 * ne), t1_bytes + planes * ne * ne * 4.0),
         "stage1_gemm_operands": (clips * fk * (crop * fft(ne) + 6.0 * crop * crop),
                                  launches * phi_bytes + clips * crop * crop * 8.0 +
-                                 clips * fk * ne * crop * (8.0 if split else 4.0)),
-        "stage2_gemm": (clips * fk * 8.0 * ne * ne * crop * (3 if split else 1),
-                        clips * fk * ne * crop * (8.0 if split else 4.0) + planes * ne * ne * 4.0),
+                                 clips * fk * ne * crop * (12.0 if split else 4.0)),
+        # executed tensor-core flops: 2 M N K per real product; the split modes take Gauss's three
+        # real products per complex multiply-add (6 M N K), each as three 16-bit products; the plain
+        # modes take four (8 M N K)
+        "stage2_gemm": (clips * fk * ne * ne * crop * (6.0 * 3 if split else 8.0),
+                        clips * fk * ne * crop * (12.0 if split else 4.0) + planes * ne * ne * 4.0),
         "resist": (planes * n * n * 4.0 * resist_taps, planes * n * n * 9.0),
     }
     if coarse:
@@ -288,7 +315,7 @@ def rooflines(prof: dict, steps: int, models: dict, peaks) -> dict:
         flops, nbytes = models[stage]
         sec = ms / steps * 1e-3
         tensor = stage == "stage2_gemm"
-        fpeak = peaks["bf16_tflops_sustained"] if tensor else ALU_PEAK_TFLOPS
+        fpeak = peaks["bf16_tflops_sustained"] if tensor else alu_peak_tflops()
         alu = {"bound": "tensor" if tensor else "alu", "achieved": flops / sec / 1e12, "peak": fpeak,
                "unit": "TFLOP/s"}
         mem = {"bound": "hbm", "achieved": nbytes / sec / 1e9, "peak": hbm, "unit": "GB/s"}
@@ -323,10 +350,113 @@ def _oracle_sample(seed: int, focus_planes):
     return time.perf_counter() - t0
 
 
+def host_facts() -> dict:
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+_SHARED = {}
+
+
+def _oracle_worker_init(names, shapes):
+    """Maps the parent's shared arrays (mask, lambdas, kernels, output slots) in a worker."""
+    from multiprocessing import shared_memory
+    for key, name in names.items():
+        shm = shared_memory.SharedMemory(name=name)
+        dt = np.float64 if key in ("m", "lam", "out") else np.complex128
+        _SHARED[key] = (shm, np.ndarray(shapes[key], dtype=dt, buffer=shm.buf))
+
+
+def _oracle_partial(task):
+    """One worker's share of the oracle's SOCS sum: the oracle's own socs_image over kernels
+    k0..k1 of focus plane f, written to output slot `slot`."""
+    from oracle import imaging as OI
+    f, k0, k1, slot = task
+    m, lam, phi, out = (_SHARED[k][1] for k in ("m", "lam", "phi", "out"))
+    out[slot] = OI.socs_image(m, lam[f, k0:k1], phi[f, k0:k1])
+    return slot
+
+
+def _oracle_all_cores(seed: int, focus_planes, workers: int):
+    """The same oracle work as _oracle_sample on all host cores: the SOCS sums of every focus
+    plane split over spawned processes by kernels (inputs and partial images in shared
+    memory, one numpy thread each), then the resist on each plane.  Returns seconds of
+    imaging + resist (the set-up of kernels and workers is not timed, as in _oracle_sample)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    from oracle import optics as OO
+    from oracle import resist as ORR
+    oo = OO.Optics(193.0, 1.35, 1.44, OO.QUADRUPOLE, 41, pole_sigma=0.8, pole_radius=0.1)
+    kern = [OO.socs_kernels(oo, N, PIXEL, z, K)[:2] for z in focus_planes]
+    F = len(focus_planes)
+    per = max(1, -(-K * F // workers))
+    tasks = []
+    for f in range(F):
+        for k0 in range(0, K, per):
+            tasks.append((f, k0, min(K, k0 + per), len(tasks)))
+    arrays = {"m": synth.manhattan_mask(N, seed=seed).astype(np.float64),
+              "lam": np.stack([k[0] for k in kern]), "phi": np.stack([k[1] for k in kern]),
+              "out": np.zeros((len(tasks), N, N))}
+    shms, names, shapes = [], {}, {}
+    try:
+        for key, arr in arrays.items():
+            shm = shared_memory.SharedMemory(create=True, size=arr.nbytes)
+            shms.append(shm)
+            np.ndarray(arr.shape, dtype=arr.dtype, buffer=shm.buf)[...] = arr
+            names[key], shapes[key] = shm.name, arr.shape
+        out = np.ndarray(shapes["out"], dtype=np.float64, buffer=shms[-1].buf)
+        env_before = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in env_before:
+            os.environ[v] = "1"
+        try:
+            with mp.get_context("spawn").Pool(workers, initializer=_oracle_worker_init,
+                                              initargs=(names, shapes)) as pool:
+                pool.map(_oracle_partial, tasks[:workers])          # workers started and warm
+                t0 = time.perf_counter()
+                pool.map(_oracle_partial, tasks)
+                for f in range(F):
+                    img = sum(out[t[3]] for t in tasks if t[0] == f)
+                    ORR.printed(ORR.blur(img, SIGMA_NM, PIXEL), THRESH)
+                return time.perf_counter() - t0
+        finally:
+            for v, old in env_before.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+    finally:
+        for shm in shms:
+            shm.close()
+            shm.unlink()
+
+
 def cpu_baseline():
+    host = host_facts()
     t = _oracle_sample(1234, FOCUS)
-    return {"value": N * N / t / 1e6, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
-            "sample": f"1 of 64 clips (seed 1234), all 3 focus planes x 24 kernels + resist; {t:.1f} s"}
+    out = {"value": N * N / t / 1e6, "unit": "Mpx/s", "cores": 1, "kind": "oracle",
+           "sample": f"1 of 64 clips (seed 1234), all 3 focus planes x 24 kernels + resist; {t:.1f} s",
+           "host": host}
+    workers = max(1, int(host["nproc"] or 1))
+    try:
+        ta = _oracle_all_cores(1234, FOCUS, workers)
+        out["all_cores"] = {"value": N * N / ta / 1e6, "unit": "Mpx/s", "cores": workers, "kind": "oracle",
+                            "sample": f"the same clip, the 72 (focus, kernel) SOCS terms split over {workers} "
+                                      f"spawned processes, then the resist; {ta:.2f} s"}
+    except Exception as e:  # a baseline, not a target: report why it is missing
+        out["all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
+    return out
 
 
 def run_reference(args):
@@ -405,10 +535,9 @@ def time_steps(ctx, step, steps, warmup, stream, sample_clocks=False):
     return [a.elapsed_time(b) for a, b in ev], (clk.summary() if clk else None)
 
 
-def run_aerial(args):
+def run_aerial(args, ctx):
     import paper_2602_15036_gb300 as P
     from paper_2602_15036_gb300 import litho as L
-    ctx = Ctx(args)
     torch = ctx.torch
     clips = args.clips
     kern = P.litho_make_kernels(P.make_optics(**OPTICS), N, PIXEL, FOCUS, K)
@@ -450,6 +579,14 @@ def run_aerial(args):
                              launches=sum(v[1] for v in prof.values()))
 
     head = results[args.precision]
+    # latency distribution of the headline step: >= 100 timed repetitions, one event pair each
+    lat_reps = max(100, args.steps)
+
+    def head_step():
+        P.litho_aerial_resist(kern, masks, precision=args.precision, sigma_nm=SIGMA_NM, threshold=THRESH, out=img,
+                              iblur=iblur, printed=printed, workspace=ws, stream=stream)
+
+    lat_ms, lat_clk = time_steps(ctx, head_step, lat_reps, 0, stream, sample_clocks=True)
     # end to end through the host-buffer C-ABI call: pinned masks in, printed bytes out
     mask_host = torch.from_numpy(masks_np).pin_memory()
     printed_host = torch.empty((clips, F, N, N), dtype=torch.uint8).pin_memory()
@@ -480,8 +617,7 @@ def run_aerial(args):
     roof["kernel"] = dominant[0]
     roof["traffic"], roof["traffic_source"] = measured_traffic(dominant[0], args.precision, clips,
                                                                roof["launches_per_step"])
-    roof["peak_source"] = (f"{peak_src} HBM copy bandwidth" if roof["bound"] == "hbm" else
-                           "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz")
+    roof["peak_source"] = (f"{peak_src} HBM copy bandwidth" if roof["bound"] == "hbm" else alu_peak_source())
     plain = results.get("fft32")
     line = {"metric": METRIC, "value": head["value"], "unit": "Mpx/s", "n_gpus": ctx.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head["total_ms"] / args.steps, "higher_is_better": True,
@@ -490,7 +626,8 @@ def run_aerial(args):
                        "error_bound_abs": ERROR_BOUND.get(args.precision),
                        "parallelism": f"replicas x{ctx.world} (clips sharded, no collective)",
                        "l2": "inputs larger than L2 (1.07 GB masks, 3.2 GB images per step); no flush"},
-            "p50_ms": statistics.median(head["step_ms"]), "p99_ms": float(np.percentile(head["step_ms"], 99)),
+            "p50_ms": statistics.median(lat_ms), "p99_ms": float(np.percentile(lat_ms, 99)),
+            "latency_reps": lat_reps, "latency_clocks": lat_clk,
             "vs_plain_fft": (head["value"] / plain["value"]) if plain else None,
             "paths": {p: {"value": r["value"], "ms_per_step": r["total_ms"] / args.steps,
                           "error_bound_abs": ERROR_BOUND.get(p),
@@ -504,18 +641,15 @@ def run_aerial(args):
             "roofline": roof, "peaks_source": peak_src, "clocks": head["clocks"]}
     if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
-    if ctx.rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
+    return line
 
 
-def run_ilt(args):
+def run_ilt(args, ctx):
     """16 clips of 1024^2, annular 21x21, K=16, 5 focus planes; one step = litho_ilt_grad on all clips
     plus the gradient-descent update theta -= 0.5 g / max|g| (torch, outside the library).  --precision
     fft32/coarse (default) evaluates fields and adjoint on the 512-point coarse grid, fft32 on 1024."""
     import paper_2602_15036_gb300 as P
     from paper_2602_15036_gb300 import litho as L
-    ctx = Ctx(args)
     torch = ctx.torch
     prec = args.precision if args.precision in ("fft32", "fft32/coarse") else "fft32/coarse"
     n, pixel, k, focus, clips = 1024, 8.0, 16, [-60.0, -30.0, 0.0, 30.0, 60.0], 16
@@ -559,21 +693,19 @@ def run_ilt(args):
             "config": {"workload": "ilt 16x1024^2@8nm annular21 K=16 focus(-60..60 step 30)", "clips_per_gpu": clips,
                        "precision": prec, "grid": kern.grid(prec) if prec.endswith("/coarse") else n},
             "loss_first_last": [losses[0], losses[-1]],
+            "loss_curve": {"steps": len(losses), "every": 1, "sum_over_clips": [float(f"{v:.6g}") for v in losses]},
             "stages_ms_per_step": {kk: v[0] / (args.steps + args.warmup) for kk, v in prof.items()},
             "roofline": roof, "stage_rooflines": {kk: {x: v[x] for x in ("bound", "frac")} for kk, v in roofs.items()},
             "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}
-    if ctx.rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
+    return line
 
 
-def run_contour(args):
+def run_contour(args, ctx):
     """Contours and edge placement on the headline's resist images: 64 clips of 2048^2 x 3 focus
     planes (made once, untimed, by litho_aerial_resist); one step = marching squares on every plane
     + Eq. (6) EPE at the edge sites of every clip's target (its mask) on its 3 planes + Eqs. (7)-(8)."""
     import paper_2602_15036_gb300 as P
     from paper_2602_15036_gb300 import litho as L
-    ctx = Ctx(args)
     torch = ctx.torch
     clips = args.clips
     kern = P.litho_make_kernels(P.make_optics(**OPTICS), N, PIXEL, FOCUS, K)
@@ -632,18 +764,15 @@ def run_contour(args):
             "epe_roofline": {"bound": "hbm", "achieved": e_bytes / sec("epe") / 1e9 if sec("epe") else None,
                              "unit": "GB/s"},
             "gpu_launches": sum(v[1] for v in prof.values()), "roofline": roof, "clocks": clk}
-    if ctx.rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
+    return line
 
 
-def run_raster(args):
+def run_raster(args, ctx):
     """Area-coverage rasterisation of the headline's masks as shapes off the pixel grid: the
     Manhattan generator's rectangles of 64 clips of 2048^2, shifted by (0.3, 0.6) px so that
     every edge is a grey level; one step = litho_rasterize of all clips."""
     import paper_2602_15036_gb300 as P  # noqa: F401
     from paper_2602_15036_gb300 import litho as L
-    ctx = Ctx(args)
     torch = ctx.torch
     clips = args.clips
     rl = []
@@ -687,18 +816,15 @@ def run_raster(args):
             "config": {"workload": f"raster {clips}x2048^2, {sum(counts)} rectangles", "clips_per_gpu": clips},
             "grey_pixel_fraction": grey, "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "gpu_launches": sum(v[1] for v in prof.values()), "roofline": roof, "clocks": clk}
-    if ctx.rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
+    return line
 
 
-def run_ai(args):
+def run_ai(args, ctx):
     """AI initialiser inputs for 16 clips of 2048^2 (the headline optics, nominal focus, K = 24):
     one step = the Eq. (9) channels (target, aerial image, intensity gradient, normalised over
     the batch) + Eqs. (15)-(17) print images and loss against the aerial image."""
     import paper_2602_15036_gb300 as P
     from paper_2602_15036_gb300 import litho as L
-    ctx = Ctx(args)
     torch = ctx.torch
     clips = min(args.clips, 16)
     kern = P.litho_make_kernels(P.make_optics(**OPTICS), N, PIXEL, [0.0], K)
@@ -743,16 +869,13 @@ def run_ai(args):
             "stages_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
             "roofline": roof, "stage_rooflines": {kk: {x: v[x] for x in ("bound", "frac")} for kk, v in roofs.items()},
             "gpu_launches": sum(v[1] for v in prof.values()), "clocks": clk}
-    if ctx.rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
+    return line
 
 
-def run_serve(args):
+def run_serve(args, ctx):
     """Poisson stream of mixed requests through litho_serve (sizes 256..2048, DUV and EUV optics,
     K in {8,16,24}, half images and half ILT steps) at 80 % of the measured saturated rate."""
     from paper_2602_15036_gb300 import litho as L
-    ctx = Ctx(args)
     duv = dict(wavelength_nm=193.0, na=1.35, n_medium=1.44, kind="annular", src_grid=21, sigma_in=0.6,
                sigma_out=0.9)
     euv = dict(wavelength_nm=13.5, na=0.33, n_medium=1.0, kind="annular", src_grid=21, sigma_in=0.6, sigma_out=0.9)
@@ -822,7 +945,7 @@ def run_serve(args):
     srv.close()
     px = sum(r[2] * r[2] for r in reqs)
     sweep = {}
-    for load in (0.5, 0.8):
+    for load in (0.5, 0.8, 0.9):
         srv = L.Server(64 << 30, max_slots=8, max_queue=total + 16)
         drain([submit(r) for r in keys.values()])
         srv.stats_reset()          # latencies of the timed stream only (not the kernel-set warm-up)
@@ -850,9 +973,31 @@ def run_serve(args):
             "stats": {k: s[k] for k in ("submitted", "completed", "rejected", "cancelled", "hbm_high_water",
                                          "kernel_sets_cached")},
             "status_counts": statuses, "first_error": first_err[0] if first_err else None}
-    if ctx.rank == 0:
-        print(json.dumps(line), flush=True)
-    ctx.close()
+    return line
+
+
+def run_all_workloads(args, ctx) -> dict:
+    """The other workloads of the library, each timed as its own bench mode would time it, for
+    the default run's JSON line: ILT (100 gradient steps of 16 x 1024^2, K = 16, 5 planes, with
+    the loss curve), AI inputs, contours + EPE, the rasteriser, and serving (4096 Poisson
+    requests at 0.5, 0.8 and 0.9 of the saturated rate)."""
+    import copy
+    out = {}
+    plans = [("ilt", run_ilt, dict(steps=100, warmup=3, precision="fft32/coarse")),
+             ("ai", run_ai, dict(steps=max(10, args.steps), warmup=3, precision="fft32/coarse", clips=16)),
+             ("contour", run_contour, dict(steps=max(10, args.steps), warmup=3, clips=64)),
+             ("raster", run_raster, dict(steps=max(10, args.steps), warmup=3, clips=64)),
+             ("serve", run_serve, dict(requests=4096))]
+    for name, fn, over in plans:
+        a = copy.copy(args)
+        for k, v in over.items():
+            setattr(a, k, v)
+        try:
+            out[name] = fn(a, ctx)
+        except Exception as e:   # report the failure in the line instead of losing the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        ctx.torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -868,21 +1013,21 @@ def main():
     ap.add_argument("--requests", type=int, default=4096)
     ap.add_argument("--no-compare", action="store_true", help="time only --precision")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="aerial workload only: skip the other workloads of the default line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "ilt":
-        run_ilt(args)
-    elif args.workload == "serve":
-        run_serve(args)
-    elif args.workload == "contour":
-        run_contour(args)
-    elif args.workload == "raster":
-        run_raster(args)
-    elif args.workload == "ai":
-        run_ai(args)
-    else:
-        run_aerial(args)
+        return
+    ctx = Ctx(args)
+    fn = {"ilt": run_ilt, "serve": run_serve, "contour": run_contour, "raster": run_raster, "ai": run_ai,
+          "aerial": run_aerial}[args.workload]
+    line = fn(args, ctx)
+    if args.workload == "aerial" and ctx.world == 1 and not args.headline_only:
+        line["workloads"] = run_all_workloads(args, ctx)
+    if ctx.rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
 
 
 if __name__ == "__main__":

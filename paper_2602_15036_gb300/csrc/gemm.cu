@@ -3,21 +3,31 @@
 // For one focus plane, E_k(y, x) = sum_c T_k(y, c) W(c, x) with the stage-1
 // field T_k (rows y, crop columns c) and the inverse-DFT matrix
 // W(c, x) = exp(+2 pi i u_c x / N), u_c = c - C/2.  Written over real
-// operands with Ar = Re T, Ai = Im T, Wr = cos, Wi = sin:
-//   D1 = Ar Wr^T,  D2 = Ai Wi^T,  D3 = Ar Wi^T + Ai Wr^T,
-//   Re E = D1 - D2,  Im E = D3,  I(y, x) += lam_k ((D1 - D2)^2 + D3^2).
-// The three products accumulate in TMEM (3 x 128 fp32 columns) and need no
-// negated operand.  The k loop runs inside the CTA: the epilogue warps fold
-// each kernel's |E|^2 into registers, so I is written once per tile.
+// operands with Ar = Re T, Ai = Im T, Wr = cos, Wi = sin.
+//
+// Split modes use Gauss's three-multiplication complex product: with the sums
+// As = Ar + Ai and Ws = Wr + Wi,
+//   D1 = Ar Wr^T,  D2 = Ai Wi^T,  D3 = As Ws^T,
+//   Re E = D1 - D2,  Im E = D3 - D1 - D2,
+// three real products per complex multiply-add instead of four (9 MMAs per
+// K step with the hi/lo split instead of 12).  The plain 16-bit modes keep
+// the four-product form, D3 = Ar Wi^T + Ai Wr^T and Im E = D3: their operands
+// carry 8 to 11 significand bits, and the cancellation in D3 - D1 - D2 would
+// enlarge their error.  Either way I(y, x) += lam_k (Re E^2 + Im E^2); the
+// three accumulators live in TMEM (3 x 128 fp32 columns).  The k loop runs
+// inside the CTA: the epilogue warps fold each kernel's |E|^2 into
+// registers, so I is written once per tile.
 //
 // Operand layout in global memory (16-bit elements, K-major): the contraction
 // index c is cut into chunks of 32 complex values stored as one 64-element
-// (128-byte) row segment [Re 32 | Im 32].  A: [plane * K + k][y][2C],
-// B: [x][2C] (same chunking, cos | sin).  TMA loads 128-row x 64-element boxes
-// with 128-byte swizzling, which is the canonical K-major SWIZZLE_128B layout
-// that tcgen05.mma reads through shared-memory descriptors; the four 16-element
-// K steps of a chunk are Re(0:16), Re(16:32), Im(0:16), Im(16:32) at byte
-// offsets 0, 32, 64, 96.
+// (128-byte) row segment [Re 32 | Im 32].  A (hi and lo): [plane * K + k][y][2C],
+// B (hi and lo): [x][2C] (same chunking, cos | sin).  The sums are stored the
+// same way with hi and lo side by side: AS = [As_hi 32 | As_lo 32] per chunk,
+// BS = [Ws_hi 32 | Ws_lo 32].  TMA loads 128-row x 64-element boxes with
+// 128-byte swizzling, which is the canonical K-major SWIZZLE_128B layout that
+// tcgen05.mma reads through shared-memory descriptors; the four 16-element K
+// steps of a chunk sit at byte offsets 0, 32 (first half: Re, or the hi sums)
+// and 64, 96 (second half: Im, or the lo sums).
 //
 // Precision modes: BF16 / FP16 (one product), BF16X3 and FP16X3
 // (operands split into hi + lo, three products hi.hi + hi.lo + lo.hi; FP16
@@ -25,9 +35,10 @@
 // stay in the normal range; plain FP16 is scaled the same way).  FP32
 // accumulation throughout.
 //
-// Kernel structure: persistent, one CTA per SM (192 KB shared memory, all 512
-// TMEM columns), warp 0 = TMA producer, warp 1 = MMA issuer (one thread),
-// warps 2..9 = epilogue.  Every mbarrier wait is bounded: past ~2 s it records
+// Kernel structure: persistent, one CTA per SM (192 KB shared memory ring:
+// two stages of six tiles in the split modes, six stages of two tiles in the
+// plain ones; all 512 TMEM columns), warp 0 = TMA producer, warp 1 = MMA
+// issuer (one thread), warps 2..9 = epilogue.  Every mbarrier wait is bounded: past ~2 s it records
 // an error code in a device flag, the CTA drains its own copies and MMAs with
 // bounded waits, frees TMEM and returns.
 #include <cuda.h>
@@ -52,13 +63,16 @@ constexpr int BM = 128;               // rows (y) per tile = UMMA M
 constexpr int XT = 128;               // x per tile = UMMA N
 constexpr int CH = 32;                // complex values per chunk
 constexpr int KE = 2 * CH;            // 16-bit elements per chunk row (128 bytes)
-constexpr int STAGES = 3;
 constexpr int TILE_BYTES = BM * KE * 2;  // 16 KB (A and B boxes are both 128 x 64)
-constexpr int STAGE_BYTES = 4 * TILE_BYTES;
+constexpr int RING_BYTES = 12 * TILE_BYTES;  // 192 KB of pipeline stages
+constexpr int MAX_STAGES = 6;
+// Tiles of a stage: split modes A_hi, A_lo, AS, B_hi, B_lo, BS (2 stages);
+// plain modes A_hi, B_hi (6 stages).
+constexpr int TILES_SPLIT = 6, TILES_PLAIN = 2;
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int SMEM_BYTES = RING_BYTES + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int GROUP_CLIPS = 4;        // clips per GEMM launch
 constexpr long long kWaitCycles = 4000000000LL;  // about 2 s at 2 GHz
 
@@ -185,17 +199,22 @@ __global__ void k_wait_selftest(int* err, long long limit, int code) {
 
 __global__ void __launch_bounds__(THREADS, 1)
     k_dft_gemm(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
-               const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo, GemmParams p) {
+               const __grid_constant__ CUtensorMap ta_s, const __grid_constant__ CUtensorMap tb_hi,
+               const __grid_constant__ CUtensorMap tb_lo, const __grid_constant__ CUtensorMap tb_s, GemmParams p) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-  // bars: full[STAGES], empty[STAGES], acc_full, acc_empty, drain
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 3);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + RING_BYTES);
+  // bars: full[MAX_STAGES], empty[MAX_STAGES], acc_full, acc_empty, drain
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * MAX_STAGES + 3);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + STAGES);
-  const uint32_t acc_full = smem_u32(bars + 2 * STAGES), acc_empty = smem_u32(bars + 2 * STAGES + 1);
-  const uint32_t drain = smem_u32(bars + 2 * STAGES + 2);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + MAX_STAGES);
+  const uint32_t acc_full = smem_u32(bars + 2 * MAX_STAGES), acc_empty = smem_u32(bars + 2 * MAX_STAGES + 1);
+  const uint32_t drain = smem_u32(bars + 2 * MAX_STAGES + 2);
+  // stage geometry of this mode (uniform across the grid)
+  const int tiles = p.split ? TILES_SPLIT : TILES_PLAIN;
+  const int STAGES = RING_BYTES / (tiles * TILE_BYTES);
+  const int STAGE_BYTES = tiles * TILE_BYTES;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -221,7 +240,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
   const int tiles_per_plane = p.tiles_y * p.tiles_x;
   const int total = p.planes * tiles_per_plane;
-  const uint32_t tx_bytes = p.split ? STAGE_BYTES : 2 * TILE_BYTES;
+  const uint32_t tx_bytes = STAGE_BYTES;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -244,11 +263,16 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
             mbar_expect_tx(full0 + 8 * s, tx_bytes);
-            tma_load_2d(base, &ta_hi, full0 + 8 * s, ch * KE, arow);
-            tma_load_2d(base + 2 * TILE_BYTES, &tb_hi, full0 + 8 * s, ch * KE, xt * XT);
             if (p.split) {
+              tma_load_2d(base, &ta_hi, full0 + 8 * s, ch * KE, arow);
               tma_load_2d(base + TILE_BYTES, &ta_lo, full0 + 8 * s, ch * KE, arow);
-              tma_load_2d(base + 3 * TILE_BYTES, &tb_lo, full0 + 8 * s, ch * KE, xt * XT);
+              tma_load_2d(base + 2 * TILE_BYTES, &ta_s, full0 + 8 * s, ch * KE, arow);
+              tma_load_2d(base + 3 * TILE_BYTES, &tb_hi, full0 + 8 * s, ch * KE, xt * XT);
+              tma_load_2d(base + 4 * TILE_BYTES, &tb_lo, full0 + 8 * s, ch * KE, xt * XT);
+              tma_load_2d(base + 5 * TILE_BYTES, &tb_s, full0 + 8 * s, ch * KE, xt * XT);
+            } else {
+              tma_load_2d(base, &ta_hi, full0 + 8 * s, ch * KE, arow);
+              tma_load_2d(base + TILE_BYTES, &tb_hi, full0 + 8 * s, ch * KE, xt * XT);
             }
           }
         }
@@ -288,26 +312,37 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             tc_fence_after();
             const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-            const uint64_t ahi = sdesc_sw128(base), alo = sdesc_sw128(base + TILE_BYTES);
-            const uint64_t bhi = sdesc_sw128(base + 2 * TILE_BYTES), blo = sdesc_sw128(base + 3 * TILE_BYTES);
+            if (p.split) {
+              const uint64_t ahi = sdesc_sw128(base), alo = sdesc_sw128(base + TILE_BYTES);
+              const uint64_t as = sdesc_sw128(base + 2 * TILE_BYTES), bhi = sdesc_sw128(base + 3 * TILE_BYTES);
+              const uint64_t blo = sdesc_sw128(base + 4 * TILE_BYTES), bs = sdesc_sw128(base + 5 * TILE_BYTES);
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-              const uint64_t re = uint64_t(2 * ks), im = uint64_t(4 + 2 * ks);  // byte offsets >> 4
-              const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
-              // D1 += Ar Wr ; D2 += Ai Wi ; D3 += Ar Wi + Ai Wr   (each x3 when split)
-              umma_f16(d1, ahi + re, bhi + re, idesc, first);
-              umma_f16(d2, ahi + im, bhi + im, idesc, first);
-              umma_f16(d3, ahi + re, bhi + im, idesc, first);
-              umma_f16(d3, ahi + im, bhi + re, idesc, 1u);
-              if (p.split) {
-                umma_f16(d1, ahi + re, blo + re, idesc, 1u);
-                umma_f16(d1, alo + re, bhi + re, idesc, 1u);
-                umma_f16(d2, ahi + im, blo + im, idesc, 1u);
-                umma_f16(d2, alo + im, bhi + im, idesc, 1u);
-                umma_f16(d3, ahi + re, blo + im, idesc, 1u);
-                umma_f16(d3, alo + re, bhi + im, idesc, 1u);
-                umma_f16(d3, ahi + im, blo + re, idesc, 1u);
-                umma_f16(d3, alo + im, bhi + re, idesc, 1u);
+              for (int ks = 0; ks < 2; ++ks) {
+                // byte offsets >> 4: first half (Re, or the hi sums), second half (Im, or the lo sums)
+                const uint64_t h1 = uint64_t(2 * ks), h2 = uint64_t(4 + 2 * ks);
+                const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
+                // Gauss: D1 += Ar Wr ; D2 += Ai Wi ; D3 += As Ws, each as hi.hi + hi.lo + lo.hi
+                umma_f16(d1, ahi + h1, bhi + h1, idesc, first);
+                umma_f16(d1, ahi + h1, blo + h1, idesc, 1u);
+                umma_f16(d1, alo + h1, bhi + h1, idesc, 1u);
+                umma_f16(d2, ahi + h2, bhi + h2, idesc, first);
+                umma_f16(d2, ahi + h2, blo + h2, idesc, 1u);
+                umma_f16(d2, alo + h2, bhi + h2, idesc, 1u);
+                umma_f16(d3, as + h1, bs + h1, idesc, first);
+                umma_f16(d3, as + h1, bs + h2, idesc, 1u);
+                umma_f16(d3, as + h2, bs + h1, idesc, 1u);
+              }
+            } else {
+              const uint64_t ahi = sdesc_sw128(base), bhi = sdesc_sw128(base + TILE_BYTES);
+#pragma unroll
+              for (int ks = 0; ks < 2; ++ks) {
+                const uint64_t re = uint64_t(2 * ks), im = uint64_t(4 + 2 * ks);
+                const uint32_t first = (ch == 0 && ks == 0) ? 0u : 1u;
+                // D1 += Ar Wr ; D2 += Ai Wi ; D3 += Ar Wi + Ai Wr
+                umma_f16(d1, ahi + re, bhi + re, idesc, first);
+                umma_f16(d2, ahi + im, bhi + im, idesc, first);
+                umma_f16(d3, ahi + re, bhi + im, idesc, first);
+                umma_f16(d3, ahi + im, bhi + re, idesc, 1u);
               }
             }
             umma_commit(empty0 + 8 * s);  // frees the stage once these MMAs complete
@@ -352,10 +387,18 @@ __global__ void __launch_bounds__(THREADS, 1)
           tmem_ld16(lane_base + 128 + col, b);
           tmem_ld16(lane_base + 256 + col, c);
           tmem_wait_ld();
+          if (p.split) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float re = a[i] - b[i];
-            acc[cc * 16 + i] = fmaf(l, fmaf(re, re, c[i] * c[i]), acc[cc * 16 + i]);
+            for (int i = 0; i < 16; ++i) {
+              const float re = a[i] - b[i], im = c[i] - (a[i] + b[i]);
+              acc[cc * 16 + i] = fmaf(l, fmaf(re, re, im * im), acc[cc * 16 + i]);
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const float re = a[i] - b[i];
+              acc[cc * 16 + i] = fmaf(l, fmaf(re, re, c[i] * c[i]), acc[cc * 16 + i]);
+            }
           }
         }
         tc_fence_before();
@@ -398,14 +441,17 @@ __device__ __forceinline__ void split16(float x, float scale, uint32_t& h, uint3
 }
 
 // Split 16-bit output of stage 1: row (j, y) of the A operand, chunked
-// [Re 32 | Im 32].  W consecutive columns (W a multiple of 4 dividing 32)
-// are packed into 8-byte stores per part.
+// [Re 32 | Im 32], and in the split modes the sums As = Re + Im for the
+// Gauss product, chunked [As_hi 32 | As_lo 32] (the sum is formed in FP32,
+// scaled like the parts, then split).  W consecutive columns (W a multiple
+// of 4 dividing 32) are packed into 8-byte stores per part.
 template <int MODE>
 struct OutSplit {
   static constexpr bool kRowWise = true;
   __device__ float2* column(int, int) const { return nullptr; }
   void* hi;
   void* lo;
+  void* sum;
   const float* scales;
   int n, crop, nk;  // row j of the operand belongs to kernel j mod nk
   template <int W>
@@ -413,27 +459,32 @@ struct OutSplit {
     static_assert(W % 4 == 0 && CH % W == 0, "column block");
     const size_t o = ((size_t)j * n + y) * (size_t)(2 * crop) + (size_t)(c0 / CH) * KE + (c0 % CH);
     const float s = scales[j % nk];
-    uint32_t rh[W], rl[W], ih[W], il[W];
+    uint32_t rh[W], rl[W], ih[W], il[W], sh[W], sl[W];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
       split16<MODE>(v[w].x, s, rh[w], rl[w]);
       split16<MODE>(v[w].y, s, ih[w], il[w]);
+      split16<MODE>(v[w].x + v[w].y, s, sh[w], sl[w]);
     }
-    uint2* hr = reinterpret_cast<uint2*>(static_cast<uint16_t*>(hi) + o);
-    uint2* hm = reinterpret_cast<uint2*>(static_cast<uint16_t*>(hi) + o + CH);
+    // one store per part and row: W 16-bit values, 16 bytes for W = 8 (fewer L2 write transactions)
+    auto put = [&](void* base, size_t off, const uint32_t (&x)[W]) {
+      uint16_t* d = static_cast<uint16_t*>(base) + off;
+      if constexpr (W == 8) {
+        *reinterpret_cast<uint4*>(d) = make_uint4(x[0] | (x[1] << 16), x[2] | (x[3] << 16), x[4] | (x[5] << 16),
+                                                  x[6] | (x[7] << 16));
+      } else {
 #pragma unroll
-    for (int q = 0; q < W / 4; ++q) {
-      hr[q] = make_uint2(rh[4 * q] | (rh[4 * q + 1] << 16), rh[4 * q + 2] | (rh[4 * q + 3] << 16));
-      hm[q] = make_uint2(ih[4 * q] | (ih[4 * q + 1] << 16), ih[4 * q + 2] | (ih[4 * q + 3] << 16));
-    }
-    if (MODE == kFP16X3 || MODE == kBF16X3) {
-      uint2* lr = reinterpret_cast<uint2*>(static_cast<uint16_t*>(lo) + o);
-      uint2* lm = reinterpret_cast<uint2*>(static_cast<uint16_t*>(lo) + o + CH);
-#pragma unroll
-      for (int q = 0; q < W / 4; ++q) {
-        lr[q] = make_uint2(rl[4 * q] | (rl[4 * q + 1] << 16), rl[4 * q + 2] | (rl[4 * q + 3] << 16));
-        lm[q] = make_uint2(il[4 * q] | (il[4 * q + 1] << 16), il[4 * q + 2] | (il[4 * q + 3] << 16));
+        for (int q = 0; q < W / 4; ++q)
+          reinterpret_cast<uint2*>(d)[q] = make_uint2(x[4 * q] | (x[4 * q + 1] << 16), x[4 * q + 2] | (x[4 * q + 3] << 16));
       }
+    };
+    put(hi, o, rh);
+    put(hi, o + CH, ih);
+    if (MODE == kFP16X3 || MODE == kBF16X3) {
+      put(lo, o, rl);
+      put(lo, o + CH, il);
+      put(sum, o, sh);
+      put(sum, o + CH, sl);
     }
   }
 };
@@ -441,21 +492,21 @@ struct OutSplit {
 // `clips` spectra in one launch; clip i writes the operand rows of kernels j + i nk.
 template <int N, int MODE>
 cudaError_t stage1_split_n(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
-                           const float* scales, void* a_hi, void* a_lo, int clips, cudaStream_t st) {
+                           const float* scales, void* a_hi, void* a_lo, void* a_s, int clips, cudaStream_t st) {
   return launch_stage1_cols<N, Stage1W<N>::W>(mhat, phi, nk, crop, tw,
-                                           OutSplit<MODE>{a_hi, a_lo, scales, N, crop, nk}, st, clips);
+                                           OutSplit<MODE>{a_hi, a_lo, a_s, scales, N, crop, nk}, st, clips);
 }
 
 template <int MODE>
 cudaError_t stage1_split_mode(int n, const float2* mhat, const float2* phi, int nk, int crop, const float2* tw,
-                              const float* scales, void* a_hi, void* a_lo, int clips, cudaStream_t st) {
+                              const float* scales, void* a_hi, void* a_lo, void* a_s, int clips, cudaStream_t st) {
   switch (n) {
-    case 128: return stage1_split_n<128, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
-    case 256: return stage1_split_n<256, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
-    case 512: return stage1_split_n<512, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
-    case 896: return stage1_split_n<896, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
-    case 1024: return stage1_split_n<1024, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
-    case 2048: return stage1_split_n<2048, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, clips, st);
+    case 128: return stage1_split_n<128, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, a_s, clips, st);
+    case 256: return stage1_split_n<256, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, a_s, clips, st);
+    case 512: return stage1_split_n<512, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, a_s, clips, st);
+    case 896: return stage1_split_n<896, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, a_s, clips, st);
+    case 1024: return stage1_split_n<1024, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, a_s, clips, st);
+    case 2048: return stage1_split_n<2048, MODE>(mhat, phi, nk, crop, tw, scales, a_hi, a_lo, a_s, clips, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -496,7 +547,8 @@ struct GemmOperands {
   bool built[kModes][2] = {};
   void* b_hi[kModes][2] = {};
   void* b_lo[kModes][2] = {};
-  CUtensorMap map_hi[kModes][2], map_lo[kModes][2];
+  void* b_s[kModes][2] = {};  // [Ws_hi 32 | Ws_lo 32] chunks, split modes
+  CUtensorMap map_hi[kModes][2], map_lo[kModes][2], map_s[kModes][2];
   float* d_lamp[kModes] = {};   // lambda / scale^2 per (f, k)
   float* d_scale[kModes] = {};  // stage-1 scale per (f, k)
   int* d_err = nullptr;
@@ -507,10 +559,12 @@ namespace {
 
 int eval_n(const litho_kernels* h, bool coarse) { return coarse ? h->nc_tc : h->n; }
 
-size_t per_clip_bytes(const litho_kernels* h, int mode, bool coarse) {
+// Bytes of one 16-bit operand array (A hi, A lo or AS) for one clip.
+size_t per_clip_array_bytes(const litho_kernels* h, bool coarse) {
   const size_t rows = size_t(h->n_focus) * h->k * eval_n(h, coarse), cols = size_t(2) * h->crop;
-  return rows * cols * 2 * (is_split(mode) ? 2 : 1);
+  return rows * cols * 2;
 }
+int arrays_of(int mode) { return is_split(mode) ? 3 : 1; }  // A_hi (+ A_lo, AS when split)
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
@@ -529,25 +583,29 @@ litho_status build_operands(const litho_kernels* hc, int mode, bool coarse) {
   if (g->built[mode][gi]) return LITHO_OK;
   const int N = eval_n(h, coarse), C = h->crop, F = h->n_focus, K = h->k;
   const size_t cols = size_t(2) * C, count = size_t(N) * cols;
-  std::vector<uint16_t> hi(count), lo(count);
+  std::vector<uint16_t> hi(count), lo(count), sum(count);
+  auto split = [&](double w, uint16_t& h16, uint16_t& l16) {
+    if (is_fp16(mode)) {
+      const __half hh = __float2half_rn(float(w));
+      h16 = __half_as_ushort(hh);
+      l16 = __half_as_ushort(__float2half_rn(float(w - double(__half2float(hh)))));
+    } else {
+      const __nv_bfloat16 hh = __float2bfloat16_rn(float(w));
+      h16 = __bfloat16_as_ushort(hh);
+      l16 = __bfloat16_as_ushort(__float2bfloat16_rn(float(w - double(__bfloat162float(hh)))));
+    }
+  };
   for (int x = 0; x < N; ++x) {
     for (size_t kk = 0; kk < cols; ++kk) {
       const int chunk = int(kk / KE), within = int(kk % KE), part = within / CH;
       const int c = chunk * CH + within % CH;
       const long long e = ((long long)(c - C / 2) * x % N + N) % N;
       const double a = 2.0 * M_PI * double(e) / double(N);
-      const double w = part ? std::sin(a) : std::cos(a);
-      if (is_fp16(mode)) {
-        const __half hh = __float2half_rn(float(w));
-        const __half ll = __float2half_rn(float(w - double(__half2float(hh))));
-        hi[size_t(x) * cols + kk] = __half_as_ushort(hh);
-        lo[size_t(x) * cols + kk] = __half_as_ushort(ll);
-      } else {
-        const __nv_bfloat16 hh = __float2bfloat16_rn(float(w));
-        const __nv_bfloat16 ll = __float2bfloat16_rn(float(w - double(__bfloat162float(hh))));
-        hi[size_t(x) * cols + kk] = __bfloat16_as_ushort(hh);
-        lo[size_t(x) * cols + kk] = __bfloat16_as_ushort(ll);
-      }
+      split(part ? std::sin(a) : std::cos(a), hi[size_t(x) * cols + kk], lo[size_t(x) * cols + kk]);
+      // the sum cos + sin of the Gauss product: hi in the first half of the chunk, lo in the second
+      uint16_t sh = 0, sl = 0;
+      split(std::cos(a) + std::sin(a), sh, sl);
+      sum[size_t(x) * cols + kk] = part ? sl : sh;
     }
   }
   // per-kernel scales: |T_k| <= max_u sum_v |Phi_k(v, u)| for masks with |m| <= 1
@@ -574,6 +632,8 @@ litho_status build_operands(const litho_kernels* hc, int mode, bool coarse) {
   if (is_split(mode)) {
     LITHO_TRY_CUDA(cudaMalloc(&g->b_lo[mode][gi], count * 2));
     LITHO_TRY_CUDA(cudaMemcpy(g->b_lo[mode][gi], lo.data(), count * 2, cudaMemcpyHostToDevice));
+    LITHO_TRY_CUDA(cudaMalloc(&g->b_s[mode][gi], count * 2));
+    LITHO_TRY_CUDA(cudaMemcpy(g->b_s[mode][gi], sum.data(), count * 2, cudaMemcpyHostToDevice));
   }
   if (!g->d_scale[mode]) {
     LITHO_TRY_CUDA(cudaMalloc(&g->d_scale[mode], scale.size() * sizeof(float)));
@@ -587,7 +647,8 @@ litho_status build_operands(const litho_kernels* hc, int mode, bool coarse) {
   }
   const int fmt = is_fp16(mode) ? 0 : 1;
   if (!make_map(&g->map_hi[mode][gi], g->b_hi[mode][gi], fmt, N, cols) ||
-      !make_map(&g->map_lo[mode][gi], is_split(mode) ? g->b_lo[mode][gi] : g->b_hi[mode][gi], fmt, N, cols)) {
+      !make_map(&g->map_lo[mode][gi], is_split(mode) ? g->b_lo[mode][gi] : g->b_hi[mode][gi], fmt, N, cols) ||
+      !make_map(&g->map_s[mode][gi], is_split(mode) ? g->b_s[mode][gi] : g->b_hi[mode][gi], fmt, N, cols)) {
     set_error("cuTensorMapEncodeTiled failed for the twiddle operand");
     return LITHO_ECUDA;
   }
@@ -603,8 +664,7 @@ litho_status build_operands(const litho_kernels* hc, int mode, bool coarse) {
 size_t gemm_workspace_bytes(const litho_kernels* h, litho_precision prec, int b, bool coarse) {
   const int mode = mode_of(prec);
   const int g = std::min(b, GROUP_CLIPS);
-  const size_t half = up256(size_t(g) * per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1));
-  return is_split(mode) ? 2 * half : half;
+  return arrays_of(mode) * up256(size_t(g) * per_clip_array_bytes(h, coarse));
 }
 
 litho_status gemm_supported(const litho_kernels* h, litho_precision prec, bool coarse) {
@@ -634,27 +694,30 @@ litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int c
   GemmOperands* g = h->gemm;
   const int N = eval_n(h, coarse), C = h->crop, F = h->n_focus, K = h->k;
   const float2* tw = coarse ? h->d_twc_tc : h->d_tw;
-  const size_t half =
-      up256(size_t(std::min(clips, GROUP_CLIPS)) * per_clip_bytes(h, mode, coarse) / (is_split(mode) ? 2 : 1));
+  const size_t arr = up256(size_t(std::min(clips, GROUP_CLIPS)) * per_clip_array_bytes(h, coarse));
   char* a_hi = static_cast<char*>(ws);
-  char* a_lo = is_split(mode) ? a_hi + half : a_hi;
+  char* a_lo = is_split(mode) ? a_hi + arr : a_hi;
+  char* a_s = is_split(mode) ? a_hi + 2 * arr : a_hi;
   {
     ProfScope ps(kStageGemmOperands, st, 1);  // one launch for the group
     cudaError_t e;
     if (mode == kBF16)
-      e = stage1_split_mode<kBF16>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, nullptr, clips, st);
+      e = stage1_split_mode<kBF16>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, nullptr, nullptr, clips,
+                                   st);
     else if (mode == kFP16)
-      e = stage1_split_mode<kFP16>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, nullptr, clips, st);
+      e = stage1_split_mode<kFP16>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, nullptr, nullptr, clips,
+                                   st);
     else if (mode == kBF16X3)
-      e = stage1_split_mode<kBF16X3>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, a_lo, clips, st);
+      e = stage1_split_mode<kBF16X3>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, a_lo, a_s, clips, st);
     else
-      e = stage1_split_mode<kFP16X3>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, a_lo, clips, st);
+      e = stage1_split_mode<kFP16X3>(N, mhat, h->d_phi, F * K, C, tw, g->d_scale[mode], a_hi, a_lo, a_s, clips, st);
     LITHO_TRY_CUDA(e);
   }
   const int fmt = is_fp16(mode) ? 0 : 1;
   const unsigned long long rows = (unsigned long long)clips * F * K * N;
-  CUtensorMap ta_hi, ta_lo;
-  if (!make_map(&ta_hi, a_hi, fmt, rows, 2ull * C) || !make_map(&ta_lo, a_lo, fmt, rows, 2ull * C)) {
+  CUtensorMap ta_hi, ta_lo, ta_s;
+  if (!make_map(&ta_hi, a_hi, fmt, rows, 2ull * C) || !make_map(&ta_lo, a_lo, fmt, rows, 2ull * C) ||
+      !make_map(&ta_s, a_s, fmt, rows, 2ull * C)) {
     set_error("cuTensorMapEncodeTiled failed for the stage-1 operand");
     return LITHO_ECUDA;
   }
@@ -676,7 +739,8 @@ litho_status gemm_aerial_group(const litho_kernels* h, const float2* mhat, int c
   const int grid = std::min(total, g->sm_count);
   LITHO_TRY_CUDA(cudaFuncSetAttribute(k_dft_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
   ProfScope ps(kStageStage2Gemm, st, 1);
-  k_dft_gemm<<<grid, THREADS, SMEM_BYTES, st>>>(ta_hi, ta_lo, g->map_hi[mode][gi], g->map_lo[mode][gi], p);
+  k_dft_gemm<<<grid, THREADS, SMEM_BYTES, st>>>(ta_hi, ta_lo, ta_s, g->map_hi[mode][gi], g->map_lo[mode][gi],
+                                                g->map_s[mode][gi], p);
   LITHO_TRY_CUDA(cudaGetLastError());
   return LITHO_OK;
 }
@@ -725,6 +789,7 @@ void gemm_free_operands(litho_kernels* h) {
     for (int gi = 0; gi < 2; ++gi) {
       cudaFree(h->gemm->b_hi[m][gi]);
       cudaFree(h->gemm->b_lo[m][gi]);
+      cudaFree(h->gemm->b_s[m][gi]);
     }
     cudaFree(h->gemm->d_lamp[m]);
     cudaFree(h->gemm->d_scale[m]);

@@ -19,7 +19,10 @@
 // With kernels, one launch can image several clips (grid x = clip, the
 // fastest-varying block index): the CTAs of all clips that need the same Phi
 // block run side by side, so each block comes from DRAM once and from L2
-// for the other clips.  Clip i writes j + i nk.
+// for the other clips.  Clip i writes j + i nk.  The row-wise (split 16-bit)
+// output swaps the two: its W columns fill only part of each 32-byte sector
+// of an operand row, so the column blocks that share those sectors are made
+// the fastest index and run side by side, and their pieces meet in L2.
 #pragma once
 
 #include <algorithm>
@@ -70,10 +73,11 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
   float2* buf = smem + N;
   float2* const blk0 = buf + W * LD;  // Phi (or spectrum) blocks [crop][W], double-buffered
   auto blk = [&](int s) { return blk0 + s * W * crop; };
-  const int tid = threadIdx.x, u0 = blockIdx.y * W, half = crop / 2;
-  const int j0 = blockIdx.z * jb, j1 = min(nk, j0 + jb), jofs = blockIdx.x * nk;
+  const int clip = Out::kRowWise ? blockIdx.y : blockIdx.x, cblk = Out::kRowWise ? blockIdx.x : blockIdx.y;
+  const int tid = threadIdx.x, u0 = cblk * W, half = crop / 2;
+  const int j0 = blockIdx.z * jb, j1 = min(nk, j0 + jb), jofs = clip * nk;
   if (j0 >= j1) return;
-  mhat += (size_t)blockIdx.x * crop * crop;
+  mhat += (size_t)clip * crop * crop;
   load_twiddles<N>(tw, tw_g);
   const float2* src_base = phi ? phi : mhat;  // the per-j operand
   auto issue = [&](int j, float2* dst) {  // W/2 16-byte pieces per row
@@ -148,8 +152,8 @@ cudaError_t launch_stage1_cols_t(const float2* mhat, const float2* phi, int nk, 
   const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop);
   cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out, BANDED>, sm);
   if (e != cudaSuccess) return e;
-  k_stage1_cols<N, W, Out, BANDED><<<dim3(clips, crop / W, (nk + JB - 1) / JB), Plan<N>::NT * W, sm, st>>>(
-      mhat, phi, crop, nk, JB, tw, out);
+  const dim3 grid = Out::kRowWise ? dim3(crop / W, clips, (nk + JB - 1) / JB) : dim3(clips, crop / W, (nk + JB - 1) / JB);
+  k_stage1_cols<N, W, Out, BANDED><<<grid, Plan<N>::NT * W, sm, st>>>(mhat, phi, crop, nk, JB, tw, out);
   return cudaGetLastError();
 }
 

@@ -107,6 +107,41 @@ def test_aerial_resist_full_size_rows(litho_lib, cuda):
                 assert np.array_equal(pr[i, f, y][sure], (ref[sure] >= THR).astype(np.uint8))
 
 
+def test_bench_shape_64_clips_sampled_rows(litho_lib, cuda):
+    """The benchmark's exact workload and launch shape: 64 clips of 2048^2 (the benchmark's
+    masks, seeds 1234..1297) through litho_aerial_resist fft32/coarse in one call, which the
+    library runs as 8 stage launches of 8 clips; sampled blurred rows of clips at the start,
+    end and inside of several launch groups, all 3 focus planes, against the oracle."""
+    import torch
+    L = litho_lib
+    n, pixel, k, focus, sigma, b = 2048, 8.0, 24, [-50.0, 0.0, 50.0], 10.0, 64
+    lam, phi = oracle_kernel_set(DUV_QUAD41, n, pixel, focus, k)
+    kern = L.litho_upload_kernels(n, pixel, lam, phi)
+    masks = np.stack([synth.manhattan_mask(n, seed=1234 + i) for i in range(b)])
+    img, ib, pr = L.litho_aerial_resist(kern, torch.from_numpy(masks).to(cuda), precision="fft32/coarse",
+                                        sigma_nm=sigma, threshold=THR)
+    L.litho_check_device(kern)
+    g = OR.gaussian_taps(sigma, pixel)
+    r = (len(g) - 1) // 2
+    c = phi.shape[-1]
+    worst_i = worst_b = 0.0
+    for i in (0, 7, 8, 35, 56, 63):
+        y = int(synth.Stream(31 + i).integers(0, n - 1, 1)[0])
+        ys = [(y + a) % n for a in range(-r, r + 1)]
+        img_i, ib_i, pr_i = img[i, :, y].cpu().numpy(), ib[i, :, y].cpu().numpy(), pr[i, :, y].cpu().numpy()
+        mb = OI.band(OI.mask_spectrum(masks[i].astype(np.float64)), c)
+        for f in range(3):
+            band_rows = OI.socs_rows(mb, lam[f], phi[f], n, ys)           # image rows y - r .. y + r
+            worst_i = max(worst_i, np.abs(img_i[f] - band_rows[r]).max())
+            col = sum(g[r - a] * band_rows[r + a] for a in range(-r, r + 1))
+            ref = sum(g[bb + r] * np.roll(col, bb) for bb in range(-r, r + 1))
+            worst_b = max(worst_b, np.abs(ib_i[f] - ref).max())
+            sure = np.abs(ref - THR) > 1e-5
+            assert np.array_equal(pr_i[f][sure], (ref[sure] >= THR).astype(np.uint8)), (i, f, y)
+    print(f"64 x 2048^2 fft32/coarse: image {worst_i:.2e} blur {worst_b:.2e}")
+    assert worst_i <= 1e-5 and worst_b <= 1e-5
+
+
 def test_clip_groups_match_single_clip_calls(litho_lib, cuda):
     """70 clips of 128^2 run as two groups of 35 per stage launch; each clip's image equals
     the image of the same clip imaged alone (bit for bit), and a few match the oracle."""

@@ -54,8 +54,13 @@ def test_two_gloo_ranks_shard_and_reduce():
 def test_stage_models_are_consistent():
     peaks = {"hbm_gbs": 6785.5, "bf16_tflops_sustained": 1709.2}
     m = bench.stage_models("fp16x3/coarse", 64, 2048, 448, 3, 24, 1024, peaks)
-    # 8 N'^2 C flops per kernel and plane, three products for the split operands
-    assert m["stage2_gemm"][0] == pytest.approx(64 * 3 * 24 * 8.0 * 1024 ** 2 * 448 * 3)
+    # split operands: Gauss's three real products (6 N'^2 C flops) per kernel and plane, each as
+    # three 16-bit products; plain 16-bit operands: four real products (8 N'^2 C)
+    assert m["stage2_gemm"][0] == pytest.approx(64 * 3 * 24 * 6.0 * 1024 ** 2 * 448 * 3)
+    mp = bench.stage_models("fp16/coarse", 64, 2048, 448, 3, 24, 1024, peaks)
+    assert mp["stage2_gemm"][0] == pytest.approx(64 * 3 * 24 * 8.0 * 1024 ** 2 * 448)
+    # operands: hi and lo of Re and Im plus the hi/lo sums, 2 bytes each, per complex value
+    assert m["stage2_gemm"][1] == pytest.approx(64 * 72 * 1024 * 448 * 12.0 + 64 * 3 * 1024 ** 2 * 4.0)
     # resist: 9 bytes per pixel and plane (f32 in, f32 blur and u8 printed out)
     assert m["resist"][1] == pytest.approx(64 * 3 * 2048 ** 2 * 9.0)
     assert "upsample" in m and "upsample_resist" in m
