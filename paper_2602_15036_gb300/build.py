@@ -22,7 +22,7 @@ LIB = os.path.join(HERE, "liblitho.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["api.cpp", "optics.cpp", "prof.cpp", "serve.cpp", "fft.cu", "interp.cu", "resist.cu", "gemm.cu", "ilt.cu",
-           "noalloc.cu", "contour.cu", "raster.cu", "ai.cu", "util.cu"]
+           "noalloc.cu", "contour.cu", "raster.cu", "ai.cu", "util.cu", "stage2_w32.cu"]
 
 
 def _nvcc() -> str:

@@ -83,6 +83,12 @@ litho_status upload(litho_kernels* h) {
     LITHO_TRY_CUDA(cudaMalloc(dst, twc.size() * sizeof(float2)));
     LITHO_TRY_CUDA(cudaMemcpy(*dst, twc.data(), twc.size() * sizeof(float2), cudaMemcpyHostToDevice));
   }
+  if (N == 1024 || h->nc == 1024) {
+    std::vector<float2> t32(kStage2W32TableLen);
+    stage2_w32_table(t32.data());
+    LITHO_TRY_CUDA(cudaMalloc(&h->d_tw32, t32.size() * sizeof(float2)));
+    LITHO_TRY_CUDA(cudaMemcpy(h->d_tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   return LITHO_OK;
 }
 
@@ -122,6 +128,7 @@ void litho_free_kernels(litho_kernels* h) {
   cudaFree(h->d_tw);
   if (h->d_twc_tc != h->d_twc) cudaFree(h->d_twc_tc);
   cudaFree(h->d_twc);
+  cudaFree(h->d_tw32);
   for (auto& s : h->host_streams)
     if (s) cudaStreamDestroy(s);
   for (auto& e : h->host_events)
@@ -471,7 +478,7 @@ static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, in
     {
       ProfScope ps(kStageStage2Fft, st, 1);
       LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda, K, NE, C, float(dose), tw, coarse ? L.ic : img, g * F,
-                                       (long long)K * NE * C, (long long)NE * NE, st, F));
+                                       (long long)K * NE * C, (long long)NE * NE, st, F, h->d_tw32));
     }
     if (coarse) {
       litho_status s = upsample(h, p, L, g * F, img, fr, size_t(c0) * F, st);

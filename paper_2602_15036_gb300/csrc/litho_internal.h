@@ -98,6 +98,8 @@ struct litho_kernels {
   float2* d_twc = nullptr;                 // FFT twiddle table for nc
   int nc_tc = 0;                           // tensor-core coarse grid: as nc, or 896 when 2 crop <= 896 < nc
   float2* d_twc_tc = nullptr;              // FFT twiddle table for nc_tc (d_twc when nc_tc == nc)
+  float2* d_tw32 = nullptr;                // second-pass twiddles of the warp-per-row 1024-point stage 2
+                                           // (when N or nc is 1024, else NULL)
   litho::GemmOperands* gemm = nullptr;     // lazily built per precision
   int device = 0;
   // streams and events of the pipelined host-buffer path (created on first use)
@@ -143,10 +145,20 @@ cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int
                               float2* t1, cudaStream_t st, int clips = 1);
 // Stage 2 FFT path: I[y][x] = dose * sum_j lam[j] |sum_c t1[j][y][c] e^{+2 pi i u_c x/N}|^2
 // for each of `planes` planes; plane p takes lam[(p mod lam_period) nk ...]
-// (lam_period <= 0: planes, no repetition).
+// (lam_period <= 0: planes, no repetition).  With tw32 (the kernel set's
+// d_tw32) a 1024-point row takes the warp-per-row radix-32 kernel.
 cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
-                              long long img_plane_stride, cudaStream_t st, int lam_period = 0);
+                              long long img_plane_stride, cudaStream_t st, int lam_period = 0,
+                              const float2* tw32 = nullptr);
+// The warp-per-row stage 2 for 1024-point rows (stage2_w32.cu) and its
+// second-pass twiddle table (31 x 32 entries w^(r l), r in [1, 32), l in [0, 32)).
+bool stage2_w32_supported(int n, int crop);
+void stage2_w32_table(float2* out);
+constexpr int kStage2W32TableLen = 31 * 32;
+cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
+                              const float2* tw2, float* img, int planes, long long t1_plane, long long img_plane,
+                              int lam_period, cudaStream_t st);
 
 // A device-side delay of about `ms` milliseconds on `st` (util.cu): one
 // thread spinning on the SM clock for a fixed number of cycles, which always
