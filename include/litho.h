@@ -432,13 +432,21 @@ typedef struct {
   double mpx_per_s;               /* completed pixels / (last completion - first submit) */
   size_t hbm_high_water;          /* peak bytes of admitted work */
   int kernel_sets_cached;
+  uint64_t batches;               /* batches launched (completed / batches = mean clips per batch) */
+  int max_batch;                  /* clips in the largest batch */
 } litho_serve_stats_t;
 
-/* A server with its own scheduler thread, max_slots concurrent requests (one
+/* A server with its own scheduler thread, max_slots concurrent batches (one
  * CUDA stream each), admission while the summed device footprint of running
- * requests stays within hbm_budget_bytes, and a queue of max_queue waiting
- * requests.  Kernel sets are built once per (optics, n, pixel, focus, k) and
- * stay resident. */
+ * batches stays within hbm_budget_bytes, and a queue of max_queue waiting
+ * requests.  Continuous batching: when a slot frees, the oldest request that
+ * fits takes with it the queued requests that can share its launches (the
+ * same optics, n, pixel, focus, k, kind, precision, dose and ILT constants),
+ * in arrival order, up to 64 clips, and the batch runs as one grouped
+ * litho_aerial / litho_ilt_grad call; each request's result is the same,
+ * bit for bit, as the request run alone.  Kernel sets are built once per
+ * (optics, n, pixel, focus, k) and stay resident (the paper's GPU-residency
+ * principle, its Section II.D). */
 litho_status litho_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, litho_server** out);
 /* EBUSY if the queue is full; EINVAL if the request's footprint exceeds the
  * whole budget or its fields are invalid. */
@@ -462,7 +470,8 @@ void litho_serve_destroy(litho_server* s);
  * the server carries on); bit 1 makes the next admitted request slow (a
  * fixed 200 ms device delay on its slot's stream before its work: one thread
  * spinning on the SM clock, which always ends), so that requests on the
- * other slots can be seen to complete meanwhile.  No GPU fault is involved. */
+ * other slots can be seen to complete meanwhile.  A request that takes an
+ * injected fault runs alone (no batch).  No GPU fault is involved. */
 litho_status litho_serve_inject_fault(litho_server* s, int fault_mask);
 
 /* ---- tracing ------------------------------------------------------------------------------------- */

@@ -1,20 +1,31 @@
 // Continuous-batching request server (litho_serve_*).
 //
 // Requests (one clip each: an aerial image, or one ILT gradient step) arrive
-// at any time.  A scheduler thread admits queued requests whenever a slot
-// (one non-blocking CUDA stream) is free and the request's device footprint
-// fits in what the HBM budget has left; a request that does not fit yet is
-// skipped so that smaller ones behind it can start (no head-of-line
-// blocking), except that the oldest request, once skipped many times, holds
-// admission until it fits (no starvation).  Admitted work is enqueued on the
-// slot's stream: stream-ordered allocation, host-to-device copy from pinned
-// staging, the imaging or gradient kernels, device-to-host copy, stream-
-// ordered free, and a host callback that records completion.  Requests on
-// different slots overlap on the device.  Kernel sets are built once per
-// (optics, n, pixel, defocus, k) on a builder thread and stay resident; a
-// request whose kernels are still being built waits without blocking others.
-// All device kernels are deterministic, so a result is bit-identical whether
-// the request ran alone or in a mix.
+// at any time.  A scheduler thread admits queued work whenever a slot (one
+// non-blocking CUDA stream) is free and the work's device footprint fits in
+// what the HBM budget has left; a request that does not fit yet is skipped so
+// that smaller ones behind it can start (no head-of-line blocking), except
+// that the oldest request, once skipped many times, holds admission until it
+// fits (no starvation).
+//
+// Batching: the admitted request takes with it every queued request that
+// can share its launches: the same kernel set (optics, n, pixel, defocus, k),
+// kind, precision and scalar parameters (dose; the ILT step's resist and
+// sigmoid constants), in arrival order, up to kMaxBatch clips and kMaxBatchPx
+// pixels, while the batch's footprint fits the budget and its pageable
+// buffers fit the slot's pinned staging.  So requests that arrived while the
+// GPU was busy run as one grouped call (litho_aerial / litho_ilt_grad on b
+// clips), which images the clips in shared launches.  A batch is enqueued on
+// its slot's stream: stream-ordered allocation, host-to-device copies (pinned
+// caller buffers by DMA, pageable ones through the slot's pinned staging),
+// the grouped imaging or gradient call, device-to-host copies, stream-ordered
+// free, and one host callback that completes every request of the batch.
+// Batches on different slots overlap on the device.  Kernel sets are built
+// once per key on a builder thread and stay resident; a request whose
+// kernels are still being built waits without blocking others.  The grouped
+// calls give each clip the same result as the clip imaged alone, bit for
+// bit, and all device kernels are deterministic, so a request's result does
+// not depend on what it ran with.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -57,17 +68,22 @@ struct Req {
   uint64_t ticket = 0;
   litho_request r{};
   std::vector<double> custom;
-  std::string key;
+  std::string key;   // kernel set
+  std::string bkey;  // batch: kernel set, kind, precision, scalar parameters
+  int crop = 0;
   int state = kQueued;
   litho_status result = LITHO_OK;
   std::string err;
-  size_t footprint = 0;
+  size_t footprint = 0;  // alone
   int skipped = 0;
   double t_submit = 0, t_done = 0;
   int slot = -1;
-  litho_server* srv = nullptr;
   bool in_pinned = false, out_pinned = false;  // caller buffers usable for DMA directly
+  size_t stage_in = 0, stage_out = 0;          // offsets in the slot's pinned staging
 };
+
+constexpr int kMaxBatch = 64;                                 // clips per batch
+constexpr double kMaxBatchPx = 32.0 * 2048.0 * 2048.0;       // pixels per batch
 
 // True for page-locked (cudaHostAlloc / cudaHostRegister) host memory.
 bool is_pinned(const void* p) {
@@ -85,6 +101,10 @@ struct Slot {
   bool busy = false;
   char* pinned = nullptr;
   size_t pinned_bytes = 0;
+  std::vector<Req*> batch;  // the requests running on this slot
+  size_t footprint = 0;     // device bytes of the batch
+  litho_server* srv = nullptr;
+  int index = 0;
 };
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
@@ -102,8 +122,24 @@ std::string kernel_key(const litho_request& r, const std::vector<double>& custom
   return s;
 }
 
-// Device bytes of one request (inputs, output, workspace) for a kernel set shape.
-size_t request_bytes(const litho_request& r, int crop) {
+std::string batch_key(const litho_request& r, const std::string& kernel_key) {
+  char buf[256];
+  snprintf(buf, sizeof(buf), "#%d|%d|%a", r.kind, r.precision, r.dose);
+  std::string s = kernel_key + buf;
+  if (r.kind == LITHO_REQ_ILT_STEP) {
+    snprintf(buf, sizeof(buf), "|%a|%a|%a|%a", r.sigma_nm, r.threshold, r.mask_steep, r.resist_steep);
+    s += buf;
+  }
+  return s;
+}
+
+// The precision code the batch's call takes (ILT steps run on the coarse grid).
+int call_precision(const litho_request& r) {
+  return r.kind == LITHO_REQ_ILT_STEP ? int(LITHO_PREC_FFT32 | LITHO_GRID_COARSE) : r.precision;
+}
+
+// Workspace bytes of the grouped call for b clips, for a kernel set shape.
+size_t workspace_bytes(const litho_request& r, int crop, int b) {
   litho_kernels shape;
   shape.n = r.n;
   shape.crop = crop;
@@ -112,14 +148,30 @@ size_t request_bytes(const litho_request& r, int crop) {
   shape.pixel_nm = r.pixel_nm;
   shape.nc = coarse_grid(crop, r.n, false);  // as the kernel upload computes them
   shape.nc_tc = coarse_grid(crop, r.n, true);
-  const size_t nn = size_t(r.n) * r.n;
   size_t ws = 0;
-  if (r.kind == LITHO_REQ_IMAGE) {
-    litho_aerial_workspace_size(&shape, 1, static_cast<litho_precision>(r.precision), &ws);
-    return up256(nn * 4) + up256(nn * 4) + up256(ws);
-  }
-  litho_ilt_workspace_size(&shape, 1, &ws, nullptr);
-  return 3 * up256(nn * 4) + up256(ws);
+  if (r.kind == LITHO_REQ_IMAGE)
+    litho_aerial_workspace_size(&shape, b, static_cast<litho_precision>(r.precision), &ws);
+  else
+    litho_ilt_workspace_size(&shape, b, &ws, nullptr);
+  return ws;
+}
+
+// Device bytes of a batch of b clips: inputs [b][n][n] (and targets for ILT),
+// outputs [b][n][n], workspace.
+size_t batch_bytes(const litho_request& r, int crop, int b) {
+  const size_t plane = up256(size_t(b) * r.n * r.n * 4);
+  return plane * (r.kind == LITHO_REQ_ILT_STEP ? 3 : 2) + up256(workspace_bytes(r, crop, b));
+}
+
+// Pinned staging bytes a request needs when its buffers are pageable.
+size_t staging_bytes(const Req* q) {
+  const size_t nn4 = size_t(q->r.n) * q->r.n * 4;
+  const bool ilt = q->r.kind == LITHO_REQ_ILT_STEP;
+  size_t b = 0;
+  if (!q->in_pinned) b += up256(nn4 * (ilt ? 2 : 1));
+  if (!q->out_pinned) b += up256(nn4);
+  if (ilt) b += 256;  // the loss
+  return b;
 }
 
 }  // namespace
@@ -140,6 +192,8 @@ struct litho_server {
   size_t in_use = 0, high_water = 0, cache_bytes = 0;
   int running = 0;
   uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0, cancelled = 0;
+  uint64_t batches = 0;  // batches launched in the statistics window
+  int max_batch = 0;     // largest batch (clips) in the window
   std::vector<double> latencies;
   double first_submit = -1.0, last_done = 0.0, pixels = 0.0;
   std::atomic<int> fault_mask{0};
@@ -153,12 +207,7 @@ void finish_locked(litho_server* s, Req* q, int state, litho_status st, const ch
   q->result = st;
   if (msg) q->err = msg;
   q->t_done = now_ms();
-  if (q->slot >= 0) {
-    s->slots[q->slot].busy = false;
-    s->running--;
-    s->in_use -= q->footprint;
-    q->slot = -1;
-  }
+  q->slot = -1;
   if (state == kDone) {
     s->completed++;
     s->latencies.push_back(q->t_done - q->t_submit);
@@ -168,105 +217,113 @@ void finish_locked(litho_server* s, Req* q, int state, litho_status st, const ch
   s->cv.notify_all();
 }
 
-void CUDART_CB on_done(void* arg) {
-  Req* q = static_cast<Req*>(arg);
-  litho_server* s = q->srv;
-  // The slot stays busy until finish_locked, so its staging buffer is ours here.
-  Slot& sl = s->slots[q->slot];
-  const size_t nn = size_t(q->r.n) * q->r.n;
-  const size_t in_bytes = nn * 4 * (q->r.kind == LITHO_REQ_ILT_STEP ? 2 : 1);
-  if (!q->out_pinned) std::memcpy(q->r.output_host, sl.pinned + up256(in_bytes), nn * 4);
-  if (q->r.kind == LITHO_REQ_ILT_STEP && q->r.loss_host)
-    std::memcpy(q->r.loss_host, sl.pinned + up256(in_bytes) + up256(nn * 4), sizeof(double));
+// Frees a slot whose batch has finished (or failed to launch).
+void release_slot_locked(litho_server* s, Slot& sl) {
+  sl.busy = false;
+  sl.batch.clear();
+  s->running--;
+  s->in_use -= sl.footprint;
+  sl.footprint = 0;
+  s->cv.notify_all();
+}
+
+void CUDART_CB on_batch_done(void* arg) {
+  Slot* sl = static_cast<Slot*>(arg);
+  litho_server* s = sl->srv;
+  // The slot stays busy until release_slot_locked, so its batch and staging are ours here.
+  for (Req* q : sl->batch) {
+    const size_t nn = size_t(q->r.n) * q->r.n;
+    if (!q->out_pinned) std::memcpy(q->r.output_host, sl->pinned + q->stage_out, nn * 4);
+    if (q->r.kind == LITHO_REQ_ILT_STEP && q->r.loss_host)
+      std::memcpy(q->r.loss_host, sl->pinned + q->stage_out + (q->out_pinned ? 0 : up256(nn * 4)), sizeof(double));
+  }
   std::lock_guard<std::mutex> lk(s->mu);
-  finish_locked(s, q, kDone, LITHO_OK, nullptr);
+  for (Req* q : sl->batch) finish_locked(s, q, kDone, LITHO_OK, nullptr);
+  release_slot_locked(s, *sl);
 }
 
 constexpr double kInjectedDelayMs = 200.0;  // the injected slow request's device delay
 
-// Enqueues an admitted request on its slot's stream (called without the lock).
-litho_status launch(litho_server* s, Req* q, litho_kernels* h, std::string* err) {
-  Slot& sl = s->slots[q->slot];
-  const litho_request& r = q->r;
+// Enqueues an admitted batch on its slot's stream (called without the lock).
+// fault: the injected fault bits this batch takes (see litho_serve_inject_fault).
+litho_status launch(litho_server* s, Slot& sl, litho_kernels* h, int fault, std::string* err) {
+  const litho_request& r = sl.batch[0]->r;
+  const int b = int(sl.batch.size());
   const size_t nn = size_t(r.n) * r.n;
   const bool ilt = r.kind == LITHO_REQ_ILT_STEP;
-  const size_t in_bytes = nn * 4 * (ilt ? 2 : 1);
-  const size_t stage = up256(in_bytes) + up256(nn * 4) + 256;
-  if (sl.pinned_bytes < stage) {
-    if (sl.pinned) cudaFreeHost(sl.pinned);
-    sl.pinned = nullptr;
-    sl.pinned_bytes = 0;
-    if (cudaMallocHost(&sl.pinned, stage) != cudaSuccess) {
-      *err = "pinned staging allocation failed";
-      return LITHO_ENOMEM;
+  // pageable buffers go through the slot's pinned staging (sized at admission)
+  size_t off = 0;
+  for (Req* q : sl.batch) {
+    q->stage_in = off;
+    if (!q->in_pinned) {
+      std::memcpy(sl.pinned + off, q->r.input_host, nn * 4);
+      if (ilt) std::memcpy(sl.pinned + off + nn * 4, q->r.target_host, nn * 4);
+      off += up256(nn * 4 * (ilt ? 2 : 1));
     }
-    sl.pinned_bytes = stage;
+    q->stage_out = off;
+    off += (q->out_pinned ? 0 : up256(nn * 4)) + (ilt ? 256 : 0);
   }
-  // Pinned caller buffers are copied by DMA directly; pageable ones go through
-  // the slot's pinned staging buffer.
-  q->in_pinned = is_pinned(r.input_host) && (!ilt || is_pinned(r.target_host));
-  q->out_pinned = is_pinned(r.output_host);
-  if (!q->in_pinned) {
-    std::memcpy(sl.pinned, r.input_host, nn * 4);
-    if (ilt) std::memcpy(sl.pinned + nn * 4, r.target_host, nn * 4);
+  if (off > sl.pinned_bytes) {  // admission keeps batches within the staging; a guard, not a path
+    *err = "pinned staging too small for the batch";
+    return LITHO_ENOMEM;
   }
-  const size_t dev_bytes = q->footprint;
-  void* d = nullptr;
-  if (s->fault_mask.load() & 1) {
-    s->fault_mask.fetch_and(~1);
+  if (fault & 1) {
     *err = "injected device allocation failure";
     return LITHO_ENOMEM;
   }
-  if (s->fault_mask.load() & 2) {  // a slow request: a fixed device delay before its work
-    s->fault_mask.fetch_and(~2);
-    if (launch_delay(sl.stream, kInjectedDelayMs) != cudaSuccess) {
-      *err = "delay launch failed";
-      return LITHO_ECUDA;
-    }
+  if ((fault & 2) && launch_delay(sl.stream, kInjectedDelayMs) != cudaSuccess) {  // a slow batch
+    *err = "delay launch failed";
+    return LITHO_ECUDA;
   }
-  if (cudaMallocAsync(&d, dev_bytes, sl.stream) != cudaSuccess) {
+  void* d = nullptr;
+  if (cudaMallocAsync(&d, sl.footprint, sl.stream) != cudaSuccess) {
     cudaGetLastError();
     *err = "device allocation failed";
     return LITHO_ENOMEM;
   }
+  const size_t plane = up256(size_t(b) * nn * 4);
   char* base = static_cast<char*>(d);
   float* d_in = reinterpret_cast<float*>(base);
-  float* d_tg = ilt ? reinterpret_cast<float*>(base + up256(nn * 4)) : nullptr;
-  float* d_out = reinterpret_cast<float*>(base + up256(nn * 4) * (ilt ? 2 : 1));
-  char* ws = base + up256(nn * 4) * (ilt ? 3 : 2);
-  const size_t ws_bytes = dev_bytes - up256(nn * 4) * (ilt ? 3 : 2);
-  litho_status st = LITHO_OK;
+  float* d_tg = ilt ? reinterpret_cast<float*>(base + plane) : nullptr;
+  float* d_out = reinterpret_cast<float*>(base + plane * (ilt ? 2 : 1));
+  char* ws = base + plane * (ilt ? 3 : 2);
+  const size_t ws_bytes = sl.footprint - plane * (ilt ? 3 : 2);
   auto fail = [&](litho_status code, const char* what) {
     *err = what;
     cudaFreeAsync(d, sl.stream);
     return code;
   };
-  if (q->in_pinned) {
-    if (cudaMemcpyAsync(d_in, r.input_host, nn * 4, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess ||
-        (ilt && cudaMemcpyAsync(d_tg, r.target_host, nn * 4, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess))
+  for (int i = 0; i < b; ++i) {
+    const Req* q = sl.batch[i];
+    const void* src_in = q->in_pinned ? static_cast<const void*>(q->r.input_host) : sl.pinned + q->stage_in;
+    if (cudaMemcpyAsync(d_in + i * nn, src_in, nn * 4, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
       return fail(LITHO_ECUDA, "host-to-device copy failed");
-  } else if (cudaMemcpyAsync(d_in, sl.pinned, in_bytes, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess) {
-    return fail(LITHO_ECUDA, "host-to-device copy failed");
+    if (ilt) {
+      const void* src_tg =
+          q->in_pinned ? static_cast<const void*>(q->r.target_host) : sl.pinned + q->stage_in + nn * 4;
+      if (cudaMemcpyAsync(d_tg + i * nn, src_tg, nn * 4, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+        return fail(LITHO_ECUDA, "host-to-device copy failed");
+    }
   }
-  if (ilt) {
-    st = litho_ilt_grad(h, d_in, d_tg, 1, r.dose, r.mask_steep, r.resist_steep, r.threshold, r.sigma_nm,
-                        static_cast<litho_precision>(LITHO_PREC_FFT32 | LITHO_GRID_COARSE), d_out, nullptr, ws,
-                        ws_bytes, sl.stream);
-  } else {
-    st = litho_aerial(h, d_in, 1, r.dose, static_cast<litho_precision>(r.precision), d_out, ws, ws_bytes, sl.stream);
-  }
+  litho_status st;
+  if (ilt)
+    st = litho_ilt_grad(h, d_in, d_tg, b, r.dose, r.mask_steep, r.resist_steep, r.threshold, r.sigma_nm,
+                        static_cast<litho_precision>(call_precision(r)), d_out, nullptr, ws, ws_bytes, sl.stream);
+  else
+    st = litho_aerial(h, d_in, b, r.dose, static_cast<litho_precision>(r.precision), d_out, ws, ws_bytes, sl.stream);
   if (st != LITHO_OK) return fail(st, litho_last_error());
-  if (cudaMemcpyAsync(q->out_pinned ? static_cast<void*>(r.output_host) : sl.pinned + up256(in_bytes), d_out, nn * 4,
-                      cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
-    return fail(LITHO_ECUDA, "device-to-host copy failed");
-  if (ilt) {
-    double* loss_dev = ilt_loss_device(h, 1, ws, ws_bytes);
-    if (cudaMemcpyAsync(sl.pinned + up256(in_bytes) + up256(nn * 4), loss_dev, sizeof(double),
-                        cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+  const double* loss_dev = ilt ? ilt_loss_device(h, b, ws, ws_bytes) : nullptr;
+  for (int i = 0; i < b; ++i) {
+    const Req* q = sl.batch[i];
+    void* dst = q->out_pinned ? static_cast<void*>(q->r.output_host) : sl.pinned + q->stage_out;
+    if (cudaMemcpyAsync(dst, d_out + i * nn, nn * 4, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+      return fail(LITHO_ECUDA, "device-to-host copy failed");
+    if (ilt && cudaMemcpyAsync(sl.pinned + q->stage_out + (q->out_pinned ? 0 : up256(nn * 4)), loss_dev + i,
+                               sizeof(double), cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
       return fail(LITHO_ECUDA, "device-to-host copy failed");
   }
   cudaFreeAsync(d, sl.stream);
-  if (cudaLaunchHostFunc(sl.stream, on_done, q) != cudaSuccess) {
+  if (cudaLaunchHostFunc(sl.stream, on_batch_done, &sl) != cudaSuccess) {
     *err = "cudaLaunchHostFunc failed";
     return LITHO_ECUDA;
   }
@@ -310,25 +367,56 @@ void scheduler(litho_server* s) {
           ++it;
           continue;
         }
-        if (s->in_use + q->footprint > s->budget - std::min(s->budget, s->cache_bytes)) {
+        const size_t avail = s->budget - std::min(s->budget, s->cache_bytes);
+        if (s->in_use + q->footprint > avail) {
           const bool oldest = (it == s->queue.begin());
           if (oldest && ++q->skipped > 64) break;  // hold admission for the oldest request
           ++it;
           continue;
         }
-        it = s->queue.erase(it);
-        q->state = kRunning;
-        q->slot = free_slot;
-        s->slots[free_slot].busy = true;
+        Slot& sl = s->slots[free_slot];
+        // an injected fault applies to a batch of this request alone
+        const int fault = s->fault_mask.exchange(0);
+        std::vector<Req*> batch{q};
+        size_t fp = q->footprint, staging = staging_bytes(q);
+        double px = double(q->r.n) * q->r.n;
+        if (!fault) {
+          for (auto jt = std::next(it); jt != s->queue.end() && int(batch.size()) < kMaxBatch; ++jt) {
+            Req* q2 = *jt;
+            if (q2->bkey != q->bkey) continue;
+            if (px + double(q2->r.n) * q2->r.n > kMaxBatchPx) break;
+            const size_t fp2 = batch_bytes(q->r, q->crop, int(batch.size()) + 1);
+            if (s->in_use + fp2 > avail) break;
+            const size_t st2 = staging + staging_bytes(q2);
+            if (st2 > sl.pinned_bytes) continue;
+            batch.push_back(q2);
+            fp = fp2;
+            staging = st2;
+            px += double(q2->r.n) * q2->r.n;
+          }
+        }
+        for (Req* m : batch) {
+          s->queue.erase(std::find(s->queue.begin(), s->queue.end(), m));
+          m->state = kRunning;
+          m->slot = free_slot;
+        }
+        sl.busy = true;
+        sl.batch = batch;
+        sl.footprint = fp;
         s->running++;
-        s->in_use += q->footprint;
+        s->in_use += fp;
         s->high_water = std::max(s->high_water, s->in_use + s->cache_bytes);
+        s->batches++;
+        s->max_batch = std::max(s->max_batch, int(batch.size()));
         litho_kernels* h = ke.h;
         lk.unlock();
         std::string err;
-        litho_status st = launch(s, q, h, &err);
+        litho_status st = launch(s, sl, h, fault, &err);
         lk.lock();
-        if (st != LITHO_OK) finish_locked(s, q, kFailed, st, err.c_str());
+        if (st != LITHO_OK) {
+          for (Req* m : sl.batch) finish_locked(s, m, kFailed, st, err.c_str());
+          release_slot_locked(s, sl);
+        }
         admitted = true;
         break;
       }
@@ -395,6 +483,10 @@ litho_status litho_serve_create(size_t hbm_budget_bytes, int max_slots, int max_
   uint64_t keep = ~0ull;
   LITHO_TRY_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
   s->slots.resize(max_slots);
+  for (int i = 0; i < max_slots; ++i) {
+    s->slots[i].srv = s.get();
+    s->slots[i].index = i;
+  }
   // Pinned staging sized up front for the largest request (2048^2 ILT step:
   // theta, target, gradient), so no slot ever reallocates it: cudaFreeHost
   // and cudaMallocHost both wait for the whole device.
@@ -442,10 +534,13 @@ litho_status litho_serve_submit(litho_server* s, const litho_request* req, uint6
   if (r.optics.kind == LITHO_SRC_CUSTOM && r.optics.custom_w)
     q->custom.assign(r.optics.custom_w, r.optics.custom_w + size_t(r.optics.src_grid) * r.optics.src_grid);
   q->r.optics.custom_w = q->custom.empty() ? nullptr : q->custom.data();
-  const int crop = band_crop(r.optics, src, r.n, r.pixel_nm);
-  q->footprint = request_bytes(q->r, crop);
+  q->crop = band_crop(r.optics, src, r.n, r.pixel_nm);
+  q->footprint = batch_bytes(q->r, q->crop, 1);
   q->key = kernel_key(q->r, q->custom);
-  q->srv = s;
+  q->bkey = batch_key(q->r, q->key);
+  // pinned caller buffers are copied by DMA directly; pageable ones through the slot's staging
+  q->in_pinned = is_pinned(r.input_host) && (r.kind != LITHO_REQ_ILT_STEP || is_pinned(r.target_host));
+  q->out_pinned = is_pinned(r.output_host);
   std::lock_guard<std::mutex> lk(s->mu);
   if (s->stop) {
     set_error("server is shutting down");
@@ -541,6 +636,8 @@ litho_status litho_serve_stats(litho_server* s, litho_serve_stats_t* out) {
   const double span = s->last_done - s->first_submit;
   out->mpx_per_s = (span > 0 && s->completed) ? s->pixels / (span * 1e-3) / 1e6 : 0.0;
   out->hbm_high_water = s->high_water;
+  out->batches = s->batches;
+  out->max_batch = s->max_batch;
   int built = 0;
   for (auto& kv : s->cache) built += kv.second.h != nullptr;
   out->kernel_sets_cached = built;
@@ -556,6 +653,8 @@ litho_status litho_serve_stats_reset(litho_server* s) {
   s->last_done = 0.0;
   s->pixels = 0.0;
   s->high_water = s->in_use + s->cache_bytes;
+  s->batches = 0;
+  s->max_batch = 0;
   return LITHO_OK;
 }
 

@@ -57,7 +57,7 @@ class litho_request(ctypes.Structure):
 class litho_serve_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("rejected", c_uint64), ("cancelled", c_uint64),
                 ("p50_ms", c_double), ("p99_ms", c_double), ("mpx_per_s", c_double), ("hbm_high_water", c_size_t),
-                ("kernel_sets_cached", c_int)]
+                ("kernel_sets_cached", c_int), ("batches", c_uint64), ("max_batch", c_int)]
 
 
 # name -> (restype, argtypes); mirrors include/litho.h

@@ -177,3 +177,52 @@ def test_injected_slow_request_does_not_hold_the_others(litho_lib, cuda):
     for o in outs:
         assert np.array_equal(o, ref)
     srv.close()
+
+
+def test_queued_requests_of_one_key_run_as_batches(litho_lib, cuda):
+    """Continuous batching: while a slow request holds the only slot, 24 images and 6 ILT
+    steps of one kernel set queue up (half of the images in pinned buffers, half pageable);
+    when the slot frees they run as grouped calls, far fewer than one per request, and each
+    result is bit-identical to the request run alone."""
+    import torch
+    L = litho_lib
+    srv = L.Server(16 << 30, max_slots=1, max_queue=256)
+    opt = L.make_optics(**DUV)
+    m0 = synth.random_rect_mask(256, seed=9)
+    t, _ = srv.submit("image", opt, 256, 8.0, 0.0, 8, m0, np.zeros_like(m0))    # builds the kernel set
+    assert srv.poll(t, 60000) == L.OK
+    srv.inject_fault(2)                       # the next request holds the only slot for 200 ms
+    hold, _ = srv.submit("image", opt, 256, 8.0, 0.0, 8, m0, np.zeros_like(m0))
+    srv.stats_reset()
+    keep, jobs = [], []
+    for i in range(24):
+        m = synth.random_rect_mask(256, seed=300 + i)
+        if i % 2:
+            mp = torch.from_numpy(m).pin_memory()
+            op = torch.zeros_like(mp).pin_memory()
+            keep += [mp, op]
+            m, out = mp.numpy(), op.numpy()
+        else:
+            out = np.zeros_like(m)
+        tk, _ = srv.submit("image", opt, 256, 8.0, 0.0, 8, m, out)
+        jobs.append(("image", tk, m, None, out, None))
+    for i in range(6):
+        th, tg = synth.ilt_clip(256, 8.0, seed=700 + i)
+        th, tg = np.ascontiguousarray(th), np.ascontiguousarray(tg)
+        out = np.zeros_like(th)
+        tk, loss = srv.submit("ilt", opt, 256, 8.0, 0.0, 8, th, out, target_host=tg)
+        jobs.append(("ilt", tk, th, tg, out, loss))
+    status, _ = _wait_all(srv, L, [hold] + [j[1] for j in jobs], timeout_s=120)
+    assert all(v == L.OK for v in status.values()), status
+    s = srv.stats()
+    print(f"batches {s['batches']} for {s['completed']} requests, largest {s['max_batch']}")
+    assert s["max_batch"] >= 6 and s["batches"] <= 8
+    srv.close()
+    kern = L.litho_make_kernels(opt, 256, 8.0, [0.0], 8)
+    for kind, _, x, tg, out, loss in jobs:
+        xd = torch.from_numpy(np.ascontiguousarray(x)[None]).to(cuda)
+        if kind == "image":
+            assert np.array_equal(out, L.litho_aerial(kern, xd).cpu().numpy()[0, 0])
+        else:
+            g, lo = L.litho_ilt_grad(kern, xd, torch.from_numpy(tg[None]).to(cuda), precision="fft32/coarse")
+            assert np.array_equal(out, g.cpu().numpy()[0]) and loss[0] == lo[0]
