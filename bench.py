@@ -270,8 +270,8 @@ def ai_models(clips: int, n: int, ne: int, crop: int, k: int, coarse: bool, roun
 # holds only while they are unchanged.
 STAGE_SOURCES = {
     "stage1_fft": ["stage1.cuh", "fft.cu", "fft_common.cuh"],
-    "stage2_fft": ["fft.cu", "fft_common.cuh"],
-    "upsample_resist": ["stage1.cuh", "fft.cu", "fft_common.cuh"],
+    "stage2_fft": ["fft.cu", "fft_common.cuh", "stage2_w32.cu"],
+    "upsample_resist": ["stage1.cuh", "fft.cu", "fft_common.cuh", "interp.cu"],
 }
 
 
@@ -602,12 +602,14 @@ def run_aerial(args, ctx):
         e2e_step()
     ctx.barrier()
     e2e_steps = max(3, min(args.steps, 10))
-    e2e_ms = []
+    e2e_ms, e2e_trace = [], []
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         t1 = time.perf_counter()
         e2e_step()                       # synchronous: returns after the printed bytes are on the host
         e2e_ms.append(1e3 * (time.perf_counter() - t1))
+        tr = dict((tag, ms) for tag, ms in L.litho_host_trace_read())
+        e2e_trace.append((tr.get(-1, 0.0), tr.get(-2, 0.0) - tr.get(-1, 0.0)))
     e2e_s = ctx.max_over_ranks(time.perf_counter() - t0)
     ctx.barrier()
     e2e_val = whole_job_rate(clips * N * N * e2e_steps / 1e6, ctx.world, [e2e_s])
@@ -637,7 +639,11 @@ def run_aerial(args, ctx):
             "gpu_launches_per_step": head["launches"] / args.steps,
             "e2e": {"value": e2e_val, "unit": "Mpx/s", "h2d_bytes_per_step": int(mask_host.numel() * 4),
                     "d2h_bytes_per_step": int(printed_host.numel()), "steps": e2e_steps,
-                    "step_ms": [round(x, 3) for x in e2e_ms]},
+                    "step_ms": [round(x, 3) for x in e2e_ms],
+                    "host_trace": {"enqueue_ms": [round(a, 3) for a, _ in e2e_trace],
+                                   "wait_ms": [round(b, 3) for _, b in e2e_trace],
+                                   "note": "per call: host time to enqueue every chunk's copies and launches, "
+                                           "then the wait for the device (litho_host_trace_read)"}},
             "roofline": roof, "peaks_source": peak_src, "clocks": head["clocks"]}
     if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -213,6 +213,14 @@ litho_status litho_aerial_host_workspace_size(const litho_kernels* h, int b, lit
 litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, int b, double dose,
                                litho_precision prec, float* intensity_host, double sigma_nm, double threshold,
                                uint8_t* printed_host, void* workspace_dev, size_t workspace_bytes, void* stream);
+/* Host timestamps of the last completed litho_aerial_host call (any thread):
+ * event i has tag tags[i] and happened ms[i] milliseconds after the call
+ * began.  Tags: 8 c + 0 / 1 / 2 when chunk c's input copy, its kernels and
+ * its output copies had been enqueued; -1 when all work was enqueued and
+ * the final wait began; -2 when the wait ended.  Up to max_events are
+ * written; *count receives the number the call recorded.  A host-side stall
+ * shows as a late enqueue, a device-side one as a long wait. */
+litho_status litho_host_trace_read(int max_events, int* tags, double* ms, int* count);
 
 /* The FP32 aerial image (same result as litho_aerial with LITHO_PREC_FFT32)
  * without any device allocation and without a workspace argument.  The paper

@@ -1,5 +1,6 @@
 // C ABI entry points: kernel handles, aerial image, resist, error reporting.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -540,6 +541,21 @@ litho_status litho_aerial_resist(const litho_kernels* h, const float* mask_dev, 
 // kernels.  Each stream owns one region of the workspace.
 static int host_chunk_clips(int b) { return b >= 4 ? std::min(8, (b + 3) / 4) : b; }
 
+// Host timestamps of the last litho_aerial_host call (litho_host_trace_read):
+// when each chunk's copies and launches were issued and how long the final
+// wait took, to tell a host-side stall from a device-side one.
+namespace {
+struct HostTrace {
+  std::mutex mu;
+  std::vector<int> tags;
+  std::vector<double> ms;
+};
+HostTrace g_host_trace;
+double host_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
 static size_t host_region_bytes(const litho_kernels* h, int cb, litho_precision prec) {
   size_t w = 0;
   if (litho_aerial_workspace_size(h, cb, prec, &w) != LITHO_OK) return 0;
@@ -572,6 +588,13 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
   }
   const int cb = host_chunk_clips(b), F = h->n_focus;
   const size_t region = host_region_bytes(h, cb, prec);
+  std::vector<int> ttag;
+  std::vector<double> tms;
+  const double t_start = host_ms();
+  auto mark = [&](int tag) {
+    ttag.push_back(tag);
+    tms.push_back(host_ms() - t_start);
+  };
   size_t w = 0;
   litho_aerial_workspace_size(h, cb, prec, &w);
   w = align_up(w);
@@ -604,17 +627,21 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
         reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(dblur) + align_up(size_t(cb) * F * nn * sizeof(float)));
     LITHO_TRY_CUDA(cudaMemcpyAsync(dmask, mask_host + size_t(c0) * nn, size_t(nb) * nn * sizeof(float),
                                    cudaMemcpyHostToDevice, st));
+    mark(ci * 8 + 0);
     if (printed_host) {
       s = litho_aerial_resist(h, dmask, nb, dose, prec, dimg, sigma_nm, threshold, dblur, dpr, base, w, st);
       if (s != LITHO_OK) return s;
+      mark(ci * 8 + 1);
       LITHO_TRY_CUDA(cudaMemcpyAsync(printed_host + size_t(c0) * F * nn, dpr, planes * nn, cudaMemcpyDeviceToHost, st));
     } else {
       s = litho_aerial(h, dmask, nb, dose, prec, dimg, base, w, st);
       if (s != LITHO_OK) return s;
+      mark(ci * 8 + 1);
     }
     if (intensity_host)
       LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host + size_t(c0) * F * nn, dimg, planes * nn * sizeof(float),
                                      cudaMemcpyDeviceToHost, st));
+    mark(ci * 8 + 2);
   }
   if (cb < b) {
     for (int i = 0; i < 2; ++i) {
@@ -622,7 +649,26 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
       LITHO_TRY_CUDA(cudaStreamWaitEvent(caller, hm->host_events[1 + i], 0));
     }
   }
+  mark(-1);  // all work issued; the wait starts
   LITHO_TRY_CUDA(cudaStreamSynchronize(caller));
+  mark(-2);  // the wait ended
+  {
+    std::lock_guard<std::mutex> tl(g_host_trace.mu);
+    g_host_trace.tags.swap(ttag);
+    g_host_trace.ms.swap(tms);
+  }
+  return LITHO_OK;
+}
+
+litho_status litho_host_trace_read(int max_events, int* tags, double* ms, int* count) {
+  LITHO_REQUIRE(count && (max_events <= 0 || (tags && ms)), "null argument");
+  std::lock_guard<std::mutex> tl(g_host_trace.mu);
+  const int n = std::min<int>(std::max(0, max_events), int(g_host_trace.tags.size()));
+  for (int i = 0; i < n; ++i) {
+    tags[i] = g_host_trace.tags[i];
+    ms[i] = g_host_trace.ms[i];
+  }
+  *count = int(g_host_trace.tags.size());
   return LITHO_OK;
 }
 

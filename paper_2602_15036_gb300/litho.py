@@ -83,6 +83,7 @@ _SIGS = {
                                   c_void_p, c_void_p, c_size_t, c_void_p]),
     "litho_check_device": (c_int, [c_void_p, c_void_p]),
     "litho_selftest_wait_limit": (c_int, [c_void_p, c_double, c_void_p]),
+    "litho_host_trace_read": (c_int, [c_int, POINTER(c_int), POINTER(c_double), POINTER(c_int)]),
     "litho_aerial_noalloc": (c_int, [c_void_p, c_void_p, c_int, c_double, c_void_p, c_void_p]),
     "litho_aerial_noalloc_max_bytes": (c_size_t, []),
     "litho_resist": (c_int, [c_void_p, c_int, c_int, c_double, c_double, c_double, c_void_p, c_void_p, c_void_p]),
@@ -342,6 +343,15 @@ def litho_aerial_noalloc(kern: Kernels, mask, out, dose=1.0, stream=None):
     _check(lib().litho_aerial_noalloc(kern.handle, c_void_p(mask.data_ptr()), mask.shape[0], dose,
                                       c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
+
+
+def litho_host_trace_read(max_events: int = 256):
+    """Host timestamps of the last litho_aerial_host call: list of (tag, ms since the call began)."""
+    tags = (c_int * max_events)()
+    ms = (c_double * max_events)()
+    count = c_int()
+    _check(lib().litho_host_trace_read(max_events, tags, ms, byref(count)))
+    return [(tags[i], ms[i]) for i in range(min(count.value, max_events))]
 
 
 def litho_aerial_noalloc_max_bytes() -> int:
