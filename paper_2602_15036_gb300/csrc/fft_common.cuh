@@ -304,18 +304,27 @@ struct SmemLoadUnused {
   __device__ float2 operator()(int) const { return make_float2(0.f, 0.f); }
 };
 
+struct NoHook {
+  __device__ void operator()() const {}
+};
+
 // Full transform: first pass from `load`, middle passes in shared memory,
 // last pass into `use`.  Threads t in [0, NT) of the calling group take part;
 // every thread of the block must call it (it contains __syncthreads).
-template <int N, int SIGN, class Load, class Use, bool BANDED = false>
-__device__ __forceinline__ void fft_load_use(float2* buf, const float2* tw, int t, Load& load, Use& use) {
+// `after_first` runs in every thread once the first pass has finished in all
+// of them (after its closing barrier): whatever `load` read is free again.
+template <int N, int SIGN, class Load, class Use, bool BANDED = false, class Hook = NoHook>
+__device__ __forceinline__ void fft_load_use(float2* buf, const float2* tw, int t, Load& load, Use& use,
+                                             const Hook& after_first = Hook()) {
   using PL = Plan<N>;
   constexpr int NT = PL::NT;
   if constexpr (PL::P == 2) {
     pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false, Load, BANDED>(buf, tw, t, load);
+    after_first();
     pass_last<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1>(buf, tw, t, use);
   } else {
     pass_to_smem<N, NT, PL::R[0], 1, SIGN, 0, false, Load, BANDED>(buf, tw, t, load);
+    after_first();
     SmemLoadUnused none;
     pass_to_smem<N, NT, PL::R[1], PL::R[0], SIGN, TwOff<N>::p1, true>(buf, tw, t, none);
     pass_last<N, NT, PL::R[2], PL::R[0] * PL::R[1], SIGN, TwOff<N>::p2>(buf, tw, t, use);

@@ -3,8 +3,11 @@
 // for a block of W crop columns c and a run of kernels j.
 //
 // A CTA keeps the twiddle table in shared memory and loops over a run of kernels;
-// the next kernel's Phi block is copied in with cp.async (two buffers) while
-// the current block's W column transforms run.  The band multiply happens in
+// the next kernel's Phi block is copied in with cp.async while the current
+// block's W column transforms run.  The FP32 output takes one block buffer,
+// refilled as soon as the first pass (the only one that reads the block) is
+// done, so that two CTAs fit an SM's shared memory; the split 16-bit output
+// keeps two buffers.  The band multiply happens in
 // the first pass's load: the mask-spectrum values a thread multiplies are
 // the same for every kernel, so they are loaded once into registers.
 // Without kernels (phi == NULL) each j transforms its own spectrum mhat[j].
@@ -57,11 +60,21 @@ template <int N, int W>
 struct Stage1Shape {
   static_assert(W % 2 == 0, "W even: rows of whole 16-byte pieces");
   static constexpr int LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
-  static size_t smem_elems(int crop) { return size_t(N) + size_t(W) * LD + 2 * size_t(W) * crop; }
+  static size_t smem_elems(int crop, int buffers) {
+    return size_t(N) + size_t(W) * LD + size_t(buffers) * W * crop;
+  }
+};
+
+// Block buffers and CTAs per SM the launch bounds ask for: the FP32 output
+// single-buffers its Phi block and runs two CTAs per SM.
+template <class Out>
+struct Stage1Pipe {
+  static constexpr int kBuffers = Out::kRowWise ? 2 : 1;
+  static constexpr int kMinBlocks = Out::kRowWise ? 1 : 2;
 };
 
 template <int N, int W, class Out, bool BANDED>
-__global__ void __launch_bounds__(Plan<N>::NT * W)
+__global__ void __launch_bounds__(Plan<N>::NT * W, Stage1Pipe<Out>::kMinBlocks)
     k_stage1_cols(const float2* __restrict__ mhat, const float2* __restrict__ phi, int crop, int nk, int jb,
                   const float2* __restrict__ tw_g, Out out) {
   constexpr int NT = Plan<N>::NT, LD = Stage1Shape<N, W>::LD, T = W * NT;
@@ -98,9 +111,10 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     const bool zero = !phi || t >= NB0 || c < 0 || c >= crop || (BANDED && r >= R0 / 4 && r < 3 * R0 / 4);
     mreg[r] = zero ? make_float2(0.f, 0.f) : __ldg(mhat + (size_t)c * crop + u0 + g);
   }
+  constexpr bool kSingle = Stage1Pipe<Out>::kBuffers == 1;
   for (int j = j0; j < j1; ++j) {
-    const int s = (j - j0) & 1;
-    if (j + 1 < j1) {
+    const int s = kSingle ? 0 : (j - j0) & 1;
+    if (!kSingle && j + 1 < j1) {
       issue(j + 1, blk(s ^ 1));
       cp_async_wait_one();
     } else {
@@ -110,6 +124,10 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     // has finished transform j - 1, so buf and the other Phi buffer are free.
     __syncthreads();
     const float2* b = blk(s) + g;
+    // single buffer: the first pass has read block j in every thread, so block j + 1 may land
+    auto refill = [&]() {
+      if (kSingle && j + 1 < j1) issue(j + 1, blk(0));
+    };
     auto load = [&](int, int r, int idx) {
       const int c = (r < R0 / 2 ? idx : idx - N) + half;  // idx < N/2 exactly when r < R0/2
       if (c < 0 || c >= crop) return make_float2(0.f, 0.f);
@@ -127,7 +145,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
     } else {
       float2* const col = out.column(jofs + j, u0 + g);  // element y at col[y crop]
       auto use = [&](int, int, int y, float2 v) { col[y * crop] = v; };
-      fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf + g * LD, tw, t, load, use);
+      fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf + g * LD, tw, t, load, use, refill);
     }
   }
 }
@@ -149,7 +167,7 @@ cudaError_t launch_stage1_cols_t(const float2* mhat, const float2* phi, int nk, 
   const long long ctas = (long long)clips * (crop / W);
   const int jblocks = int(std::min<long long>(nk, std::max<long long>(1, (2LL * sms + ctas - 1) / ctas)));
   const int JB = (nk + jblocks - 1) / jblocks;
-  const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop);
+  const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop, Stage1Pipe<Out>::kBuffers);
   cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out, BANDED>, sm);
   if (e != cudaSuccess) return e;
   const dim3 grid = Out::kRowWise ? dim3(crop / W, clips, (nk + JB - 1) / JB) : dim3(clips, crop / W, (nk + JB - 1) / JB);
