@@ -217,9 +217,12 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
  * event i has tag tags[i] and happened ms[i] milliseconds after the call
  * began.  Tags: 8 c + 0 / 1 / 2 when chunk c's input copy, its kernels and
  * its output copies had been enqueued; -1 when all work was enqueued and
- * the final wait began; -2 when the wait ended.  Up to max_events are
- * written; *count receives the number the call recorded.  A host-side stall
- * shows as a late enqueue, a device-side one as a long wait. */
+ * the final wait began; -2 when the wait ended; and, in device time since
+ * the call's first work item started, 100 + 8 c + 0 / 1 / 2 when chunk c's
+ * input copy, its kernels and its output copies finished (CUDA events).  Up
+ * to max_events are written; *count receives the number the call recorded.
+ * A host-side stall shows as a late enqueue, a device-side one as a long
+ * wait, and the device times tell copies from kernels. */
 litho_status litho_host_trace_read(int max_events, int* tags, double* ms, int* count);
 
 /* The FP32 aerial image (same result as litho_aerial with LITHO_PREC_FFT32)

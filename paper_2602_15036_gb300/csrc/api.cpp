@@ -84,6 +84,12 @@ litho_status upload(litho_kernels* h) {
     LITHO_TRY_CUDA(cudaMalloc(dst, twc.size() * sizeof(float2)));
     LITHO_TRY_CUDA(cudaMemcpy(*dst, twc.data(), twc.size() * sizeof(float2), cudaMemcpyHostToDevice));
   }
+  if (N == 512 || h->nc == 512) {
+    std::vector<float2> t512(kAdj512TableLen);
+    adj512_table(t512.data());
+    LITHO_TRY_CUDA(cudaMalloc(&h->d_tw512, t512.size() * sizeof(float2)));
+    LITHO_TRY_CUDA(cudaMemcpy(h->d_tw512, t512.data(), t512.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
   if (N == 1024 || h->nc == 1024) {
     std::vector<float2> t32(kStage2W32TableLen);
     stage2_w32_table(t32.data());
@@ -130,10 +136,12 @@ void litho_free_kernels(litho_kernels* h) {
   if (h->d_twc_tc != h->d_twc) cudaFree(h->d_twc_tc);
   cudaFree(h->d_twc);
   cudaFree(h->d_tw32);
+  cudaFree(h->d_tw512);
   for (auto& s : h->host_streams)
     if (s) cudaStreamDestroy(s);
   for (auto& e : h->host_events)
     if (e) cudaEventDestroy(e);
+  for (auto& e : h->host_timing) cudaEventDestroy(e);
   gemm_free_operands(h);
   cudaSetDevice(cur);
   delete h;
@@ -604,6 +612,15 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
   litho_kernels* hm = const_cast<litho_kernels*>(h);
   // concurrent host-path calls on one kernel set share its two streams: one at a time
   std::lock_guard<std::mutex> lk(hm->host_mu);
+  // device timestamps: a start event on the caller's stream, then per chunk the end of its input
+  // copy, of its kernels and of its output copies on its lane (read after the final wait)
+  const int chunks = (b + cb - 1) / cb;
+  while (hm->host_timing.size() < size_t(1 + 3 * chunks)) {
+    cudaEvent_t e;
+    LITHO_TRY_CUDA(cudaEventCreate(&e));
+    hm->host_timing.push_back(e);
+  }
+  LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[0], caller));
   if (cb < b) {
     for (int i = 0; i < 2; ++i)
       if (!hm->host_streams[i]) LITHO_TRY_CUDA(cudaStreamCreateWithFlags(&hm->host_streams[i], cudaStreamNonBlocking));
@@ -627,20 +644,24 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
         reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(dblur) + align_up(size_t(cb) * F * nn * sizeof(float)));
     LITHO_TRY_CUDA(cudaMemcpyAsync(dmask, mask_host + size_t(c0) * nn, size_t(nb) * nn * sizeof(float),
                                    cudaMemcpyHostToDevice, st));
+    LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[1 + 3 * ci], st));
     mark(ci * 8 + 0);
     if (printed_host) {
       s = litho_aerial_resist(h, dmask, nb, dose, prec, dimg, sigma_nm, threshold, dblur, dpr, base, w, st);
       if (s != LITHO_OK) return s;
+      LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[2 + 3 * ci], st));
       mark(ci * 8 + 1);
       LITHO_TRY_CUDA(cudaMemcpyAsync(printed_host + size_t(c0) * F * nn, dpr, planes * nn, cudaMemcpyDeviceToHost, st));
     } else {
       s = litho_aerial(h, dmask, nb, dose, prec, dimg, base, w, st);
       if (s != LITHO_OK) return s;
+      LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[2 + 3 * ci], st));
       mark(ci * 8 + 1);
     }
     if (intensity_host)
       LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host + size_t(c0) * F * nn, dimg, planes * nn * sizeof(float),
                                      cudaMemcpyDeviceToHost, st));
+    LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[3 + 3 * ci], st));
     mark(ci * 8 + 2);
   }
   if (cb < b) {
@@ -652,6 +673,14 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
   mark(-1);  // all work issued; the wait starts
   LITHO_TRY_CUDA(cudaStreamSynchronize(caller));
   mark(-2);  // the wait ended
+  for (int ci = 0; ci < chunks; ++ci)
+    for (int k = 0; k < 3; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, hm->host_timing[0], hm->host_timing[1 + 3 * ci + k]) == cudaSuccess) {
+        ttag.push_back(100 + ci * 8 + k);
+        tms.push_back(ms);
+      }
+    }
   {
     std::lock_guard<std::mutex> tl(g_host_trace.mu);
     g_host_trace.tags.swap(ttag);

@@ -164,6 +164,62 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
   }
 }
 
+// cos and sin of 2 pi t / 32 for t in [0, 32) (exact mathematical constants rounded to float)
+__device__ __forceinline__ constexpr float cos32(int t) {
+  t &= 31;
+  if (t > 16) t = 32 - t;  // cos is even
+  const float c[17] = {1.0f, 0.98078528040323044913f, 0.92387953251128675613f, 0.83146961230254523708f,
+                       0.70710678118654752440f, 0.55557023301960222474f, 0.38268343236508977173f,
+                       0.19509032201612826785f, 0.0f, -0.19509032201612826785f, -0.38268343236508977173f,
+                       -0.55557023301960222474f, -0.70710678118654752440f, -0.83146961230254523708f,
+                       -0.92387953251128675613f, -0.98078528040323044913f, -1.0f};
+  return c[t];
+}
+__device__ __forceinline__ constexpr float sin32(int t) { return cos32(8 - t); }
+
+// 32-point DFT in registers, v'[q] = sum_r v[r] e^{SIGN 2 pi i r q / 32}: a
+// radix-2 decimation-in-frequency network, output in natural order.  BANDED:
+// v[r] for r in [8, 24) is zero and not read.
+template <int SIGN, bool BANDED>
+__device__ __forceinline__ void dft32(float2 (&v)[32]) {
+#pragma unroll
+  for (int span = 32 / 2; span >= 1; span /= 2) {
+#pragma unroll
+    for (int b = 0; b < 32; b += 2 * span) {
+#pragma unroll
+      for (int i = 0; i < span; ++i) {
+        float2 d;
+        if (BANDED && span == 32 / 2) {
+          if (i < 32 / 4) {
+            d = v[i];  // v[i + 16] is zero
+          } else {     // v[i] is zero
+            v[i] = v[i + span];
+            d = make_float2(-v[i].x, -v[i].y);
+          }
+        } else {
+          const float2 a = v[b + i], c = v[b + i + span];
+          v[b + i] = cadd(a, c);
+          d = csub(a, c);
+        }
+        const int t = i * (32 / (2 * span));  // twiddle e^{SIGN 2 pi i t / 32}
+        if (t != 0) {
+          if (t == 8) {
+            d = make_float2(-SIGN * d.y, SIGN * d.x);  // multiply by SIGN i
+          } else {
+            d = cmul(d, make_float2(cos32(t), SIGN * sin32(t)));
+          }
+        }
+        v[b + i + span] = d;
+      }
+    }
+  }
+  float2 o[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) o[q] = v[bitrev(q, 5)];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) v[q] = o[q];
+}
+
 // Radix plans: passes in order, product N.  NT = threads per transform.
 // Besides the powers of two, 896 = 16 x 8 x 7: the smallest grid that holds
 // the 2C - 1 frequencies of an image whose field band has C = 448 columns.

@@ -141,6 +141,141 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_adj_rows(const float2* __restri
   }
 }
 
+// Backward rows for 512-point rows, two rows per warp (same result as
+// k_adj_rows<512>): per kernel, E = inverse transform of the band row, P = G E,
+// U = forward transform of P on the crop columns.  512 = 16 x 32 in Stockham
+// order:
+//   inverse pass 1 (radix 16): lane l takes x[l + 32 r] of both rows -> 16 l + q;
+//   inverse pass 2 (radix 32): lanes 0-15 take row A, lanes 16-31 row B; lane j
+//     takes position j + 16 r, applies w^(r j) (w = e^{+2 pi i/512}) and forms a
+//     32-point DFT whose output q is E(x) at x = j + 16 q;
+//   forward pass 1 (radix 32): the forward transform's first butterfly j needs
+//     P(j + 16 r), r < 32 -- exactly what lane j holds, so P = G E and this
+//     pass stay in registers (output q at 32 j + q);
+//   forward pass 2 (radix 16): lane l takes position l + 32 r of both rows,
+//     applies conj(w)^(r l) and forms a 16-point DFT whose output q is U(u) at
+//     u = l + 32 q; the crop columns are stored.
+// Two shared-memory exchanges per row and kernel (padded i + i/16 and
+// i + i/32, conflict-free), no block barrier inside the kernel loop; the next
+// kernel's band rows are staged with cp.async while the current ones are
+// transformed.  BANDED: crop / 2 <= 128, so inputs r in [4, 12) of the first
+// pass are zero.
+constexpr int kAdjWarps = 8;
+constexpr int kAdjTw1 = 31 * 16, kAdjTw2 = 15 * 32;  // w^(r j), r < 32, j < 16; conj(w)^(r l), r < 16, l < 32
+constexpr int kAdjBuf = 512 + 32;                     // one row, either padding
+
+__device__ __forceinline__ void adj_cp16(void* smem_dst, const void* gmem_src) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+
+template <bool BANDED>
+__global__ void __launch_bounds__(32 * kAdjWarps, 2)
+    k_adj_rows_w512(const float2* __restrict__ t1, const float* __restrict__ lam, int nk, int crop,
+                    const float* __restrict__ g, const float2* __restrict__ tw_g, float2* __restrict__ u,
+                    int lam_period) {
+  constexpr int N = 512;
+  extern __shared__ float4 smem_raw[];
+  float2* tw1 = reinterpret_cast<float2*>(smem_raw);  // inverse pass 2: (r - 1) 16 + j
+  float2* tw2 = tw1 + kAdjTw1;                        // forward pass 2: (r - 1) 32 + l
+  float2* bufs = tw2 + kAdjTw2;                       // [warp][2 rows][kAdjBuf]
+  float2* stage0 = bufs + kAdjWarps * 2 * kAdjBuf;    // [warp][2 rows][crop]
+  for (int i = threadIdx.x; i < kAdjTw1 + kAdjTw2; i += blockDim.x) tw1[i] = tw_g[i];
+  __syncthreads();
+  const int lane = threadIdx.x % 32, wp = threadIdx.x / 32, half = crop / 2;
+  const int y0 = (blockIdx.x * kAdjWarps + wp) * 2, plane = blockIdx.y;
+  if (y0 >= N) return;  // no block barrier below
+  float2* buf = bufs + wp * 2 * kAdjBuf;
+  float2* stage = stage0 + (size_t)wp * 2 * crop;
+  const float* lp = lam + (plane % lam_period) * nk;
+  const size_t field = (size_t)N * crop;
+  const float2* t1p = t1 + (size_t)plane * nk * field;
+  float2* up = u + (size_t)plane * nk * field;
+  // this lane's row in passes 2 and 3 (inverse pass 2, forward pass 1) and its butterfly
+  const int rsel = lane / 16, jj = lane % 16;
+  float gv[32];  // G(y, jj + 16 q) of the lane's row
+  {
+    const float* grow = g + ((size_t)plane * N + y0 + rsel) * N;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) gv[q] = __ldg(grow + jj + 16 * q);
+  }
+  auto fetch = [&](int k) {  // band rows y0, y0 + 1 of kernel k: 2 x crop/2 pieces of 16 bytes
+    const float2* src = t1p + (size_t)k * field + (size_t)y0 * crop;
+    for (int i = lane; i < crop; i += 32) adj_cp16(stage + 2 * i, src + 2 * i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  fetch(0);
+  for (int k = 0; k < nk; ++k) {
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    // inverse pass 1 for both rows (lane l: x[l + 32 r])
+    float2 a[2][16];
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const float2* band = stage + row * crop;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        if (BANDED && r >= 4 && r < 12) {
+          a[row][r] = make_float2(0.f, 0.f);
+        } else {
+          const int idx = lane + 32 * r;
+          const int c = (r < 8 ? idx : idx - N) + half;
+          a[row][r] = (c >= 0 && c < crop) ? band[c] : make_float2(0.f, 0.f);
+        }
+      }
+    }
+    __syncwarp();  // both band rows are in registers: the staging buffer takes kernel k + 1
+    if (k + 1 < nk) fetch(k + 1);
+    if (lp[k] == 0.f) continue;  // a zero kernel: U is not written (the column pass skips it)
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      dft_reg<16, +1, BANDED>(a[row]);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) buf[row * kAdjBuf + pad16(16 * lane + q)] = a[row][q];
+    }
+    __syncwarp();
+    // inverse pass 2: lane j = jj of row rsel, positions j + 16 r
+    float2 v[32];
+    const float2* rb = buf + rsel * kAdjBuf;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      v[r] = rb[pad16(jj + 16 * r)];
+      if (r > 0) v[r] = cmul(v[r], tw1[(r - 1) * 16 + jj]);
+    }
+    __syncwarp();  // the row buffers are read; the forward pass writes them next
+    dft32<+1, false>(v);  // v[q] = E(jj + 16 q)
+    // P = G E, then forward pass 1 over the same 32 values
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = make_float2(v[q].x * gv[q], v[q].y * gv[q]);
+    dft32<-1, false>(v);  // output q at 32 jj + q
+    float2* wb = buf + rsel * kAdjBuf;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) wb[32 * jj + q + jj] = v[q];  // padded i + i/32 (i = 32 jj + q)
+    __syncwarp();
+    // forward pass 2 for both rows: lane l, positions l + 32 r
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const float2* fb = buf + row * kAdjBuf;
+      float2 b[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int i = lane + 32 * r;
+        b[r] = fb[i + i / 32];
+        if (r > 0) b[r] = cmul(b[r], tw2[(r - 1) * 32 + lane]);
+      }
+      dft_reg<16, -1, false>(b);  // b[q] = U(lane + 32 q)
+      float2* urow = up + (size_t)k * field + (size_t)(y0 + row) * crop;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int idx = lane + 32 * q;
+        const int c = (q < 8 ? idx : idx - N) + half;
+        if (c >= 0 && c < crop) urow[c] = b[q];
+      }
+    }
+    __syncwarp();  // the row buffers are free for the next kernel
+  }
+}
+
 template <int N> struct AdjW { static constexpr int W = ColW<N>::W; };
 
 // Backward columns: forward FFT over y of U_j[:, c], crop rows, times lam_j conj(Phi_j);
@@ -243,7 +378,15 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_grad_rows(const float2* __restr
 
 template <int N>
 cudaError_t adj_rows_n(const float2* t1, const float* lam, int nk, int crop, const float* g, const float2* tw,
-                       float2* u, int planes, int lam_period, cudaStream_t st) {
+                       float2* u, int planes, int lam_period, cudaStream_t st, const float2* tw512) {
+  if (N == 512 && tw512 && crop % 2 == 0 && crop / 2 <= 128) {  // two rows per warp
+    const size_t sm = sizeof(float2) * (kAdjTw1 + kAdjTw2 + kAdjWarps * 2 * (size_t(kAdjBuf) + crop));
+    cudaError_t e = smem_attrs(k_adj_rows_w512<true>, sm);
+    if (e != cudaSuccess) return e;
+    k_adj_rows_w512<true><<<dim3(N / (2 * kAdjWarps), planes), 32 * kAdjWarps, sm, st>>>(t1, lam, nk, crop, g,
+                                                                                          tw512, u, lam_period);
+    return cudaGetLastError();
+  }
   const size_t sm = sizeof(float2) * (N + 2 * PadLen<N>::value);
   auto kern = 2 * crop <= N ? k_adj_rows<N, true> : k_adj_rows<N, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -286,8 +429,9 @@ cudaError_t grad_rows_n(const float2* qf, int crop, float scale, const float* m,
   }
 
 cudaError_t launch_adj_rows(int n, const float2* t1, const float* lam, int nk, int crop, const float* g,
-                            const float2* tw, float2* u, int planes, int lam_period, cudaStream_t st) {
-#define CALL(N) adj_rows_n<N>(t1, lam, nk, crop, g, tw, u, planes, lam_period, st)
+                            const float2* tw, float2* u, int planes, int lam_period, cudaStream_t st,
+                            const float2* tw512) {
+#define CALL(N) adj_rows_n<N>(t1, lam, nk, crop, g, tw, u, planes, lam_period, st, tw512)
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
@@ -382,6 +526,20 @@ bool ilt_plan(const litho_kernels* h, int b, int planes, size_t bytes, int* P, i
 
 }  // namespace
 
+void adj512_table(float2* out) {
+  const double two_pi = 2.0 * 3.14159265358979323846;
+  for (int r = 1; r < 32; ++r)
+    for (int j = 0; j < 16; ++j) {
+      const double a = two_pi * double(r * j) / 512.0;
+      out[(r - 1) * 16 + j] = make_float2(float(std::cos(a)), float(std::sin(a)));
+    }
+  for (int r = 1; r < 16; ++r)
+    for (int l = 0; l < 32; ++l) {
+      const double a = two_pi * double(r * l) / 512.0;
+      out[kAdjTw1 + (r - 1) * 32 + l] = make_float2(float(std::cos(a)), float(-std::sin(a)));
+    }
+}
+
 double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes) {
   (void)h;
   (void)b;
@@ -424,7 +582,7 @@ litho_status ai_channels(const litho_kernels* h, const float* target, int b, dou
       float* ones = coarse ? L.ic : L.img;
       k_fill<<<256, 256, 0, st>>>(ones, float((double(N) / NE) * (double(N) / NE)), size_t(g) * NE * NE);
       LITHO_TRY_CUDA(cudaGetLastError());
-      LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, ones, twe, L.u, g, 1, st));
+      LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, ones, twe, L.u, g, 1, st, h->d_tw512));
       LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, g * K, K, st));
       k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, K, size_t(C) * C, L.s, 0);
       LITHO_TRY_CUDA(cudaGetLastError());
@@ -550,7 +708,7 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
         } else {
           LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
         }
-        LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, gsrc, twe, L.u, gp, P, st));
+        LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, gsrc, twe, L.u, gp, P, st, h->d_tw512));
         LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, gp * K, P * K, st));
         k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, P * K, size_t(C) * C, L.s, f0 > 0 ? 1 : 0);
         LITHO_TRY_CUDA(cudaGetLastError());
@@ -634,7 +792,8 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
         }
       }
       LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, p * K, NE, C, twe, L.t1, st, g));
-      LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, h->d_lambda + size_t(f0) * K, K, C, up, twe, L.u, g * p, p, st));
+      LITHO_TRY_CUDA(
+          launch_adj_rows(NE, L.t1, h->d_lambda + size_t(f0) * K, K, C, up, twe, L.u, g * p, p, st, h->d_tw512));
       LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
                                      twe, L.sk, g * p * K, p * K, st));
       k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, p * K, size_t(C) * C, L.s, f0 > f_first ? 1 : 0);

@@ -100,12 +100,16 @@ struct litho_kernels {
   float2* d_twc_tc = nullptr;              // FFT twiddle table for nc_tc (d_twc when nc_tc == nc)
   float2* d_tw32 = nullptr;                // second-pass twiddles of the warp-per-row 1024-point stage 2
                                            // (when N or nc is 1024, else NULL)
+  float2* d_tw512 = nullptr;               // twiddles of the 512-point adjoint rows, two rows per warp
+                                           // (when N or nc is 512, else NULL)
   litho::GemmOperands* gemm = nullptr;     // lazily built per precision
   int device = 0;
   // streams and events of the pipelined host-buffer path (created on first use)
   std::mutex host_mu;
   cudaStream_t host_streams[2] = {nullptr, nullptr};
   cudaEvent_t host_events[3] = {nullptr, nullptr, nullptr};
+  // timing events of the host-buffer path (one start, three per chunk), grown on demand
+  std::vector<cudaEvent_t> host_timing;
 };
 
 namespace litho {
@@ -164,6 +168,10 @@ cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n,
 // thread spinning on the SM clock for a fixed number of cycles, which always
 // ends.  The slow request of the serving tests.
 cudaError_t launch_delay(cudaStream_t st, double ms);
+
+// Twiddle table of the 512-point adjoint-rows kernel (ilt.cu): kAdj512TableLen entries.
+constexpr int kAdj512TableLen = 31 * 16 + 15 * 32;
+void adj512_table(float2* out);
 
 // Device address of the per-clip FP64 losses inside an ILT workspace (ilt.cu).
 double* ilt_loss_device(const litho_kernels* h, int b, void* workspace, size_t workspace_bytes);
