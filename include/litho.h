@@ -453,11 +453,15 @@ typedef struct {
  * requests.  Continuous batching: when a slot frees, the oldest request that
  * fits takes with it the queued requests that can share its launches (the
  * same optics, n, pixel, focus, k, kind, precision, dose and ILT constants),
- * in arrival order, up to 64 clips, and the batch runs as one grouped
+ * in arrival order, up to 64 clips and 8 x 2048^2 pixels of work (an ILT
+ * step counting twice), and the batch runs as one grouped
  * litho_aerial / litho_ilt_grad call; each request's result is the same,
  * bit for bit, as the request run alone.  Kernel sets are built once per
  * (optics, n, pixel, focus, k) and stay resident (the paper's GPU-residency
- * principle, its Section II.D). */
+ * principle, its Section II.D).  Batches take their device memory from the
+ * device's default memory pool, in which the server reserves its budget (at
+ * most half of the free memory) when it is created and which it trims when it
+ * is destroyed. */
 litho_status litho_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, litho_server** out);
 /* EBUSY if the queue is full; EINVAL if the request's footprint exceeds the
  * whole budget or its fields are invalid. */

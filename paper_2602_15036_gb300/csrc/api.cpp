@@ -487,7 +487,7 @@ static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, in
     {
       ProfScope ps(kStageStage2Fft, st, 1);
       LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda, K, NE, C, float(dose), tw, coarse ? L.ic : img, g * F,
-                                       (long long)K * NE * C, (long long)NE * NE, st, F, h->d_tw32));
+                                       (long long)K * NE * C, (long long)NE * NE, st, F, h->d_tw32, h->d_tw512));
     }
     if (coarse) {
       litho_status s = upsample(h, p, L, g * F, img, fr, size_t(c0) * F, st);

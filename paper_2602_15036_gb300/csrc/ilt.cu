@@ -567,7 +567,7 @@ litho_status ai_channels(const litho_kernels* h, const float* target, int b, dou
       LITHO_TRY_CUDA(launch_mask_spectrum(target + c0 * nn, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
       LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, K, NE, C, twe, L.t1, st, g));
       LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, g,
-                                       (long long)K * NE * C, (long long)NE * NE, st, 1, h->d_tw32));
+                                       (long long)K * NE * C, (long long)NE * NE, st, 1, h->d_tw32, h->d_tw512));
       if (coarse) {
         LITHO_TRY_CUDA(launch_mask_rows(L.ic, g, NE, C2, twe, L.mid, st));
         LITHO_TRY_CUDA(launch_interp_cols(L.mid, g, NE, N, C2, twe, h->d_tw, nullptr, L.big, st));
@@ -682,7 +682,7 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
         ProfScope ps(kStageIltForward, st, 5);
         LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, P * K, NE, C, twe, L.t1, st, g));
         LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, gp,
-                                         (long long)K * NE * C, (long long)NE * NE, st, P, h->d_tw32));
+                                         (long long)K * NE * C, (long long)NE * NE, st, P, h->d_tw32, h->d_tw512));
         if (coarse) {  // the blurred image straight from the interpolation (blur applied to the spectrum)
           LITHO_TRY_CUDA(launch_mask_rows(L.ic, gp, NE, C2, twe, L.mid, st));
           LITHO_TRY_CUDA(launch_interp_cols(L.mid, gp, NE, N, C2, twe, h->d_tw, L.gain, L.big, st));

@@ -150,14 +150,20 @@ cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int
 // Stage 2 FFT path: I[y][x] = dose * sum_j lam[j] |sum_c t1[j][y][c] e^{+2 pi i u_c x/N}|^2
 // for each of `planes` planes; plane p takes lam[(p mod lam_period) nk ...]
 // (lam_period <= 0: planes, no repetition).  With tw32 (the kernel set's
-// d_tw32) a 1024-point row takes the warp-per-row radix-32 kernel.
+// d_tw32) a 1024-point row takes the warp-per-row radix-32 kernel, with
+// tw512 (d_tw512) 512-point rows the two-rows-per-warp kernel.
 cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
                               long long img_plane_stride, cudaStream_t st, int lam_period = 0,
-                              const float2* tw32 = nullptr);
+                              const float2* tw32 = nullptr, const float2* tw512 = nullptr);
 // The warp-per-row stage 2 for 1024-point rows (stage2_w32.cu) and its
 // second-pass twiddle table (31 x 32 entries w^(r l), r in [1, 32), l in [0, 32)).
 bool stage2_w32_supported(int n, int crop);
+// The two-rows-per-warp stage 2 for 512-point rows (twiddles: the kernel set's d_tw512).
+bool stage2_w512_supported(int n, int crop);
+cudaError_t launch_stage2_w512(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
+                               const float2* tw512, float* img, int planes, long long t1_plane, long long img_plane,
+                               int lam_period, cudaStream_t st);
 void stage2_w32_table(float2* out);
 constexpr int kStage2W32TableLen = 31 * 32;
 cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n, int crop, float dose,

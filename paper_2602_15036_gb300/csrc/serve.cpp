@@ -11,8 +11,8 @@
 // Batching: the admitted request takes with it every queued request that
 // can share its launches: the same kernel set (optics, n, pixel, defocus, k),
 // kind, precision and scalar parameters (dose; the ILT step's resist and
-// sigmoid constants), in arrival order, up to kMaxBatch clips and kMaxBatchPx
-// pixels, while the batch's footprint fits the budget and its pageable
+// sigmoid constants), in arrival order, up to kMaxBatch clips and kMaxBatchWork
+// pixels (ILT steps counted twice), while the batch's footprint fits the budget and its pageable
 // buffers fit the slot's pinned staging.  So requests that arrived while the
 // GPU was busy run as one grouped call (litho_aerial / litho_ilt_grad on b
 // clips), which images the clips in shared launches.  A batch is enqueued on
@@ -82,8 +82,16 @@ struct Req {
   size_t stage_in = 0, stage_out = 0;          // offsets in the slot's pinned staging
 };
 
-constexpr int kMaxBatch = 64;                                 // clips per batch
-constexpr double kMaxBatchPx = 32.0 * 2048.0 * 2048.0;       // pixels per batch
+constexpr int kMaxBatch = 64;  // clips per batch
+// Work per batch, in pixels with an ILT step counting twice (it images and
+// back-propagates): 8 image clips of 2048^2.  Larger batches would leave one
+// slot with seconds of work while the others run dry.
+constexpr double kMaxBatchWork = 8.0 * 2048.0 * 2048.0;
+double work_px(const litho_request& r) { return double(r.n) * r.n * (r.kind == LITHO_REQ_ILT_STEP ? 2.0 : 1.0); }
+// Batches of at most this much work run on their slot's high-priority stream:
+// the GPU dispatches their thread blocks ahead of the waiting blocks of large
+// requests, so small requests are not held behind them.
+constexpr double kSmallBatchWork = 2.0 * 1024.0 * 1024.0;
 
 // True for page-locked (cudaHostAlloc / cudaHostRegister) host memory.
 bool is_pinned(const void* p) {
@@ -97,7 +105,8 @@ bool is_pinned(const void* p) {
 }
 
 struct Slot {
-  cudaStream_t stream = nullptr;
+  cudaStream_t stream = nullptr;      // the running batch's stream: one of the two below
+  cudaStream_t lo = nullptr, hi = nullptr;  // low and high stream priority
   bool busy = false;
   char* pinned = nullptr;
   size_t pinned_bytes = 0;
@@ -190,6 +199,7 @@ struct litho_server {
   std::map<std::string, litho::KernelEntry> cache;
   std::deque<std::string> build_queue;
   size_t in_use = 0, high_water = 0, cache_bytes = 0;
+  size_t reserved = 0;  // bytes reserved in the default memory pool at creation
   int running = 0;
   uint64_t next_ticket = 1, submitted = 0, completed = 0, rejected = 0, cancelled = 0;
   uint64_t batches = 0;  // batches launched in the statistics window
@@ -379,12 +389,12 @@ void scheduler(litho_server* s) {
         const int fault = s->fault_mask.exchange(0);
         std::vector<Req*> batch{q};
         size_t fp = q->footprint, staging = staging_bytes(q);
-        double px = double(q->r.n) * q->r.n;
+        double work = work_px(q->r);
         if (!fault) {
           for (auto jt = std::next(it); jt != s->queue.end() && int(batch.size()) < kMaxBatch; ++jt) {
             Req* q2 = *jt;
             if (q2->bkey != q->bkey) continue;
-            if (px + double(q2->r.n) * q2->r.n > kMaxBatchPx) break;
+            if (work + work_px(q2->r) > kMaxBatchWork) break;
             const size_t fp2 = batch_bytes(q->r, q->crop, int(batch.size()) + 1);
             if (s->in_use + fp2 > avail) break;
             const size_t st2 = staging + staging_bytes(q2);
@@ -392,7 +402,7 @@ void scheduler(litho_server* s) {
             batch.push_back(q2);
             fp = fp2;
             staging = st2;
-            px += double(q2->r.n) * q2->r.n;
+            work += work_px(q2->r);
           }
         }
         for (Req* m : batch) {
@@ -403,6 +413,7 @@ void scheduler(litho_server* s) {
         sl.busy = true;
         sl.batch = batch;
         sl.footprint = fp;
+        sl.stream = work <= kSmallBatchWork ? sl.hi : sl.lo;
         s->running++;
         s->in_use += fp;
         s->high_water = std::max(s->high_water, s->in_use + s->cache_bytes);
@@ -492,10 +503,32 @@ litho_status litho_serve_create(size_t hbm_budget_bytes, int max_slots, int max_
   // and cudaMallocHost both wait for the whole device.
   const size_t nn = size_t(2048) * 2048;
   const size_t stage = up256(nn * 4 * 2) + up256(nn * 4) + 256;
+  int prio_lo = 0, prio_hi = 0;  // numerically lower is higher priority
+  LITHO_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
   for (auto& sl : s->slots) {
-    LITHO_TRY_CUDA(cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking));
+    LITHO_TRY_CUDA(cudaStreamCreateWithPriority(&sl.lo, cudaStreamNonBlocking, prio_lo));
+    LITHO_TRY_CUDA(cudaStreamCreateWithPriority(&sl.hi, cudaStreamNonBlocking, prio_hi));
+    sl.stream = sl.lo;
     LITHO_TRY_CUDA(cudaMallocHost(&sl.pinned, stage));
     sl.pinned_bytes = stage;
+  }
+  // Reserve the budget in the pool now (at most half of the free memory): the
+  // scheduler thread allocates each batch with cudaMallocAsync, and a pool
+  // that must grow maps memory inside that call, which holds up every later
+  // admission.  One allocation and its free leave the pages mapped in the
+  // pool (release threshold above), so batches are carved from them.
+  size_t free_b = 0, total_b = 0;
+  LITHO_TRY_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  s->reserved = std::min(hbm_budget_bytes, free_b / 2);
+  if (s->reserved > 0) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, s->reserved, s->slots[0].stream) == cudaSuccess) {
+      LITHO_TRY_CUDA(cudaFreeAsync(p, s->slots[0].stream));
+      LITHO_TRY_CUDA(cudaStreamSynchronize(s->slots[0].stream));
+    } else {
+      cudaGetLastError();  // the reservation is an optimisation: carry on without it
+      s->reserved = 0;
+    }
   }
   litho_server* raw = s.release();
   raw->sched = std::thread(scheduler, raw);
@@ -680,14 +713,19 @@ void litho_serve_destroy(litho_server* s) {
   if (s->sched.joinable()) s->sched.join();
   if (s->builder.joinable()) s->builder.join();
   for (auto& sl : s->slots) {
-    if (sl.stream) {
-      cudaStreamSynchronize(sl.stream);
-      cudaStreamDestroy(sl.stream);
+    for (cudaStream_t st : {sl.lo, sl.hi}) {
+      if (!st) continue;
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
     }
     if (sl.pinned) cudaFreeHost(sl.pinned);
   }
   for (auto& kv : s->cache)
     if (kv.second.h) litho_free_kernels(kv.second.h);
+  if (s->reserved) {  // hand the reservation back to the device
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, s->device) == cudaSuccess) cudaMemPoolTrimTo(pool, 0);
+  }
   delete s;
 }
 

@@ -1,4 +1,5 @@
-// Stage 2 of the FP32 path for 1024-point rows, one warp per row (paper
+// Stage 2 of the FP32 path for 1024-point rows, one warp per row, and for
+// 512-point rows, two rows per warp (paper
 // Eq. (4): I(y, x) = dose sum_k lam_k |sum_u T_k(y, u) e^{+2 pi i u x / N}|^2).
 //
 // The 1024-point inverse transform of a row is two radix-32 passes
@@ -132,6 +133,91 @@ cudaError_t launch_w32_t(const float2* t1, const float* lam, int nk, int crop, f
   return cudaGetLastError();
 }
 
+// The same stage 2 for 512-point rows, two rows per warp (512 = 16 x 32):
+// lane l takes x[l + 32 r] of both rows for the first (radix-16) pass; in the
+// second (radix-32) pass lanes 0-15 take row A and lanes 16-31 row B, lane j
+// applying w^(r j) to positions j + 16 r and forming the 32-point DFT whose
+// output q is the sample x = j + 16 q.  One padded exchange (i + i/16) per
+// row and kernel; lam |E|^2 accumulates in registers.  The second-pass
+// twiddles are the first 31 x 16 entries of the kernel set's 512-point
+// table (w^(r j), r in [1, 32), j in [0, 16)).
+constexpr int kW512Warps = 8, kW512Buf = 512 + 32;
+
+template <bool BANDED>
+__global__ void __launch_bounds__(32 * kW512Warps, 2)
+    k_stage2_w512(const float2* __restrict__ t1, const float* __restrict__ lam, int nk, int crop, float dose,
+                  const float2* __restrict__ tw_g, float* __restrict__ img, long long t1_plane, long long img_plane,
+                  int lam_period) {
+  constexpr int N = 512;
+  extern __shared__ float4 smem_raw[];
+  float2* tw = reinterpret_cast<float2*>(smem_raw);  // (r - 1) 16 + j
+  float2* bufs = tw + 31 * 16;                        // [warp][2 rows][kW512Buf]
+  float2* stage0 = bufs + kW512Warps * 2 * kW512Buf;  // [warp][2 rows][crop]
+  for (int i = threadIdx.x; i < 31 * 16; i += blockDim.x) tw[i] = tw_g[i];
+  __syncthreads();
+  const int lane = threadIdx.x % 32, wp = threadIdx.x / 32, half = crop / 2;
+  const int y0 = (blockIdx.x * kW512Warps + wp) * 2, plane = blockIdx.y;
+  if (y0 >= N) return;  // no block barrier below
+  float2* buf = bufs + wp * 2 * kW512Buf;
+  float2* stage = stage0 + (size_t)wp * 2 * crop;
+  const float* lp = lam + (plane % lam_period) * nk;
+  const float2* base = t1 + plane * t1_plane + (size_t)y0 * crop;
+  const int rsel = lane / 16, jj = lane % 16;
+  auto fetch = [&](int k) {  // band rows y0, y0 + 1 of kernel k
+    const float2* src = base + (size_t)k * N * crop;
+    for (int i = lane; i < crop; i += 32) cp_async16(stage + 2 * i, src + 2 * i);
+    cp_async_commit();
+  };
+  float acc[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) acc[q] = 0.f;
+  fetch(0);
+  for (int k = 0; k < nk; ++k) {
+    cp_async_wait<0>();
+    __syncwarp();
+    float2 a[2][16];
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      const float2* band = stage + row * crop;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        if (BANDED && r >= 4 && r < 12) {
+          a[row][r] = make_float2(0.f, 0.f);
+        } else {
+          const int idx = lane + 32 * r;
+          const int c = (r < 8 ? idx : idx - N) + half;
+          a[row][r] = (c >= 0 && c < crop) ? band[c] : make_float2(0.f, 0.f);
+        }
+      }
+    }
+    __syncwarp();  // both rows are in registers: the staging buffer takes kernel k + 1
+    if (k + 1 < nk) fetch(k + 1);
+    const float l = __ldg(lp + k);
+    if (l == 0.f) continue;  // a zero kernel (beyond the rank): uniform across the warp
+#pragma unroll
+    for (int row = 0; row < 2; ++row) {
+      dft_reg<16, +1, BANDED>(a[row]);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) buf[row * kW512Buf + pad16(16 * lane + q)] = a[row][q];
+    }
+    __syncwarp();
+    float2 v[32];
+    const float2* rb = buf + rsel * kW512Buf;
+#pragma unroll
+    for (int r = 0; r < 32; ++r) {
+      v[r] = rb[pad16(jj + 16 * r)];
+      if (r > 0) v[r] = cmul(v[r], tw[(r - 1) * 16 + jj]);
+    }
+    __syncwarp();  // the row buffers are free for the next kernel
+    dft32<+1, false>(v);
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = fmaf(l, fmaf(v[q].x, v[q].x, v[q].y * v[q].y), acc[q]);
+  }
+  float* out = img + plane * img_plane + (size_t)(y0 + rsel) * N;
+#pragma unroll
+  for (int q = 0; q < 32; ++q) out[jj + 16 * q] = dose * acc[q];
+}
+
 }  // namespace
 
 // crop: even (16-byte row pieces) and at most 512 (staging buffers within shared memory)
@@ -143,6 +229,29 @@ void stage2_w32_table(float2* out) {
       const double a = 2.0 * 3.14159265358979323846 * double(r * l) / double(kN);
       out[(r - 1) * kR + l] = make_float2(float(std::cos(a)), float(std::sin(a)));
     }
+}
+
+bool stage2_w512_supported(int n, int crop) { return n == 512 && crop >= 2 && crop <= 256 && crop % 2 == 0; }
+
+cudaError_t launch_stage2_w512(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
+                               const float2* tw512, float* img, int planes, long long t1_plane, long long img_plane,
+                               int lam_period, cudaStream_t st) {
+  if (!stage2_w512_supported(n, crop) || !tw512) return cudaErrorInvalidValue;
+  if (lam_period <= 0) lam_period = planes;
+  const dim3 grid(512 / (2 * kW512Warps), planes);
+  const size_t sm = sizeof(float2) * (31 * 16 + kW512Warps * 2 * (size_t(kW512Buf) + crop));
+  if (crop / 2 <= 128) {  // the band leaves indices [N/4, 3N/4) empty
+    cudaError_t e = smem_attrs(k_stage2_w512<true>, sm);
+    if (e != cudaSuccess) return e;
+    k_stage2_w512<true><<<grid, 32 * kW512Warps, sm, st>>>(t1, lam, nk, crop, dose, tw512, img, t1_plane, img_plane,
+                                                           lam_period);
+  } else {
+    cudaError_t e = smem_attrs(k_stage2_w512<false>, sm);
+    if (e != cudaSuccess) return e;
+    k_stage2_w512<false><<<grid, 32 * kW512Warps, sm, st>>>(t1, lam, nk, crop, dose, tw512, img, t1_plane,
+                                                            img_plane, lam_period);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
