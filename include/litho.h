@@ -396,7 +396,8 @@ litho_status litho_ilt_workspace_size(const litho_kernels* h, int b, size_t* ful
  *   m = sigmoid(mask_steep * theta), I_f = dose * SOCS_f(m), Ib_f = g (x) I_f,
  *   Z_f = sigmoid(resist_steep * (Ib_f - threshold)),
  *   loss = sum_f sum_x (Z_f - target)^2,   grad = d loss / d theta.
- * theta_dev, target_dev, grad_dev: float32 [b][n][n] on the device.
+ * theta_dev, target_dev, grad_dev: float32 [b][n][n] on the device (theta_dev
+ * 16-byte aligned, else EINVAL).
  * loss_host (may be NULL): b doubles, reduced in FP64 on the device; when
  * given, the call waits for the stream.  A workspace between min_bytes and
  * full_bytes selects recomputation of the forward fields; below min_bytes is

@@ -39,9 +39,13 @@ constexpr int kPartials = 1024;  // blocks of k_resist_grad, fixed for a determi
 
 __device__ __forceinline__ int freq_of_idx(int idx, int n) { return idx < n / 2 ? idx : idx - n; }
 
-__global__ void k_sigmoid(const float* __restrict__ theta, float alpha, float* __restrict__ m, size_t count) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
-    m[i] = 1.0f / (1.0f + expf(-alpha * theta[i]));
+// m = sigmoid(alpha theta), four values per thread and step (count a multiple of 4, 16-byte aligned)
+__global__ void k_sigmoid(const float4* __restrict__ theta, float alpha, float4* __restrict__ m, size_t count4) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count4; i += (size_t)gridDim.x * blockDim.x) {
+    const float4 t = theta[i];
+    m[i] = make_float4(1.0f / (1.0f + expf(-alpha * t.x)), 1.0f / (1.0f + expf(-alpha * t.y)),
+                       1.0f / (1.0f + expf(-alpha * t.z)), 1.0f / (1.0f + expf(-alpha * t.w)));
+  }
 }
 
 // Clip blockIdx.y: its `planes` planes of ib and q, its target, its
@@ -55,12 +59,16 @@ __global__ void __launch_bounds__(256) k_resist_grad(const float* __restrict__ i
   target += clip * nn;
   partial += clip * gridDim.x;
   double acc = 0.0;
-  const size_t total = nn * planes;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+  const size_t total = nn * planes, stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t pix = i % nn;  // i mod nn, carried along instead of recomputed
+  for (; i < total; i += stride) {
     const float z = 1.0f / (1.0f + expf(-beta * (ib[i] - thr)));
-    const float d = z - target[i % nn];
+    const float d = z - target[pix];
     acc += double(d) * double(d);
     q[i] = 2.0f * d * beta * z * (1.0f - z);
+    pix += stride;
+    while (pix >= nn) pix -= nn;
   }
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   __shared__ double ws[8];
@@ -276,42 +284,50 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2)
   }
 }
 
-template <int N> struct AdjW { static constexpr int W = ColW<N>::W; };
-
 // Backward columns: forward FFT over y of U_j[:, c], crop rows, times lam_j conj(Phi_j);
-// field j uses kernel j mod period.
+// field j uses kernel j mod period.  W columns per CTA with the lanes of a
+// warp interleaved over them (as in stage 1): the first pass reads U straight
+// from global memory (W adjacent columns of 32/W rows per warp load: whole
+// sectors), the last pass writes the cropped, weighted outputs from
+// registers, and a CTA runs `jb` fields in turn so that its twiddle table is
+// loaded once.
+template <int N> struct AdjW { static constexpr int W = Plan<N>::NT <= 64 ? 8 : 4; };
+
 template <int N>
 __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const float2* __restrict__ u,
                                                                         const float2* __restrict__ phi,
                                                                         const float* __restrict__ lam, int crop,
                                                                         const float2* __restrict__ tw_g,
-                                                                        float2* __restrict__ sk, int period) {
-  constexpr int W = AdjW<N>::W, NT = Plan<N>::NT, LD = ColLD<N>::value;
+                                                                        float2* __restrict__ sk, int period,
+                                                                        int fields, int jb) {
+  constexpr int W = AdjW<N>::W, NT = Plan<N>::NT, LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
-  const int j = blockIdx.y, jk = j % period, c0 = blockIdx.x * W, tid = threadIdx.x, half = crop / 2;
-  const float l = lam[jk];
-  float2* dst = sk + (size_t)j * crop * crop + c0;
-  if (l == 0.f) {  // uniform across the block
-    for (int i = tid; i < crop * W; i += blockDim.x) dst[(size_t)(i / W) * crop + i % W] = make_float2(0.f, 0.f);
-    return;
-  }
+  const int tid = threadIdx.x, g = tid % W, t = tid / W, c0 = blockIdx.x * W, half = crop / 2;
+  const int j0 = blockIdx.y * jb, j1 = min(fields, j0 + jb);
   load_twiddles<N>(tw, tw_g);
-  const float2* src = u + (size_t)j * N * crop + c0;
-  for (int i = tid; i < N * W; i += blockDim.x) {
-    const int y = i / W, w = i % W;
-    buf[w * LD + pad16(y)] = src[(size_t)y * crop + w];
-  }
   __syncthreads();
-  fft_smem<N, -1>(buf + (tid / NT) * LD, tw, tid % NT);
-  const float2* ph = phi + (size_t)jk * crop * crop + c0;
-  for (int i = tid; i < crop * W; i += blockDim.x) {
-    const int cv = i / W, w = i % W;
-    const float2 h = buf[w * LD + pad16((cv - half + N) % N)];
-    const float2 p = __ldg(ph + (size_t)cv * crop + w);
-    // lam conj(p) h
-    dst[(size_t)cv * crop + w] = make_float2(l * (p.x * h.x + p.y * h.y), l * (p.x * h.y - p.y * h.x));
+  for (int j = j0; j < j1; ++j) {
+    const int jk = j % period;
+    const float l = lam[jk];
+    float2* dst = sk + (size_t)j * crop * crop + c0 + g;  // crop row cv at dst[cv crop]
+    if (l == 0.f) {  // uniform across the block
+      for (int cv = t; cv < crop; cv += NT) dst[(size_t)cv * crop] = make_float2(0.f, 0.f);
+      continue;
+    }
+    const float2* src = u + (size_t)j * N * crop + c0 + g;  // row y at src[y crop]
+    const float2* ph = phi + (size_t)jk * crop * crop + c0 + g;
+    auto load = [&](int y) { return __ldg(src + (size_t)y * crop); };
+    auto use = [&](int, int, int idx, float2 h) {
+      const int cv = freq_of_idx(idx, N) + half;
+      if (cv >= 0 && cv < crop) {
+        const float2 p = __ldg(ph + (size_t)cv * crop);
+        // lam conj(p) h
+        dst[(size_t)cv * crop] = make_float2(l * (p.x * h.x + p.y * h.y), l * (p.x * h.y - p.y * h.x));
+      }
+    };
+    fft_load_use<N, -1>(buf + g * LD, tw, t, load, use);
   }
 }
 
@@ -399,10 +415,24 @@ template <int N>
 cudaError_t adj_cols_n(const float2* u, const float2* phi, const float* lam, int crop, const float2* tw, float2* sk,
                        int planes, int period, cudaStream_t st) {
   constexpr int W = AdjW<N>::W;
-  const size_t sm = sizeof(float2) * (N + W * ColLD<N>::value);
+  if (crop % W != 0) return cudaErrorInvalidValue;
+  constexpr int LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
+  const size_t sm = sizeof(float2) * (N + W * LD);
   cudaError_t e = smem_attrs(k_adj_cols<N>, sm);
   if (e != cudaSuccess) return e;
-  k_adj_cols<N><<<dim3(crop / W, planes), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, sk, period);
+  // fields per CTA: about four waves of CTAs over the GPU, at least one field each
+  static int sms = 0;  // the same GPU model throughout a process
+  if (!sms) {
+    int dev = 0, v = 0;
+    sms = cudaGetDevice(&dev) == cudaSuccess &&
+                  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0
+              ? v
+              : 152;
+  }
+  const long long cols = crop / W;
+  const int jb = int(std::max<long long>(1, (long long)planes * cols / (8LL * sms)));
+  k_adj_cols<N><<<dim3(crop / W, (planes + jb - 1) / jb), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, sk,
+                                                                                     period, planes, jb);
   return cudaGetLastError();
 }
 
@@ -631,6 +661,10 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
     set_error("workspace must be 256-byte aligned");
     return LITHO_EINVAL;
   }
+  if ((reinterpret_cast<uintptr_t>(theta_dev) & 15) != 0) {
+    set_error("theta must be 16-byte aligned");
+    return LITHO_EINVAL;
+  }
   ResistTaps taps;
   std::string why;
   if (!resist_taps(sigma_nm, h->pixel_nm, &taps, &why)) {
@@ -671,7 +705,12 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
     const int g = std::min(G, b - c0), gp = g * P;
     {
       ProfScope ps(kStageIltForward, st, 3);
-      k_sigmoid<<<256, 256, 0, st>>>(theta_dev + c0 * nn, float(mask_steep), L.m, size_t(g) * nn);
+      {
+        const size_t c4 = size_t(g) * nn / 4;  // nn = N^2 with N >= 32: a multiple of 4
+        const int blocks = int(std::min<size_t>((c4 + 255) / 256, 4096));
+        k_sigmoid<<<blocks, 256, 0, st>>>(reinterpret_cast<const float4*>(theta_dev + c0 * nn), float(mask_steep),
+                                          reinterpret_cast<float4*>(L.m), c4);
+      }
       LITHO_TRY_CUDA(cudaGetLastError());
       LITHO_TRY_CUDA(launch_mask_spectrum(L.m, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
     }
