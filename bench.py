@@ -609,14 +609,12 @@ def run_aerial(args, ctx):
         e2e_step()                       # synchronous: returns after the printed bytes are on the host
         e2e_ms.append(1e3 * (time.perf_counter() - t1))
         tr = dict((tag, ms) for tag, ms in L.litho_host_trace_read())
-        # device time per chunk: input copy, kernels, output copies (from the previous stage's end)
+        # device time per chunk, ms since the call's first work: input copied, kernels done, outputs copied
         dev = []
         for c in range(64):
             if 100 + 8 * c not in tr:
                 break
-            t_in, t_k, t_out = (tr[100 + 8 * c + i] for i in range(3))
-            t_prev = tr.get(100 + 8 * (c - 2) + 2, 0.0) if c >= 2 else 0.0     # chunks alternate two streams
-            dev.append((round(t_in - t_prev, 3), round(t_k - t_in, 3), round(t_out - t_k, 3)))
+            dev.append(tuple(round(tr[100 + 8 * c + i], 3) for i in range(3)))
         e2e_trace.append((tr.get(-1, 0.0), tr.get(-2, 0.0) - tr.get(-1, 0.0), dev))
     e2e_s = ctx.max_over_ranks(time.perf_counter() - t0)
     ctx.barrier()
@@ -652,9 +650,9 @@ def run_aerial(args, ctx):
                                    "wait_ms": [round(b, 3) for _, b, _ in e2e_trace],
                                    "chunk_device_ms": [c for _, _, c in e2e_trace],
                                    "note": "per call: host time to enqueue every chunk's copies and launches, "
-                                           "then the wait for the device; per chunk (input copy, kernels, output "
-                                           "copies) in device ms, each from the end of the previous item on its "
-                                           "stream (litho_host_trace_read)"}},
+                                           "then the wait for the device; per chunk the device times (ms since "
+                                           "the call's first work) at which its input copy, its kernels and its "
+                                           "output copies ended (litho_host_trace_read)"}},
             "roofline": roof, "peaks_source": peak_src, "clocks": head["clocks"]}
     if ctx.rank == 0 and ctx.world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()

@@ -205,10 +205,11 @@ litho_status litho_selftest_wait_limit(const litho_kernels* h, double limit_ms, 
  * litho_resist threshold of the blurred image with sigma_nm and threshold) is
  * non-NULL, then waits for the stream.  Device buffers are carved from
  * workspace_dev (litho_aerial_host_workspace_size bytes).  Batches of 4 or more
- * clips run in chunks alternating between two library streams (ordered after
- * `stream`), so that one chunk's copies overlap another chunk's kernels;
- * pinned host memory lets the copies run asynchronously at full link speed.
- * Calls on the same kernel set are serialised. */
+ * clips run in chunks on three library streams (ordered after `stream`):
+ * input copies, the kernels of one chunk after another, and output copies,
+ * so that neighbouring chunks' copies overlap the kernels; pinned host
+ * memory lets the copies run asynchronously at full link speed.  Calls on
+ * the same kernel set are serialised. */
 litho_status litho_aerial_host_workspace_size(const litho_kernels* h, int b, litho_precision prec, size_t* bytes);
 litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, int b, double dose,
                                litho_precision prec, float* intensity_host, double sigma_nm, double threshold,

@@ -142,6 +142,7 @@ void litho_free_kernels(litho_kernels* h) {
   for (auto& e : h->host_events)
     if (e) cudaEventDestroy(e);
   for (auto& e : h->host_timing) cudaEventDestroy(e);
+  for (auto& e : h->host_sync) cudaEventDestroy(e);
   gemm_free_operands(h);
   cudaSetDevice(cur);
   delete h;
@@ -544,9 +545,11 @@ litho_status litho_aerial_resist(const litho_kernels* h, const float* mask_dev, 
   return aerial_run(h, mask_dev, b, dose, p, coarse, intensity_dev, L, &fr, st);
 }
 
-// The host-buffer path images the batch in chunks of clips that alternate
-// between two streams, so that one chunk's copies overlap another chunk's
-// kernels.  Each stream owns one region of the workspace.
+// The host-buffer path images the batch in chunks of clips on three library
+// streams: input copies, kernels (one chunk after another, as the device
+// path runs them) and output copies, ordered by events, so that the copies
+// of neighbouring chunks overlap the kernels.  Chunks alternate between two
+// regions of the workspace.
 static int host_chunk_clips(int b) { return b >= 4 ? std::min(8, (b + 3) / 4) : b; }
 
 // Host timestamps of the last litho_aerial_host call (litho_host_trace_read):
@@ -595,6 +598,7 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
     return LITHO_ENOMEM;
   }
   const int cb = host_chunk_clips(b), F = h->n_focus;
+  const int chunks = (b + cb - 1) / cb;
   const size_t region = host_region_bytes(h, cb, prec);
   std::vector<int> ttag;
   std::vector<double> tms;
@@ -608,33 +612,34 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
   w = align_up(w);
   const size_t nn = size_t(h->n) * h->n;
   cudaStream_t caller = static_cast<cudaStream_t>(stream);
-  cudaStream_t lanes[2] = {caller, caller};
   litho_kernels* hm = const_cast<litho_kernels*>(h);
-  // concurrent host-path calls on one kernel set share its two streams: one at a time
+  // concurrent host-path calls on one kernel set share its streams and events: one at a time
   std::lock_guard<std::mutex> lk(hm->host_mu);
-  // device timestamps: a start event on the caller's stream, then per chunk the end of its input
-  // copy, of its kernels and of its output copies on its lane (read after the final wait)
-  const int chunks = (b + cb - 1) / cb;
+  for (auto& st : hm->host_streams)
+    if (!st) LITHO_TRY_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  if (!hm->host_events[0]) LITHO_TRY_CUDA(cudaEventCreateWithFlags(&hm->host_events[0], cudaEventDisableTiming));
+  // per chunk: input copied, kernels done, outputs copied (ordering), and the same three for timing
+  while (hm->host_sync.size() < size_t(3 * chunks)) {
+    cudaEvent_t e;
+    LITHO_TRY_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    hm->host_sync.push_back(e);
+  }
   while (hm->host_timing.size() < size_t(1 + 3 * chunks)) {
     cudaEvent_t e;
     LITHO_TRY_CUDA(cudaEventCreate(&e));
     hm->host_timing.push_back(e);
   }
-  LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[0], caller));
-  if (cb < b) {
-    for (int i = 0; i < 2; ++i)
-      if (!hm->host_streams[i]) LITHO_TRY_CUDA(cudaStreamCreateWithFlags(&hm->host_streams[i], cudaStreamNonBlocking));
-    if (!hm->host_events[0])
-      for (int i = 0; i < 3; ++i) LITHO_TRY_CUDA(cudaEventCreateWithFlags(&hm->host_events[i], cudaEventDisableTiming));
-    lanes[0] = hm->host_streams[0];
-    lanes[1] = hm->host_streams[1];
-    LITHO_TRY_CUDA(cudaEventRecord(hm->host_events[0], caller));
-    for (int i = 0; i < 2; ++i) LITHO_TRY_CUDA(cudaStreamWaitEvent(lanes[i], hm->host_events[0], 0));
-  }
+  cudaStream_t s_in = hm->host_streams[0], s_comp = hm->host_streams[1], s_out = hm->host_streams[2];
+  auto ev_in = [&](int ci) { return hm->host_sync[3 * ci]; };
+  auto ev_comp = [&](int ci) { return hm->host_sync[3 * ci + 1]; };
+  auto ev_out = [&](int ci) { return hm->host_sync[3 * ci + 2]; };
+  LITHO_TRY_CUDA(cudaEventRecord(hm->host_events[0], caller));
+  for (cudaStream_t st : {s_in, s_comp, s_out}) LITHO_TRY_CUDA(cudaStreamWaitEvent(st, hm->host_events[0], 0));
+  LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[0], s_in));
   for (int c0 = 0, ci = 0; c0 < b; c0 += cb, ++ci) {
     const int nb = std::min(cb, b - c0);
     const size_t planes = size_t(nb) * F;
-    cudaStream_t st = lanes[ci & 1];
+    // chunks alternate between two workspace regions
     char* base = static_cast<char*>(workspace_dev) + (ci & 1) * (cb < b ? region : 0);
     float* dmask = reinterpret_cast<float*>(base + w);
     float* dimg = reinterpret_cast<float*>(base + w + align_up(size_t(cb) * nn * sizeof(float)));
@@ -642,34 +647,39 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
         reinterpret_cast<float*>(reinterpret_cast<char*>(dimg) + align_up(size_t(cb) * F * nn * sizeof(float)));
     uint8_t* dpr =
         reinterpret_cast<uint8_t*>(reinterpret_cast<char*>(dblur) + align_up(size_t(cb) * F * nn * sizeof(float)));
+    // input copy: the region's mask buffer is free once the kernels of chunk ci - 2 are done
+    if (ci >= 2) LITHO_TRY_CUDA(cudaStreamWaitEvent(s_in, ev_comp(ci - 2), 0));
     LITHO_TRY_CUDA(cudaMemcpyAsync(dmask, mask_host + size_t(c0) * nn, size_t(nb) * nn * sizeof(float),
-                                   cudaMemcpyHostToDevice, st));
-    LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[1 + 3 * ci], st));
+                                   cudaMemcpyHostToDevice, s_in));
+    LITHO_TRY_CUDA(cudaEventRecord(ev_in(ci), s_in));
+    LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[1 + 3 * ci], s_in));
     mark(ci * 8 + 0);
-    if (printed_host) {
-      s = litho_aerial_resist(h, dmask, nb, dose, prec, dimg, sigma_nm, threshold, dblur, dpr, base, w, st);
-      if (s != LITHO_OK) return s;
-      LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[2 + 3 * ci], st));
-      mark(ci * 8 + 1);
-      LITHO_TRY_CUDA(cudaMemcpyAsync(printed_host + size_t(c0) * F * nn, dpr, planes * nn, cudaMemcpyDeviceToHost, st));
-    } else {
-      s = litho_aerial(h, dmask, nb, dose, prec, dimg, base, w, st);
-      if (s != LITHO_OK) return s;
-      LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[2 + 3 * ci], st));
-      mark(ci * 8 + 1);
-    }
+    // kernels, one chunk after another on one stream: after the input copy, and once the
+    // region's output buffers have been copied out for chunk ci - 2
+    LITHO_TRY_CUDA(cudaStreamWaitEvent(s_comp, ev_in(ci), 0));
+    if (ci >= 2) LITHO_TRY_CUDA(cudaStreamWaitEvent(s_comp, ev_out(ci - 2), 0));
+    if (printed_host)
+      s = litho_aerial_resist(h, dmask, nb, dose, prec, dimg, sigma_nm, threshold, dblur, dpr, base, w, s_comp);
+    else
+      s = litho_aerial(h, dmask, nb, dose, prec, dimg, base, w, s_comp);
+    if (s != LITHO_OK) return s;
+    LITHO_TRY_CUDA(cudaEventRecord(ev_comp(ci), s_comp));
+    LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[2 + 3 * ci], s_comp));
+    mark(ci * 8 + 1);
+    // output copies
+    LITHO_TRY_CUDA(cudaStreamWaitEvent(s_out, ev_comp(ci), 0));
+    if (printed_host)
+      LITHO_TRY_CUDA(
+          cudaMemcpyAsync(printed_host + size_t(c0) * F * nn, dpr, planes * nn, cudaMemcpyDeviceToHost, s_out));
     if (intensity_host)
       LITHO_TRY_CUDA(cudaMemcpyAsync(intensity_host + size_t(c0) * F * nn, dimg, planes * nn * sizeof(float),
-                                     cudaMemcpyDeviceToHost, st));
-    LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[3 + 3 * ci], st));
+                                     cudaMemcpyDeviceToHost, s_out));
+    LITHO_TRY_CUDA(cudaEventRecord(ev_out(ci), s_out));
+    LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[3 + 3 * ci], s_out));
     mark(ci * 8 + 2);
   }
-  if (cb < b) {
-    for (int i = 0; i < 2; ++i) {
-      LITHO_TRY_CUDA(cudaEventRecord(hm->host_events[1 + i], lanes[i]));
-      LITHO_TRY_CUDA(cudaStreamWaitEvent(caller, hm->host_events[1 + i], 0));
-    }
-  }
+  // the last output copy follows every earlier step on all three streams
+  LITHO_TRY_CUDA(cudaStreamWaitEvent(caller, ev_out(chunks - 1), 0));
   mark(-1);  // all work issued; the wait starts
   LITHO_TRY_CUDA(cudaStreamSynchronize(caller));
   mark(-2);  // the wait ended

@@ -106,10 +106,11 @@ struct litho_kernels {
   int device = 0;
   // streams and events of the pipelined host-buffer path (created on first use)
   std::mutex host_mu;
-  cudaStream_t host_streams[2] = {nullptr, nullptr};
+  cudaStream_t host_streams[3] = {nullptr, nullptr, nullptr};  // input copies, kernels, output copies
   cudaEvent_t host_events[3] = {nullptr, nullptr, nullptr};
   // timing events of the host-buffer path (one start, three per chunk), grown on demand
   std::vector<cudaEvent_t> host_timing;
+  std::vector<cudaEvent_t> host_sync;  // ordering events of the host-buffer path, three per chunk
 };
 
 namespace litho {
