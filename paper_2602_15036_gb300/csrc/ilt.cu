@@ -304,9 +304,19 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
+  constexpr int R0 = Plan<N>::R[0], NB0 = N / R0;
+  static_assert(PassShape<N, NT, R0>::PER == 1, "one first-pass butterfly per thread");
   const int tid = threadIdx.x, g = tid % W, t = tid / W, c0 = blockIdx.x * W, half = crop / 2;
   const int j0 = blockIdx.y * jb, j1 = min(fields, j0 + jb);
   load_twiddles<N>(tw, tw_g);
+  // this thread's first-pass inputs (rows t + r N/R0) of a field, loaded one field ahead
+  float2 nxt[R0];
+  auto prefetch = [&](int j) {
+    const float2* src = u + (size_t)j * N * crop + c0 + g;  // row y at src[y crop]
+#pragma unroll
+    for (int r = 0; r < R0; ++r) nxt[r] = t < NB0 ? __ldg(src + (size_t)(t + r * NB0) * crop) : make_float2(0.f, 0.f);
+  };
+  if (j0 < j1) prefetch(j0);
   __syncthreads();
   for (int j = j0; j < j1; ++j) {
     const int jk = j % period;
@@ -314,11 +324,18 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
     float2* dst = sk + (size_t)j * crop * crop + c0 + g;  // crop row cv at dst[cv crop]
     if (l == 0.f) {  // uniform across the block
       for (int cv = t; cv < crop; cv += NT) dst[(size_t)cv * crop] = make_float2(0.f, 0.f);
+      if (j + 1 < j1) prefetch(j + 1);
       continue;
     }
-    const float2* src = u + (size_t)j * N * crop + c0 + g;  // row y at src[y crop]
     const float2* ph = phi + (size_t)jk * crop * crop + c0 + g;
-    auto load = [&](int y) { return __ldg(src + (size_t)y * crop); };
+    float2 cur[R0];
+#pragma unroll
+    for (int r = 0; r < R0; ++r) cur[r] = nxt[r];
+    auto load = [&](int, int r, int) { return cur[r]; };
+    // once the first pass has consumed this field's inputs, the next field's loads go out
+    auto after_first = [&]() {
+      if (j + 1 < j1) prefetch(j + 1);
+    };
     auto use = [&](int, int, int idx, float2 h) {
       const int cv = freq_of_idx(idx, N) + half;
       if (cv >= 0 && cv < crop) {
@@ -327,7 +344,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
         dst[(size_t)cv * crop] = make_float2(l * (p.x * h.x + p.y * h.y), l * (p.x * h.y - p.y * h.x));
       }
     };
-    fft_load_use<N, -1>(buf + g * LD, tw, t, load, use);
+    fft_load_use<N, -1, decltype(load), decltype(use), false>(buf + g * LD, tw, t, load, use, after_first);
   }
 }
 
