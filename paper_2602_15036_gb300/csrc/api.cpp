@@ -598,7 +598,19 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
     return LITHO_ENOMEM;
   }
   const int cb = host_chunk_clips(b), F = h->n_focus;
-  const int chunks = (b + cb - 1) / cb;
+  // Chunk starts: the first and the last chunk take 2 clips when the batch is long, so that
+  // the one input copy and the one output copy that nothing overlaps are short; the others
+  // take at most cb clips, as evenly as possible.
+  std::vector<int> starts{0};
+  {
+    const bool ends = b >= 4 * cb;
+    const int head = ends ? 2 : 0, tail = ends ? 2 : 0, mid = b - head - tail;
+    if (head) starts.push_back(head);
+    const int nmid = (mid + cb - 1) / cb;
+    for (int i = 1; i <= nmid; ++i) starts.push_back(head + int((long long)mid * i / nmid));
+    if (tail) starts.push_back(b);
+  }
+  const int chunks = int(starts.size()) - 1;
   const size_t region = host_region_bytes(h, cb, prec);
   std::vector<int> ttag;
   std::vector<double> tms;
@@ -636,8 +648,8 @@ litho_status litho_aerial_host(const litho_kernels* h, const float* mask_host, i
   LITHO_TRY_CUDA(cudaEventRecord(hm->host_events[0], caller));
   for (cudaStream_t st : {s_in, s_comp, s_out}) LITHO_TRY_CUDA(cudaStreamWaitEvent(st, hm->host_events[0], 0));
   LITHO_TRY_CUDA(cudaEventRecord(hm->host_timing[0], s_in));
-  for (int c0 = 0, ci = 0; c0 < b; c0 += cb, ++ci) {
-    const int nb = std::min(cb, b - c0);
+  for (int ci = 0; ci < chunks; ++ci) {
+    const int c0 = starts[ci], nb = starts[ci + 1] - c0;
     const size_t planes = size_t(nb) * F;
     // chunks alternate between two workspace regions
     char* base = static_cast<char*>(workspace_dev) + (ci & 1) * (cb < b ? region : 0);
