@@ -598,7 +598,7 @@ def run_aerial(args, ctx):
         P.litho_aerial_host(kern, mask_host, ws_host, printed_host=printed_host, precision=args.precision,
                             sigma_nm=SIGMA_NM, threshold=THRESH, stream=stream)
 
-    for _ in range(2):
+    for _ in range(3):
         e2e_step()
     ctx.barrier()
     e2e_steps = max(3, min(args.steps, 10))

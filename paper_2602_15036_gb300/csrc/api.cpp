@@ -91,6 +91,18 @@ litho_status upload(litho_kernels* h) {
     LITHO_TRY_CUDA(cudaMemcpy(h->d_tw512, t512.data(), t512.size() * sizeof(float2), cudaMemcpyHostToDevice));
   }
   if (N == 1024 || h->nc == 1024) {
+    // sqrt(lam_fk) Phi_fk for the aerial path's stage 1 (FP64 product, then rounded)
+    std::vector<float2> phs(phi.size());
+    const size_t cc = size_t(C) * C;
+    for (size_t fk = 0; fk < size_t(F) * K; ++fk) {
+      const double r = std::sqrt(std::max(0.0, h->lambda[fk]));
+      for (size_t i = 0; i < cc; ++i) {
+        const size_t e = fk * cc + i;
+        phs[e] = make_float2(float(r * h->phi_host[2 * e]), float(r * h->phi_host[2 * e + 1]));
+      }
+    }
+    LITHO_TRY_CUDA(cudaMalloc(&h->d_phi_s, phs.size() * sizeof(float2)));
+    LITHO_TRY_CUDA(cudaMemcpy(h->d_phi_s, phs.data(), phs.size() * sizeof(float2), cudaMemcpyHostToDevice));
     std::vector<float2> t32(kStage2W32TableLen);
     stage2_w32_table(t32.data());
     LITHO_TRY_CUDA(cudaMalloc(&h->d_tw32, t32.size() * sizeof(float2)));
@@ -136,6 +148,7 @@ void litho_free_kernels(litho_kernels* h) {
   if (h->d_twc_tc != h->d_twc) cudaFree(h->d_twc_tc);
   cudaFree(h->d_twc);
   cudaFree(h->d_tw32);
+  cudaFree(h->d_phi_s);
   cudaFree(h->d_tw512);
   for (auto& s : h->host_streams)
     if (s) cudaStreamDestroy(s);
@@ -478,17 +491,21 @@ static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, in
   }
   const int NE = coarse ? coarse_n(h, p) : N;
   const float2* tw = coarse ? coarse_tw(h, p) : h->d_tw;
+  // On a 1024-point grid stage 1 takes sqrt(lam) Phi and the warp-per-row stage 2 sums |E|^2 unweighted
+  const bool folded = h->d_phi_s && h->d_tw32 && stage2_w32_supported(NE, C);
   for (int c0 = 0; c0 < b; c0 += G) {
     const int g = std::min(G, b - c0);
     float* img = intensity_dev + size_t(c0) * F * N * N;
     {
       ProfScope ps(kStageStage1Fft, st, 1);
-      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat + size_t(c0) * C * C, h->d_phi, F * K, NE, C, tw, L.t1, st, g));
+      LITHO_TRY_CUDA(launch_stage1_fft(L.mhat + size_t(c0) * C * C, folded ? h->d_phi_s : h->d_phi, F * K, NE, C, tw,
+                                       L.t1, st, g));
     }
     {
       ProfScope ps(kStageStage2Fft, st, 1);
       LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda, K, NE, C, float(dose), tw, coarse ? L.ic : img, g * F,
-                                       (long long)K * NE * C, (long long)NE * NE, st, F, h->d_tw32, h->d_tw512));
+                                       (long long)K * NE * C, (long long)NE * NE, st, F, h->d_tw32, h->d_tw512,
+                                       folded));
     }
     if (coarse) {
       litho_status s = upsample(h, p, L, g * F, img, fr, size_t(c0) * F, st);

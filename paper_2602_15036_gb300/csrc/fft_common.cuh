@@ -177,45 +177,96 @@ __device__ __forceinline__ constexpr float cos32(int t) {
 }
 __device__ __forceinline__ constexpr float sin32(int t) { return cos32(8 - t); }
 
-// 32-point DFT in registers, v'[q] = sum_r v[r] e^{SIGN 2 pi i r q / 32}: a
-// radix-2 decimation-in-frequency network, output in natural order.  BANDED:
-// v[r] for r in [8, 24) is zero and not read.
+// x times e^{SIGN 2 pi i t / 32} for a compile-time t (the multiples of 8 are a
+// quarter turn, a sign or nothing).
+template <int SIGN, int T>
+__device__ __forceinline__ float2 twiddle32(float2 x) {
+  constexpr int t = T % 32;
+  if constexpr (t == 0) {
+    return x;
+  } else if constexpr (t == 8) {
+    return make_float2(-SIGN * x.y, SIGN * x.x);
+  } else if constexpr (t == 16) {
+    return make_float2(-x.x, -x.y);
+  } else if constexpr (t == 24) {
+    return make_float2(SIGN * x.y, -SIGN * x.x);
+  } else {
+    return cmul(x, make_float2(cos32(t), SIGN * sin32(t)));
+  }
+}
+
+// 4-point DFT in place, y[k] = sum_m x[m] e^{SIGN 2 pi i m k / 4}, on v[i0 + s m].
+// X1_X2_ZERO: v[i0 + s] and v[i0 + 2 s] are known to be zero and are not read.
+template <int SIGN, bool X1_X2_ZERO>
+__device__ __forceinline__ void dft4_at(float2 (&v)[32], int i0, int s) {
+  const float2 x0 = v[i0], x3 = v[i0 + 3 * s];
+  float2 a, b, c, d;
+  if constexpr (X1_X2_ZERO) {
+    a = x0;
+    b = x0;
+    c = x3;
+    d = make_float2(-SIGN * x3.y, SIGN * x3.x);  // (x1 - x3) SIGN i with x1 = 0 ...
+    d = make_float2(-d.x, -d.y);                 // ... = -x3 SIGN i
+  } else {
+    const float2 x1 = v[i0 + s], x2 = v[i0 + 2 * s];
+    a = cadd(x0, x2);
+    b = csub(x0, x2);
+    c = cadd(x1, x3);
+    const float2 e = csub(x1, x3);
+    d = make_float2(-SIGN * e.y, SIGN * e.x);  // e SIGN i
+  }
+  v[i0] = cadd(a, c);
+  v[i0 + s] = cadd(b, d);
+  v[i0 + 2 * s] = csub(a, c);
+  v[i0 + 3 * s] = csub(b, d);
+}
+
+// 32-point DFT in registers, v'[q] = sum_r v[r] e^{SIGN 2 pi i r q / 32}, output in
+// natural order.  Decimation in frequency with radices 4, 4, 2: a radix-4 stage over
+// stride 8 with twiddles w^(i k1), a radix-4 stage over stride 2 within each block of
+// 8 with twiddles w^(4 j k2), a radix-2 stage on pairs; position 8 k1 + 2 k2 + k3 then
+// holds output k1 + 4 k2 + 16 k3.  28 non-trivial twiddle products against 34 for a
+// radix-2 network, the same additions.  BANDED: v[r] for r in [8, 24) is zero and
+// not read (the first stage's middle inputs).
 template <int SIGN, bool BANDED>
 __device__ __forceinline__ void dft32(float2 (&v)[32]) {
 #pragma unroll
-  for (int span = 32 / 2; span >= 1; span /= 2) {
+  for (int i = 0; i < 8; ++i) dft4_at<SIGN, BANDED>(v, i, 8);
 #pragma unroll
-    for (int b = 0; b < 32; b += 2 * span) {
+  for (int i = 1; i < 8; ++i) {
 #pragma unroll
-      for (int i = 0; i < span; ++i) {
-        float2 d;
-        if (BANDED && span == 32 / 2) {
-          if (i < 32 / 4) {
-            d = v[i];  // v[i + 16] is zero
-          } else {     // v[i] is zero
-            v[i] = v[i + span];
-            d = make_float2(-v[i].x, -v[i].y);
-          }
-        } else {
-          const float2 a = v[b + i], c = v[b + i + span];
-          v[b + i] = cadd(a, c);
-          d = csub(a, c);
-        }
-        const int t = i * (32 / (2 * span));  // twiddle e^{SIGN 2 pi i t / 32}
-        if (t != 0) {
-          if (t == 8) {
-            d = make_float2(-SIGN * d.y, SIGN * d.x);  // multiply by SIGN i
-          } else {
-            d = cmul(d, make_float2(cos32(t), SIGN * sin32(t)));
-          }
-        }
-        v[b + i + span] = d;
+    for (int k1 = 1; k1 < 4; ++k1) {
+      const int t = i * k1;
+      float2& x = v[i + 8 * k1];
+      if (t == 8) {
+        x = twiddle32<SIGN, 8>(x);
+      } else if (t % 32 != 0) {
+        x = cmul(x, make_float2(cos32(t), SIGN * sin32(t)));
       }
     }
   }
+#pragma unroll
+  for (int blk = 0; blk < 4; ++blk) {
+#pragma unroll
+    for (int j = 0; j < 2; ++j) dft4_at<SIGN, false>(v, 8 * blk + j, 2);
+    // j = 1: twiddles w^(4 k2), k2 = 1, 2, 3 (w^8 is a quarter turn)
+    v[8 * blk + 3] = cmul(v[8 * blk + 3], make_float2(cos32(4), SIGN * sin32(4)));
+    v[8 * blk + 5] = twiddle32<SIGN, 8>(v[8 * blk + 5]);
+    v[8 * blk + 7] = cmul(v[8 * blk + 7], make_float2(cos32(12), SIGN * sin32(12)));
+  }
+#pragma unroll
+  for (int p = 0; p < 32; p += 2) {
+    const float2 a = v[p], b = v[p + 1];
+    v[p] = cadd(a, b);
+    v[p + 1] = csub(a, b);
+  }
   float2 o[32];
 #pragma unroll
-  for (int q = 0; q < 32; ++q) o[q] = v[bitrev(q, 5)];
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2)
+#pragma unroll
+      for (int k3 = 0; k3 < 2; ++k3) o[k1 + 4 * k2 + 16 * k3] = v[8 * k1 + 2 * k2 + k3];
 #pragma unroll
   for (int q = 0; q < 32; ++q) v[q] = o[q];
 }

@@ -100,6 +100,8 @@ struct litho_kernels {
   float2* d_twc_tc = nullptr;              // FFT twiddle table for nc_tc (d_twc when nc_tc == nc)
   float2* d_tw32 = nullptr;                // second-pass twiddles of the warp-per-row 1024-point stage 2
                                            // (when N or nc is 1024, else NULL)
+  float2* d_phi_s = nullptr;               // sqrt(lam_fk) Phi_fk [F][K][C][C]: the aerial path's stage 1 on a
+                                           // 1024-point grid, so that stage 2 sums |E|^2 unweighted (with d_tw32)
   float2* d_tw512 = nullptr;               // twiddles of the 512-point adjoint rows, two rows per warp
                                            // (when N or nc is 512, else NULL)
   litho::GemmOperands* gemm = nullptr;     // lazily built per precision
@@ -152,11 +154,13 @@ cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int
 // for each of `planes` planes; plane p takes lam[(p mod lam_period) nk ...]
 // (lam_period <= 0: planes, no repetition).  With tw32 (the kernel set's
 // d_tw32) a 1024-point row takes the warp-per-row radix-32 kernel, with
-// tw512 (d_tw512) 512-point rows the two-rows-per-warp kernel.
+// tw512 (d_tw512) 512-point rows the two-rows-per-warp kernel.  folded (with
+// tw32 only): the fields were made from sqrt(lam) Phi, so |E|^2 is summed
+// without the weight (lam still marks the zero kernels, which are skipped).
 cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
                               long long img_plane_stride, cudaStream_t st, int lam_period = 0,
-                              const float2* tw32 = nullptr, const float2* tw512 = nullptr);
+                              const float2* tw32 = nullptr, const float2* tw512 = nullptr, bool folded = false);
 // The warp-per-row stage 2 for 1024-point rows (stage2_w32.cu) and its
 // second-pass twiddle table (31 x 32 entries w^(r l), r in [1, 32), l in [0, 32)).
 bool stage2_w32_supported(int n, int crop);
@@ -169,7 +173,7 @@ void stage2_w32_table(float2* out);
 constexpr int kStage2W32TableLen = 31 * 32;
 cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw2, float* img, int planes, long long t1_plane, long long img_plane,
-                              int lam_period, cudaStream_t st);
+                              int lam_period, cudaStream_t st, bool folded = false);
 
 // A device-side delay of about `ms` milliseconds on `st` (util.cu): one
 // thread spinning on the SM clock for a fixed number of cycles, which always

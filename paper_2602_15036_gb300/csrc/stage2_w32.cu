@@ -47,7 +47,7 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int PENDING>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory"); }
 
-template <bool BANDED, int kWarps>
+template <bool BANDED, int kWarps, bool FOLDED>
 __global__ void __launch_bounds__(32 * kWarps, 1)
     k_stage2_w32(const float2* __restrict__ t1, const float* __restrict__ lam, int nk, int crop, float dose,
                  const float2* __restrict__ tw2_g, float* __restrict__ img, long long t1_plane, long long img_plane,
@@ -106,31 +106,38 @@ __global__ void __launch_bounds__(32 * kWarps, 1)
     __syncwarp();  // every lane has read buf before the next kernel's pass 1 writes it
     dft32<+1, false>(v);
 #pragma unroll
-    for (int q = 0; q < kR; ++q) acc[q] = fmaf(l, fmaf(v[q].x, v[q].x, v[q].y * v[q].y), acc[q]);
+    for (int q = 0; q < kR; ++q)
+      acc[q] = FOLDED ? fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, acc[q]))  // sqrt(lam) is in the field
+                      : fmaf(l, fmaf(v[q].x, v[q].x, v[q].y * v[q].y), acc[q]);
   }
   float* out = img + plane * img_plane + (size_t)y * kN;
 #pragma unroll
   for (int q = 0; q < kR; ++q) out[lane + kR * q] = dose * acc[q];
 }
 
-template <int kWarps>
-cudaError_t launch_w32_t(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw2,
+template <bool BANDED, int kWarps, bool FOLDED>
+cudaError_t launch_w32_k(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw2,
                          float* img, int planes, long long t1_plane, long long img_plane, int lam_period,
                          cudaStream_t st) {
   const dim3 grid((kN + kWarps - 1) / kWarps, planes);
   const size_t sm = sizeof(float2) * ((kR - 1) * kR + kWarps * kRowLd + size_t(kWarps) * crop);
-  if (crop / 2 <= kN / 4) {  // the band leaves indices [N/4, 3N/4) empty
-    cudaError_t e = smem_attrs(k_stage2_w32<true, kWarps>, sm);
-    if (e != cudaSuccess) return e;
-    k_stage2_w32<true, kWarps><<<grid, 32 * kWarps, sm, st>>>(t1, lam, nk, crop, dose, tw2, img, t1_plane,
-                                                              img_plane, lam_period);
-  } else {
-    cudaError_t e = smem_attrs(k_stage2_w32<false, kWarps>, sm);
-    if (e != cudaSuccess) return e;
-    k_stage2_w32<false, kWarps><<<grid, 32 * kWarps, sm, st>>>(t1, lam, nk, crop, dose, tw2, img, t1_plane,
-                                                               img_plane, lam_period);
-  }
+  cudaError_t e = smem_attrs(k_stage2_w32<BANDED, kWarps, FOLDED>, sm);
+  if (e != cudaSuccess) return e;
+  k_stage2_w32<BANDED, kWarps, FOLDED><<<grid, 32 * kWarps, sm, st>>>(t1, lam, nk, crop, dose, tw2, img, t1_plane,
+                                                                      img_plane, lam_period);
   return cudaGetLastError();
+}
+
+template <int kWarps>
+cudaError_t launch_w32_t(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw2,
+                         float* img, int planes, long long t1_plane, long long img_plane, int lam_period,
+                         cudaStream_t st, bool folded) {
+  const bool banded = crop / 2 <= kN / 4;  // the band leaves indices [N/4, 3N/4) empty
+#define W32(B, F) \
+  launch_w32_k<B, kWarps, F>(t1, lam, nk, crop, dose, tw2, img, planes, t1_plane, img_plane, lam_period, st)
+  if (banded) return folded ? W32(true, true) : W32(true, false);
+  return folded ? W32(false, true) : W32(false, false);
+#undef W32
 }
 
 // The same stage 2 for 512-point rows, two rows per warp (512 = 16 x 32):
@@ -256,13 +263,13 @@ cudaError_t launch_stage2_w512(const float2* t1, const float* lam, int nk, int n
 
 cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw2, float* img, int planes, long long t1_plane, long long img_plane,
-                              int lam_period, cudaStream_t st) {
+                              int lam_period, cudaStream_t st, bool folded) {
   if (!stage2_w32_supported(n, crop) || !tw2) return cudaErrorInvalidValue;
   if (lam_period <= 0) lam_period = planes;
   // 12 warps per CTA: one CTA of 384 threads fits the SM's registers (about 160 per thread);
   // measured on the 2048^2 workload's 1024-point rows: 5.90 ms per step against 6.29 with 8
   // warps and 6.04 with 16 (128 registers)
-  return launch_w32_t<12>(t1, lam, nk, crop, dose, tw2, img, planes, t1_plane, img_plane, lam_period, st);
+  return launch_w32_t<12>(t1, lam, nk, crop, dose, tw2, img, planes, t1_plane, img_plane, lam_period, st, folded);
 }
 
 }  // namespace litho
