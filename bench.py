@@ -535,6 +535,24 @@ def time_steps(ctx, step, steps, warmup, stream, sample_clocks=False):
     return [a.elapsed_time(b) for a, b in ev], (clk.summary() if clk else None)
 
 
+def tensor_summary(results, plain, peaks, models_fn, clips, crop, n_focus, k_eff, kern):
+    """The split tensor-core path against both FP32 FFT paths, and its tensor-pipe use over the whole
+    step (executed MMA flops of the step / step time / the measured sustained bf16/fp16 peak)."""
+    tp = "fp16x3/coarse"
+    r = results.get(tp)
+    if r is None:
+        return None
+    coarse = results.get("fft32/coarse")
+    flops = models_fn(tp, clips, N, crop, n_focus, k_eff, kern.grid(tp), peaks)["stage2_gemm"][0]
+    step_s = r["total_ms"] / len(r["step_ms"]) * 1e-3
+    return {"precision": tp, "value": r["value"], "ms_per_step": step_s * 1e3,
+            "vs_plain_fft_full_grid": r["value"] / plain["value"] if plain else None,
+            "vs_fft32_coarse": r["value"] / coarse["value"] if coarse else None,
+            "step_tensor_frac": flops / step_s / (peaks["bf16_tflops_sustained"] * 1e12),
+            "note": "executed MMA flops (Gauss 3M, split x3) over the whole step time, against the measured "
+                    "sustained dense bf16/fp16 peak"}
+
+
 def run_aerial(args, ctx):
     import paper_2602_15036_gb300 as P
     from paper_2602_15036_gb300 import litho as L
@@ -637,6 +655,7 @@ def run_aerial(args, ctx):
             "p50_ms": statistics.median(lat_ms), "p99_ms": float(np.percentile(lat_ms, 99)),
             "latency_reps": lat_reps, "latency_clocks": lat_clk,
             "vs_plain_fft": (head["value"] / plain["value"]) if plain else None,
+            "tensor_path": tensor_summary(results, plain, peaks, stage_models, clips, c, F, k_eff, kern),
             "paths": {p: {"value": r["value"], "ms_per_step": r["total_ms"] / args.steps,
                           "error_bound_abs": ERROR_BOUND.get(p),
                           "stages_ms_per_step": {k: v[0] / args.steps for k, v in r["prof"].items()},

@@ -37,19 +37,36 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_mask_rows(const float* __restri
   load_twiddles<N>(tw, tw_g);
   __syncthreads();
   const int b = blockIdx.y, t = threadIdx.x, half = crop / 2;
-  // pairs [blockIdx.x * pairs_per_cta, ...): the next pair's first pass writes
-  // buf only after a barrier that follows this pair's reads of zc
-  for (int pr = blockIdx.x * pairs_per_cta; pr < min(N / 2, (blockIdx.x + 1) * pairs_per_cta); ++pr) {
+  constexpr int R0 = Plan<N>::R[0], NB0 = N / R0;
+  static_assert(PassShape<N, Plan<N>::NT, R0>::PER == 1, "one first-pass butterfly per thread");
+  // this thread's first-pass inputs (columns t + r N/R0 of both rows) of a pair, loaded one pair ahead
+  float2 nxt[R0];
+  auto prefetch = [&](int pr) {
+    const float* r0 = m + ((size_t)b * N + 2 * pr) * N;
+#pragma unroll
+    for (int r = 0; r < R0; ++r)
+      nxt[r] = t < NB0 ? make_float2(__ldg(r0 + t + r * NB0), __ldg(r0 + N + t + r * NB0)) : make_float2(0.f, 0.f);
+  };
+  const int pr0 = blockIdx.x * pairs_per_cta, pr1 = min(N / 2, (blockIdx.x + 1) * pairs_per_cta);
+  if (pr0 < pr1) prefetch(pr0);
+  // pairs [pr0, pr1): the next pair's first pass writes buf only after a
+  // barrier that follows this pair's reads of zc
+  for (int pr = pr0; pr < pr1; ++pr) {
     const int y0 = 2 * pr;
-    const float* r0 = m + ((size_t)b * N + y0) * N;
-    const float* r1 = r0 + N;
-    auto load = [&](int i) { return make_float2(__ldg(r0 + i), __ldg(r1 + i)); };
+    float2 cur[R0];
+#pragma unroll
+    for (int r = 0; r < R0; ++r) cur[r] = nxt[r];
+    auto load = [&](int, int r, int) { return cur[r]; };
     auto use = [&](int, int, int idx, float2 v) {
       const int u = freq_of(idx, N);
       if (u >= -half && u <= half) zc[u + half] = v;
       if (u == -N / 2 && half == N / 2) zc[crop] = v;  // crop == N: Z(N/2) is Z(-N/2)
     };
-    fft_load_use<N, -1>(buf, tw, t, load, use);
+    // once the first pass has consumed this pair, the next pair's loads go out
+    auto after_first = [&]() {
+      if (pr + 1 < pr1) prefetch(pr + 1);
+    };
+    fft_load_use<N, -1, decltype(load), decltype(use), false>(buf, tw, t, load, use, after_first);
     __syncthreads();
     float2* o0 = rowbuf + ((size_t)b * N + y0) * crop;
     float2* o1 = o0 + crop;
