@@ -250,6 +250,110 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_resist(const float2* 
   }
 }
 
+// ILT forward end on the coarse grid, for a pair of rows (y0, y0 + 1) of a
+// full-grid plane whose band rows R_y carry S (1 + i gain (x) gain), so that
+// the imaginary part of IDFT(R_y) is the blurred row.  The blurred row's
+// spectrum is (R_y(u) - conj R_y(-u)) / 2i, so one inverse transform of
+// Bl_y0 + i Bl_y1 gives both blurred rows as its real and imaginary parts.
+// The sigmoid resist z = 1 / (1 + e^{-beta (blur - thr)}), the residual
+// d = z - target and dL/dI = 2 d beta z (1 - z) follow on the spot (Eqs. (5)
+// and (10)); the two dL/dI rows go forward as one complex row
+// q[y0] + i q[y1] and leave as their two band spectra, as k_mask_rows writes
+// them.  The pair's sum of d^2 goes to partial[plane][pair] in FP64: one
+// partial per row pair, whatever the launch shape, so the loss does not
+// depend on how clips are grouped.  Plane p belongs to clip
+// p / planes_per_clip of `target`.
+template <int N>
+struct GradRowsShape {
+  using PL = Plan<N>;
+  static constexpr int NT = PL::NT, R0 = PL::R[0], RL = PL::R[PL::P - 1];
+  static constexpr int PERL = (N / RL + NT - 1) / NT;
+  // the inverse transform's last pass hands thread t the elements t + NT r,
+  // r = p + PERL q, which are the forward first pass's inputs of thread t
+  static constexpr bool kRegs = N / R0 == NT && N / RL == PERL * NT && R0 == PERL * RL;
+};
+
+template <int N, bool BANDED>
+__global__ void __launch_bounds__(Plan<N>::NT, N >= 512 ? 640 / Plan<N>::NT : 1) k_resist_grad_rows(const float2* __restrict__ band, int crop,
+                                                                   const float2* __restrict__ tw_g,
+                                                                   const float* __restrict__ target,
+                                                                   int planes_per_clip, float beta, float thr,
+                                                                   float2* __restrict__ rowbuf,
+                                                                   double* __restrict__ partial, int pairs_per_cta) {
+  using SH = GradRowsShape<N>;
+  constexpr int NT = SH::NT, NW = (NT + 31) / 32, PERL = SH::PERL;
+  extern __shared__ float2 smem[];
+  float2* tw = smem;
+  float2* buf = smem + N;
+  // Z(u) on the crop, index u + C/2 (crop + 1 entries); without kRegs, first
+  // the pair's dL/dI rows (N entries: x row y0, y row y0 + 1)
+  float2* zq = smem + N + PadLen<N>::value;
+  __shared__ double wsum[NW];
+  load_twiddles<N>(tw, tw_g);
+  __syncthreads();
+  const int p = blockIdx.y, t = threadIdx.x, half = crop / 2;
+  const float* tg = target + (size_t)(p / planes_per_clip) * N * N;
+  for (int pr = blockIdx.x * pairs_per_cta; pr < min(N / 2, (blockIdx.x + 1) * pairs_per_cta); ++pr) {
+    const int y0 = 2 * pr;
+    const float2* r0 = band + ((size_t)p * N + y0) * crop;
+    const float2* r1 = r0 + crop;
+    const float* t0 = tg + (size_t)y0 * N;
+    const float* t1 = t0 + N;
+    auto load = [&](int, int r, int idx) {
+      const int u = r < Plan<N>::R[0] / 2 ? idx : idx - N;  // first pass: idx < N/2 exactly when r < R/2
+      const int c = u + half, cm = half - u;
+      const bool in = c >= 0 && c < crop, inm = cm >= 0 && cm < crop;
+      const float2 a = in ? __ldg(r0 + c) : make_float2(0.f, 0.f), b = inm ? __ldg(r0 + cm) : make_float2(0.f, 0.f);
+      const float2 e = in ? __ldg(r1 + c) : make_float2(0.f, 0.f), f = inm ? __ldg(r1 + cm) : make_float2(0.f, 0.f);
+      // Bl0 + i Bl1 = ((R1(u) - conj R1(-u)) - i (R0(u) - conj R0(-u))) / 2
+      return make_float2(0.5f * (e.x - f.x + a.y + b.y), 0.5f * (e.y + f.y + b.x - a.x));
+    };
+    float racc = 0.f;  // this thread's residuals of the pair, summed in FP32 before the FP64 sum
+    float2 qreg[SH::kRegs ? SH::R0 : 1];
+    auto use = [&](int pp, int qq, int x, float2 v) {
+      const float z0 = 1.0f / (1.0f + expf(-beta * (v.x - thr)));
+      const float z1 = 1.0f / (1.0f + expf(-beta * (v.y - thr)));
+      const float d0 = z0 - __ldg(t0 + x), d1 = z1 - __ldg(t1 + x);
+      racc = fmaf(d0, d0, fmaf(d1, d1, racc));
+      const float2 q = make_float2(2.0f * d0 * beta * z0 * (1.0f - z0), 2.0f * d1 * beta * z1 * (1.0f - z1));
+      if constexpr (SH::kRegs)
+        qreg[pp + PERL * qq] = q;
+      else
+        zq[x] = q;
+    };
+    fft_load_use<N, +1, decltype(load), decltype(use), BANDED>(buf, tw, t, load, use);
+    double acc = double(racc);
+    auto usez = [&](int, int, int idx, float2 v) {
+      const int u = freq_of(idx, N);
+      if (u >= -half && u <= half) zq[u + half] = v;
+      if (u == -N / 2 && half == N / 2) zq[crop] = v;  // crop == N: Z(N/2) is Z(-N/2)
+    };
+    if constexpr (SH::kRegs) {
+      auto loadq = [&](int, int r, int) { return qreg[r]; };
+      fft_load_use<N, -1, decltype(loadq), decltype(usez), false>(buf, tw, t, loadq, usez);
+    } else {
+      __syncthreads();  // both dL/dI rows in zq
+      auto loadz = [&](int, int, int idx) { return zq[idx]; };
+      fft_load_use<N, -1, decltype(loadz), decltype(usez), false>(buf, tw, t, loadz, usez);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (t % 32 == 0) wsum[t / 32] = acc;
+    __syncthreads();  // Z on the crop and the warps' sums
+    if (t == 0) {
+      double sum = 0.0;
+      for (int w = 0; w < NW; ++w) sum += wsum[w];
+      partial[(size_t)p * (N / 2) + pr] = sum;
+    }
+    float2* o0 = rowbuf + ((size_t)p * N + y0) * crop;
+    float2* o1 = o0 + crop;
+    for (int c = t; c < crop; c += NT) {
+      const float2 zp = zq[c], zm = zq[crop - c];
+      o0[c] = make_float2(0.5f * (zp.x + zm.x), 0.5f * (zp.y - zm.y));
+      o1[c] = make_float2(0.5f * (zp.y + zm.y), -0.5f * (zp.x - zm.x));
+    }
+  }
+}
+
 // Rows per CTA for the one-row-per-transform kernels: enough CTAs for about
 // eight waves of `per_sm` CTAs per SM, each CTA reusing its twiddle table
 // for its rows.
@@ -281,6 +385,27 @@ cudaError_t band_rows_resist_n(const float2* q, int planes, int crop, const floa
 }
 
 template <int N>
+cudaError_t resist_grad_rows_n(const float2* band, int planes, int crop, const float2* tw, const float* target,
+                               int planes_per_clip, float beta, float thr, float2* rowbuf, double* partial,
+                               cudaStream_t st) {
+  static_assert(Plan<N>::NT % 32 == 0, "whole warps");
+  const size_t sm = sizeof(float2) * (N + PadLen<N>::value + (GradRowsShape<N>::kRegs ? crop + 1 : N + 1));
+  const int ppc = rows_per_cta(N / 2, planes, 2048 / Plan<N>::NT), grid = (N / 2 + ppc - 1) / ppc;
+  cudaError_t e;
+  if (2 * crop <= N) {
+    if ((e = smem_attrs(k_resist_grad_rows<N, true>, sm)) != cudaSuccess) return e;
+    k_resist_grad_rows<N, true><<<dim3(grid, planes), Plan<N>::NT, sm, st>>>(band, crop, tw, target, planes_per_clip,
+                                                                            beta, thr, rowbuf, partial, ppc);
+  } else {
+    if ((e = smem_attrs(k_resist_grad_rows<N, false>, sm)) != cudaSuccess) return e;
+    k_resist_grad_rows<N, false><<<dim3(grid, planes), Plan<N>::NT, sm, st>>>(band, crop, tw, target,
+                                                                             planes_per_clip, beta, thr, rowbuf,
+                                                                             partial, ppc);
+  }
+  return cudaGetLastError();
+}
+
+template <int N>
 cudaError_t band_rows_real_n(const float2* q, int planes, int crop, float scale, const float2* tw, float* out,
                              cudaStream_t st) {
   const int rpc = rows_per_cta(N, planes, 2048 / Plan<N>::NT), grid = (N + rpc - 1) / rpc;
@@ -294,6 +419,17 @@ cudaError_t band_rows_real_n(const float2* q, int planes, int crop, float scale,
 template <int N>
 size_t col_smem_bytes() {
   return sizeof(float2) * (N + ColW<N>::W * ColLD<N>::value);
+}
+
+template <int N>
+cudaError_t mask_cols_n(const float2* rowbuf, int b, int crop, const float2* tw, float2* mhat, const float* gain,
+                        bool gain_real, cudaStream_t st) {
+  const size_t sm = col_smem_bytes<N>();
+  cudaError_t e = smem_attrs(k_mask_cols<N>, sm);
+  if (e != cudaSuccess) return e;
+  k_mask_cols<N><<<dim3(crop / ColW<N>::W, b), Plan<N>::NT * ColW<N>::W, sm, st>>>(rowbuf, crop, tw, gain, mhat,
+                                                                                   gain_real ? 1 : 0);
+  return cudaGetLastError();
 }
 
 template <int N>
@@ -410,6 +546,19 @@ cudaError_t launch_blur_gain(const ResistTaps& taps, int n, int crop, float* gai
   return cudaGetLastError();
 }
 
+cudaError_t launch_resist_grad_rows(const float2* band, int planes, int n, int crop, const float2* tw,
+                                    const float* target, int planes_per_clip, float beta, float thr, float2* rowbuf,
+                                    double* partial, cudaStream_t st) {
+#define CALL(N) resist_grad_rows_n<N>(band, planes, crop, tw, target, planes_per_clip, beta, thr, rowbuf, partial, st)
+  LITHO_DISPATCH_N(n, CALL)
+#undef CALL
+}
+cudaError_t launch_mask_cols(const float2* rowbuf, int b, int n, int crop, const float2* tw, float2* mhat,
+                             const float* gain, bool gain_real, cudaStream_t st) {
+#define CALL(N) mask_cols_n<N>(rowbuf, b, crop, tw, mhat, gain, gain_real, st)
+  LITHO_DISPATCH_NC(n, CALL)
+#undef CALL
+}
 cudaError_t launch_band_rows_resist(const float2* q, int planes, int n, int crop, const float2* tw, float threshold,
                                     float* img, float* iblur, uint8_t* printed, cudaStream_t st) {
 #define CALL(N) band_rows_resist_n<N>(q, planes, crop, tw, threshold, img, iblur, printed, st)

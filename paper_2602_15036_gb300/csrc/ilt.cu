@@ -545,7 +545,8 @@ IltLayout ilt_layout(const litho_kernels* h, int b, int P, int G, void* base) {
   L.qf = reinterpret_cast<float2*>(take(g * N * C * 8));
   L.img = reinterpret_cast<float*>(take(PG * N * N * 4));
   L.blur = reinterpret_cast<float*>(take(PG * N * N * 4));
-  L.partial = reinterpret_cast<double*>(take(g * kPartials * 8));
+  // k_resist_grad: kPartials per clip; the coarse grid's fused rows: one per row pair of each plane
+  L.partial = reinterpret_cast<double*>(take(g * std::max<size_t>(kPartials, size_t(P) * N / 2) * 8));
   const size_t NC = h->nc, C2 = 2 * C;
   if (NC > 0) {
     L.ic = reinterpret_cast<float*>(take(PG * NC * NC * 4));
@@ -715,6 +716,13 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
   const float2* twe = coarse ? h->d_twc : h->d_tw;
   const float lp_scale = float((double(N) / NE) * (double(N) / NE));
   if (coarse) LITHO_TRY_CUDA(launch_blur_gain(taps, N, C2, L.gain, st));
+  // coarse grid: the row spectra of dL/dI on the 2C band, gp x N x 2C, in the image buffer (gp x N x N floats)
+  // (the coarse grid is a power of two nc <= N/2 with 2C <= nc, so 2 x 2C floats fit in a row of N)
+  if (coarse && 2 * C2 > N) {
+    set_error("coarse grid band 2C = %d wider than half the grid (%d)", C2, N);
+    return LITHO_EINVAL;
+  }
+  float2* qrows = reinterpret_cast<float2*>(L.img);
   // Groups of g clips: every launch covers the group's g x P planes (plane
   // i P + p is focus plane f0 + p of clip c0 + i; its fields follow the
   // plane's K kernels).
@@ -735,29 +743,32 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
       const float2* phi = h->d_phi + size_t(f0) * K * C * C;
       const float* lam = h->d_lambda + size_t(f0) * K;
       {
-        ProfScope ps(kStageIltForward, st, 5);
+        ProfScope ps(kStageIltForward, st, coarse ? 6 : 5);
         LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, P * K, NE, C, twe, L.t1, st, g));
         LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, gp,
                                          (long long)K * NE * C, (long long)NE * NE, st, P, h->d_tw32, h->d_tw512));
         if (coarse) {  // the blurred image straight from the interpolation (blur applied to the spectrum)
           LITHO_TRY_CUDA(launch_mask_rows(L.ic, gp, NE, C2, twe, L.mid, st));
           LITHO_TRY_CUDA(launch_interp_cols(L.mid, gp, NE, N, C2, twe, h->d_tw, L.gain, L.big, st));
-          LITHO_TRY_CUDA(launch_band_rows_resist(L.big, gp, N, C2, h->d_tw, float(threshold), nullptr, L.blur,
-                                                 nullptr, st));
+          // blurred rows, resist, dL/dI and its row spectra on the 2C band (into the free image
+          // buffer), partial losses per row pair
+          LITHO_TRY_CUDA(launch_resist_grad_rows(L.big, gp, N, C2, h->d_tw, target_dev + c0 * nn, P,
+                                                 float(resist_steep), float(threshold), qrows, L.partial, st));
+          k_reduce_loss<<<g, 1024, 0, st>>>(L.partial, P * N / 2, L.loss + c0, f0 > 0 ? 1 : 0);
         } else {
           LITHO_TRY_CUDA(launch_resist(L.img, gp, N, taps, float(threshold), L.blur, nullptr, st));
+          k_resist_grad<<<dim3(kPartials, g), 256, 0, st>>>(L.blur, target_dev + c0 * nn, nn, P,
+                                                           float(resist_steep), float(threshold), L.img, L.partial);
+          LITHO_TRY_CUDA(cudaGetLastError());
+          k_reduce_loss<<<g, 1024, 0, st>>>(L.partial, kPartials, L.loss + c0, f0 > 0 ? 1 : 0);
         }
-        k_resist_grad<<<dim3(kPartials, g), 256, 0, st>>>(L.blur, target_dev + c0 * nn, nn, P, float(resist_steep),
-                                                         float(threshold), L.img, L.partial);
-        LITHO_TRY_CUDA(cudaGetLastError());
-        k_reduce_loss<<<g, 1024, 0, st>>>(L.partial, kPartials, L.loss + c0, f0 > 0 ? 1 : 0);
         LITHO_TRY_CUDA(cudaGetLastError());
       }
       {
         ProfScope ps(kStageIltBackward, st, coarse ? 6 : 4);
         const float* gsrc = L.blur;
         if (coarse) {  // low-pass of g (x) q: the spectrum of q on the 2C band times the blur's transfer function
-          LITHO_TRY_CUDA(launch_mask_spectrum(L.img, gp, N, C2, h->d_tw, L.big, L.spec, st, L.gain, true));
+          LITHO_TRY_CUDA(launch_mask_cols(qrows, gp, N, C2, h->d_tw, L.spec, L.gain, true, st));
           LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, gp, NE, C2, twe, L.mid, st));
           LITHO_TRY_CUDA(launch_band_rows_real(L.mid, gp, NE, C2, lp_scale, twe, L.ic, st));
           gsrc = L.ic;

@@ -205,6 +205,16 @@ struct ResistTaps;
 cudaError_t launch_blur_gain(const ResistTaps& taps, int n, int crop, float* gain, cudaStream_t st);
 // Band rows carrying the blur channel: z = sum_c q[p][y][c] e^{+2 pi i u_c x/N};
 // img = Re z (skipped when NULL), iblur = Im z, printed = [Im z >= threshold] (skipped when NULL).
+// ILT forward end on the coarse grid, per pair of full-grid rows: blurred rows from the
+// band rows, sigmoid resist, dL/dI and its row spectra on the crop (rowbuf, as
+// launch_mask_rows), and one FP64 partial loss per row pair at partial[plane][pair]
+// (planes x n/2 doubles).  Plane p uses target clip p / planes_per_clip.
+cudaError_t launch_resist_grad_rows(const float2* band, int planes, int n, int crop, const float2* tw,
+                                    const float* target, int planes_per_clip, float beta, float thr, float2* rowbuf,
+                                    double* partial, cudaStream_t st);
+// Column half of launch_mask_spectrum on row spectra already in rowbuf.
+cudaError_t launch_mask_cols(const float2* rowbuf, int b, int n, int crop, const float2* tw, float2* mhat,
+                             const float* gain, bool gain_real, cudaStream_t st);
 cudaError_t launch_band_rows_resist(const float2* q, int planes, int n, int crop, const float2* tw, float threshold,
                                     float* img, float* iblur, uint8_t* printed, cudaStream_t st);
 

@@ -139,18 +139,28 @@ def test_ilt_fp32_finite_differences(litho_lib, cuda):
         assert abs(fd - g[0, y, x]) <= 1e-2 * np.abs(g).max(), (fd, g[0, y, x])
 
 
-def test_ilt_full_size_1024_k16_five_focus(litho_lib, cuda):
+_ORACLE_1024 = {}
+
+
+@pytest.mark.parametrize("precision", ["fft32", "fft32/coarse"])
+def test_ilt_full_size_1024_k16_five_focus(litho_lib, cuda, precision):
+    """The benchmark's clip size and optics, on both grids (the coarse grid's
+    1024-point rows keep dL/dI in registers between their two transforms)."""
     n, pixel, k = 1024, 8.0, 16
     focus = [-60.0, -30.0, 0.0, 30.0, 60.0]
     lam, phi = oracle_kernel_set(DUV_ANNULAR, n, pixel, focus, k)
     kern = litho_lib.litho_upload_kernels(n, pixel, lam, phi)
+    if precision.endswith("/coarse"):
+        assert 0 < kern.grid(precision) < n
     theta, target = synth.ilt_clip(n, pixel, seed=4000)
-    g, loss = _gpu(litho_lib, cuda, kern, theta[None], target[None])
-    lo, ref = _oracle(theta, target, lam, phi, pixel)
+    g, loss = _gpu(litho_lib, cuda, kern, theta[None], target[None], precision=precision)
+    if not _ORACLE_1024:
+        _ORACLE_1024["r"] = _oracle(theta, target, lam, phi, pixel)
+    lo, ref = _ORACLE_1024["r"]
     st = synth.Stream(65)
     pts = list(zip(st.integers(0, n - 1, 64), st.integers(0, n - 1, 64)))
     rel, per = _check(g[0], ref, pts)
-    print(f"1024: loss {loss[0]:.4f} vs {lo:.4f}; grad rel l2 {rel:.2e}, per-pixel {per:.2e}")
+    print(f"1024 {precision}: loss {loss[0]:.4f} vs {lo:.4f}; grad rel l2 {rel:.2e}, per-pixel {per:.2e}")
     assert abs(loss[0] - lo) <= 1e-5 * lo
     assert rel <= 1e-4 and per <= 1e-4
 
