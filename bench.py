@@ -633,10 +633,10 @@ def run_aerial(args, ctx):
         tr = dict((tag, ms) for tag, ms in L.litho_host_trace_read())
         # device time per chunk, ms since the call's first work: input copied, kernels done, outputs copied
         dev = []
-        for c in range(64):
-            if 100 + 8 * c not in tr:
+        for ci in range(64):
+            if 100 + 8 * ci not in tr:
                 break
-            dev.append(tuple(round(tr[100 + 8 * c + i], 3) for i in range(3)))
+            dev.append(tuple(round(tr[100 + 8 * ci + i], 3) for i in range(3)))
         e2e_trace.append((tr.get(-1, 0.0), tr.get(-2, 0.0) - tr.get(-1, 0.0), dev))
     e2e_s = ctx.max_over_ranks(time.perf_counter() - t0)
     ctx.barrier()

@@ -310,15 +310,40 @@ struct TwOff {
 };
 
 // Twiddle + DFT of one butterfly's R values.
+// The pass's table holds w^(r k), r = 1..R-1, for its root w.  For R = 4, 8
+// and 16 only the powers r = 1, 2, 4, 8 are read and the others formed as
+// products of two or three of them (w^3 = w^1 w^2, w^(r+4) = w^r w^4,
+// w^(r+8) = w^r w^8): a few packed multiplies instead of shared-memory loads,
+// which bound the column transforms, at one to two roundings more per twiddle.
 template <int N, int R, int NS, int SIGN, int OFF, bool BANDED = false>
 __device__ __forceinline__ void twiddle_dft(float2 (&v)[R], int j, const float2* __restrict__ tw) {
   if (NS > 1) {
     const int k = j % NS;
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
+    auto ld = [&](int r) {
       float2 w = tw[OFF + (r - 1) * NS + k];
       if (SIGN > 0) w.y = -w.y;
-      v[r] = cmul(v[r], w);
+      return w;
+    };
+    if constexpr (R == 4 || R == 8 || R == 16) {
+      float2 w[R];
+      w[1] = ld(1);
+      w[2] = ld(2);
+      w[3] = cmul(w[1], w[2]);
+      if constexpr (R >= 8) {
+        w[4] = ld(4);
+#pragma unroll
+        for (int r = 5; r < 8; ++r) w[r] = cmul(w[r - 4], w[4]);
+      }
+      if constexpr (R == 16) {
+        w[8] = ld(8);
+#pragma unroll
+        for (int r = 9; r < 16; ++r) w[r] = cmul(w[r - 8], w[8]);
+      }
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], w[r]);
+    } else {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[r] = cmul(v[r], ld(r));
     }
   }
   dft_reg<R, SIGN, BANDED>(v);
