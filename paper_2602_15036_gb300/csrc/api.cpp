@@ -408,14 +408,15 @@ struct FusedResist {
 
 // `planes` coarse images in L.ic -> N x N planes at `out` (plane offset `p0`
 // of the call for the fused resist outputs).
+// rows_done: stage 2 has already written the coarse images' row spectra to L.rowbuf2.
 static litho_status upsample(const litho_kernels* h, litho_precision p, const AerialLayout& L, int planes, float* out,
-                             const FusedResist* fr, size_t p0, cudaStream_t st) {
+                             const FusedResist* fr, size_t p0, cudaStream_t st, bool rows_done = false) {
   const int N = h->n, NC = coarse_n(h, p), C2 = 2 * h->crop;
   const float2* twc = coarse_tw(h, p);
   const float* gain = fr ? L.gain : nullptr;
-  ProfScope ps(fr ? kStageUpsampleResist : kStageUpsample, st, 3);
+  ProfScope ps(fr ? kStageUpsampleResist : kStageUpsample, st, rows_done ? 2 : 3);
   if (interp_cols_supported(NC, N)) {
-    LITHO_TRY_CUDA(launch_mask_rows(L.ic, planes, NC, C2, twc, L.rowbuf2, st));
+    if (!rows_done) LITHO_TRY_CUDA(launch_mask_rows(L.ic, planes, NC, C2, twc, L.rowbuf2, st));
     LITHO_TRY_CUDA(launch_interp_cols(L.rowbuf2, planes, NC, N, C2, twc, h->d_tw, gain, L.q, st));
   } else {
     LITHO_TRY_CUDA(launch_mask_spectrum(L.ic, planes, NC, C2, twc, L.rowbuf2, L.spec, st, gain));
@@ -493,6 +494,9 @@ static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, in
   const float2* tw = coarse ? coarse_tw(h, p) : h->d_tw;
   // On a 1024-point grid stage 1 takes sqrt(lam) Phi and the warp-per-row stage 2 sums |E|^2 unweighted
   const bool folded = h->d_phi_s && h->d_tw32 && stage2_w32_supported(NE, C);
+  // with the warp-per-row stage 2 on the coarse grid, stage 2 writes the row spectra that the
+  // interpolation's column pass reads, in place of the coarse images
+  const bool rows_in_stage2 = coarse && folded && interp_cols_supported(NE, N);
   for (int c0 = 0; c0 < b; c0 += G) {
     const int g = std::min(G, b - c0);
     float* img = intensity_dev + size_t(c0) * F * N * N;
@@ -505,10 +509,10 @@ static litho_status aerial_run(const litho_kernels* h, const float* mask_dev, in
       ProfScope ps(kStageStage2Fft, st, 1);
       LITHO_TRY_CUDA(launch_stage2_fft(L.t1, h->d_lambda, K, NE, C, float(dose), tw, coarse ? L.ic : img, g * F,
                                        (long long)K * NE * C, (long long)NE * NE, st, F, h->d_tw32, h->d_tw512,
-                                       folded));
+                                       folded, rows_in_stage2 ? L.rowbuf2 : nullptr, 2 * C));
     }
     if (coarse) {
-      litho_status s = upsample(h, p, L, g * F, img, fr, size_t(c0) * F, st);
+      litho_status s = upsample(h, p, L, g * F, img, fr, size_t(c0) * F, st, rows_in_stage2);
       if (s != LITHO_OK) return s;
     }
   }

@@ -576,12 +576,13 @@ cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int
 cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
                               long long img_plane_stride, cudaStream_t st, int lam_period, const float2* tw32,
-                              const float2* tw512, bool folded) {
+                              const float2* tw512, bool folded, float2* spec, int spec_crop) {
   if (lam_period <= 0) lam_period = planes;
   if (tw32 && stage2_w32_supported(n, crop))
     return launch_stage2_w32(t1, lam, nk, n, crop, dose, tw32, img, planes, t1_plane_stride, img_plane_stride,
-                             lam_period, st, folded);
-  if (folded) return cudaErrorInvalidValue;  // only the warp-per-row kernel sums unweighted
+                             lam_period, st, folded, spec, spec_crop);
+  // only the warp-per-row kernel sums unweighted or writes row spectra
+  if (folded || spec) return cudaErrorInvalidValue;
   if (tw512 && stage2_w512_supported(n, crop))
     return launch_stage2_w512(t1, lam, nk, n, crop, dose, tw512, img, planes, t1_plane_stride, img_plane_stride,
                               lam_period, st);

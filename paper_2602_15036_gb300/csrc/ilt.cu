@@ -608,16 +608,19 @@ litho_status ai_channels(const litho_kernels* h, const float* target, int b, dou
   const float2* phi = h->d_phi + size_t(focus) * K * C * C;
   const float* lam = h->d_lambda + size_t(focus) * K;
   const float scale = float(2.0 * dose / (double(N) * double(N)));
+  // a 1024-point coarse grid: the warp-per-row stage 2 writes the coarse image's row spectra itself
+  const bool rows2 = coarse && h->d_tw32 && stage2_w32_supported(NE, C);
   for (int c0 = 0; c0 < b; c0 += G) {
     const int g = std::min(G, b - c0);
     {  // channel 1: the aerial image of the targets (interpolated from the coarse grid)
-      ProfScope ps(kStageIltForward, st, coarse ? 7 : 4);
+      ProfScope ps(kStageIltForward, st, coarse ? (rows2 ? 6 : 7) : 4);
       LITHO_TRY_CUDA(launch_mask_spectrum(target + c0 * nn, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
       LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, K, NE, C, twe, L.t1, st, g));
       LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, g,
-                                       (long long)K * NE * C, (long long)NE * NE, st, 1, h->d_tw32, h->d_tw512));
+                                       (long long)K * NE * C, (long long)NE * NE, st, 1, h->d_tw32, h->d_tw512, false,
+                                       rows2 ? L.mid : nullptr, C2));
       if (coarse) {
-        LITHO_TRY_CUDA(launch_mask_rows(L.ic, g, NE, C2, twe, L.mid, st));
+        if (!rows2) LITHO_TRY_CUDA(launch_mask_rows(L.ic, g, NE, C2, twe, L.mid, st));
         LITHO_TRY_CUDA(launch_interp_cols(L.mid, g, NE, N, C2, twe, h->d_tw, nullptr, L.big, st));
         LITHO_TRY_CUDA(launch_band_rows_real(L.big, g, N, C2, 1.0f, h->d_tw, L.img, st));
       }
@@ -716,6 +719,8 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
   const float2* twe = coarse ? h->d_twc : h->d_tw;
   const float lp_scale = float((double(N) / NE) * (double(N) / NE));
   if (coarse) LITHO_TRY_CUDA(launch_blur_gain(taps, N, C2, L.gain, st));
+  // a 1024-point coarse grid: the warp-per-row stage 2 writes the coarse image's row spectra itself
+  const bool rows2 = coarse && h->d_tw32 && stage2_w32_supported(NE, C);
   // coarse grid: the row spectra of dL/dI on the 2C band, gp x N x 2C, in the image buffer (gp x N x N floats)
   // (the coarse grid is a power of two nc <= N/2 with 2C <= nc, so 2 x 2C floats fit in a row of N)
   if (coarse && 2 * C2 > N) {
@@ -743,12 +748,13 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
       const float2* phi = h->d_phi + size_t(f0) * K * C * C;
       const float* lam = h->d_lambda + size_t(f0) * K;
       {
-        ProfScope ps(kStageIltForward, st, coarse ? 6 : 5);
+        ProfScope ps(kStageIltForward, st, coarse ? (rows2 ? 5 : 6) : 5);
         LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, phi, P * K, NE, C, twe, L.t1, st, g));
         LITHO_TRY_CUDA(launch_stage2_fft(L.t1, lam, K, NE, C, float(dose), twe, coarse ? L.ic : L.img, gp,
-                                         (long long)K * NE * C, (long long)NE * NE, st, P, h->d_tw32, h->d_tw512));
+                                         (long long)K * NE * C, (long long)NE * NE, st, P, h->d_tw32, h->d_tw512,
+                                         false, rows2 ? L.mid : nullptr, C2));
         if (coarse) {  // the blurred image straight from the interpolation (blur applied to the spectrum)
-          LITHO_TRY_CUDA(launch_mask_rows(L.ic, gp, NE, C2, twe, L.mid, st));
+          if (!rows2) LITHO_TRY_CUDA(launch_mask_rows(L.ic, gp, NE, C2, twe, L.mid, st));
           LITHO_TRY_CUDA(launch_interp_cols(L.mid, gp, NE, N, C2, twe, h->d_tw, L.gain, L.big, st));
           // blurred rows, resist, dL/dI and its row spectra on the 2C band (into the free image
           // buffer), partial losses per row pair

@@ -157,10 +157,14 @@ cudaError_t launch_stage1_fft(const float2* mhat, const float2* phi, int nk, int
 // tw512 (d_tw512) 512-point rows the two-rows-per-warp kernel.  folded (with
 // tw32 only): the fields were made from sqrt(lam) Phi, so |E|^2 is summed
 // without the weight (lam still marks the zero kernels, which are skipped).
+// spec (with tw32 only): instead of the image, each image row's forward
+// transform on the spec_crop frequencies |u| < spec_crop/2, laid out as
+// launch_mask_rows writes them ([planes][n][spec_crop]); img is not written.
 cudaError_t launch_stage2_fft(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw, float* img, int planes, long long t1_plane_stride,
                               long long img_plane_stride, cudaStream_t st, int lam_period = 0,
-                              const float2* tw32 = nullptr, const float2* tw512 = nullptr, bool folded = false);
+                              const float2* tw32 = nullptr, const float2* tw512 = nullptr, bool folded = false,
+                              float2* spec = nullptr, int spec_crop = 0);
 // The warp-per-row stage 2 for 1024-point rows (stage2_w32.cu) and its
 // second-pass twiddle table (31 x 32 entries w^(r l), r in [1, 32), l in [0, 32)).
 bool stage2_w32_supported(int n, int crop);
@@ -173,7 +177,8 @@ void stage2_w32_table(float2* out);
 constexpr int kStage2W32TableLen = 31 * 32;
 cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw2, float* img, int planes, long long t1_plane, long long img_plane,
-                              int lam_period, cudaStream_t st, bool folded = false);
+                              int lam_period, cudaStream_t st, bool folded = false, float2* spec = nullptr,
+                              int c2 = 0);
 
 // A device-side delay of about `ms` milliseconds on `st` (util.cu): one
 // thread spinning on the SM clock for a fixed number of cycles, which always

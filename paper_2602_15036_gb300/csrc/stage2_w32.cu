@@ -47,11 +47,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int PENDING>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory"); }
 
-template <bool BANDED, int kWarps, bool FOLDED>
+// SPEC: instead of the image row, its forward transform cropped to the c2
+// frequencies |u| < c2/2 (index u + c2/2 of row y of plane p in `spec`, plane
+// stride 1024 c2), as the first step of the exact Fourier interpolation:
+// the row x = lane + 32 q is already where the four-step forward transform
+// wants it (pass 1 over q, twiddle e^{-2 pi i lane u1 / 1024}, exchange,
+// pass 2 over the lanes, output u1 + 32 u2 in lane u1).
+template <bool BANDED, int kWarps, bool FOLDED, bool SPEC>
 __global__ void __launch_bounds__(32 * kWarps, 1)
     k_stage2_w32(const float2* __restrict__ t1, const float* __restrict__ lam, int nk, int crop, float dose,
                  const float2* __restrict__ tw2_g, float* __restrict__ img, long long t1_plane, long long img_plane,
-                 int lam_period) {
+                 int lam_period, float2* __restrict__ spec, int c2) {
   extern __shared__ float4 smem_raw[];
   float2* tw2 = reinterpret_cast<float2*>(smem_raw);  // w^(r l) at (r - 1) 32 + l
   float2* rowbuf = tw2 + (kR - 1) * kR;                // [kWarps][kRowLd]
@@ -110,33 +116,64 @@ __global__ void __launch_bounds__(32 * kWarps, 1)
       acc[q] = FOLDED ? fmaf(v[q].x, v[q].x, fmaf(v[q].y, v[q].y, acc[q]))  // sqrt(lam) is in the field
                       : fmaf(l, fmaf(v[q].x, v[q].x, v[q].y * v[q].y), acc[q]);
   }
-  float* out = img + plane * img_plane + (size_t)y * kN;
+  if constexpr (SPEC) {
+    float2 v[kR];
 #pragma unroll
-  for (int q = 0; q < kR; ++q) out[lane + kR * q] = dose * acc[q];
+    for (int q = 0; q < kR; ++q) v[q] = make_float2(dose * acc[q], 0.f);
+    dft32<-1, false>(v);
+#pragma unroll
+    for (int u1 = 0; u1 < kR; ++u1) {
+      float2 x = v[u1];
+      if (u1 > 0) {
+        const float2 w = tw2[(u1 - 1) * kR + lane];
+        x = cmul(x, make_float2(w.x, -w.y));
+      }
+      buf[lane * (kR + 1) + u1] = x;  // position (u1, lane), padded
+    }
+    __syncwarp();
+#pragma unroll
+    for (int l = 0; l < kR; ++l) v[l] = buf[lane + (kR + 1) * l];
+    dft32<-1, false>(v);
+    float2* srow = spec + (size_t)plane * kN * c2 + (size_t)y * c2;
+    const int h2 = c2 / 2;
+#pragma unroll
+    for (int u2 = 0; u2 < kR; ++u2) {
+      const int u = lane + kR * u2, us = u < kN / 2 ? u : u - kN;
+      if (us >= -h2 && us < h2) srow[us + h2] = v[u2];
+    }
+  } else {
+    float* out = img + plane * img_plane + (size_t)y * kN;
+#pragma unroll
+    for (int q = 0; q < kR; ++q) out[lane + kR * q] = dose * acc[q];
+  }
 }
 
-template <bool BANDED, int kWarps, bool FOLDED>
+template <bool BANDED, int kWarps, bool FOLDED, bool SPEC>
 cudaError_t launch_w32_k(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw2,
                          float* img, int planes, long long t1_plane, long long img_plane, int lam_period,
-                         cudaStream_t st) {
+                         cudaStream_t st, float2* spec, int c2) {
   const dim3 grid((kN + kWarps - 1) / kWarps, planes);
   const size_t sm = sizeof(float2) * ((kR - 1) * kR + kWarps * kRowLd + size_t(kWarps) * crop);
-  cudaError_t e = smem_attrs(k_stage2_w32<BANDED, kWarps, FOLDED>, sm);
+  cudaError_t e = smem_attrs(k_stage2_w32<BANDED, kWarps, FOLDED, SPEC>, sm);
   if (e != cudaSuccess) return e;
-  k_stage2_w32<BANDED, kWarps, FOLDED><<<grid, 32 * kWarps, sm, st>>>(t1, lam, nk, crop, dose, tw2, img, t1_plane,
-                                                                      img_plane, lam_period);
+  k_stage2_w32<BANDED, kWarps, FOLDED, SPEC><<<grid, 32 * kWarps, sm, st>>>(t1, lam, nk, crop, dose, tw2, img,
+                                                                            t1_plane, img_plane, lam_period, spec, c2);
   return cudaGetLastError();
 }
 
 template <int kWarps>
 cudaError_t launch_w32_t(const float2* t1, const float* lam, int nk, int crop, float dose, const float2* tw2,
                          float* img, int planes, long long t1_plane, long long img_plane, int lam_period,
-                         cudaStream_t st, bool folded) {
+                         cudaStream_t st, bool folded, float2* spec, int c2) {
   const bool banded = crop / 2 <= kN / 4;  // the band leaves indices [N/4, 3N/4) empty
-#define W32(B, F) \
-  launch_w32_k<B, kWarps, F>(t1, lam, nk, crop, dose, tw2, img, planes, t1_plane, img_plane, lam_period, st)
-  if (banded) return folded ? W32(true, true) : W32(true, false);
-  return folded ? W32(false, true) : W32(false, false);
+#define W32(B, F, S) \
+  launch_w32_k<B, kWarps, F, S>(t1, lam, nk, crop, dose, tw2, img, planes, t1_plane, img_plane, lam_period, st, spec, c2)
+  if (spec) {
+    if (banded) return folded ? W32(true, true, true) : W32(true, false, true);
+    return folded ? W32(false, true, true) : W32(false, false, true);
+  }
+  if (banded) return folded ? W32(true, true, false) : W32(true, false, false);
+  return folded ? W32(false, true, false) : W32(false, false, false);
 #undef W32
 }
 
@@ -263,13 +300,15 @@ cudaError_t launch_stage2_w512(const float2* t1, const float* lam, int nk, int n
 
 cudaError_t launch_stage2_w32(const float2* t1, const float* lam, int nk, int n, int crop, float dose,
                               const float2* tw2, float* img, int planes, long long t1_plane, long long img_plane,
-                              int lam_period, cudaStream_t st, bool folded) {
+                              int lam_period, cudaStream_t st, bool folded, float2* spec, int c2) {
   if (!stage2_w32_supported(n, crop) || !tw2) return cudaErrorInvalidValue;
+  if (spec && (c2 < 2 || c2 > kN || c2 % 2 != 0)) return cudaErrorInvalidValue;
   if (lam_period <= 0) lam_period = planes;
   // 12 warps per CTA: one CTA of 384 threads fits the SM's registers (about 160 per thread);
   // measured on the 2048^2 workload's 1024-point rows: 5.90 ms per step against 6.29 with 8
   // warps and 6.04 with 16 (128 registers)
-  return launch_w32_t<12>(t1, lam, nk, crop, dose, tw2, img, planes, t1_plane, img_plane, lam_period, st, folded);
+  return launch_w32_t<12>(t1, lam, nk, crop, dose, tw2, img, planes, t1_plane, img_plane, lam_period, st, folded,
+                          spec, c2);
 }
 
 }  // namespace litho

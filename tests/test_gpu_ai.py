@@ -63,6 +63,22 @@ def test_ai_inputs_match_oracle(litho_lib, cuda, precision):
     assert np.isclose(x[:, 1].max(), 1.0) and np.isclose(x[:, 2].min(), 0.0) and np.isclose(x[:, 2].max(), 1.0)
 
 
+def test_ai_inputs_2048_on_the_1024_point_coarse_grid(litho_lib, cuda):
+    """The AI step's clip size: on a 1024-point coarse grid the warp-per-row stage 2 writes the
+    coarse image's row spectra for the interpolation itself."""
+    import torch
+    L = litho_lib
+    n = 2048
+    lam, phi, targets = _setup(n, focus=(0.0,), k=6, b=1)
+    kern = L.litho_upload_kernels(n, 8.0, lam, phi)
+    assert kern.grid("fft32/coarse") == 1024
+    x = L.litho_ai_inputs(kern, torch.from_numpy(targets).to(cuda), focus=0, precision="fft32/coarse").cpu().numpy()
+    ref, _, _ = OA.ai_channels(targets, lam[0], phi[0])
+    assert np.array_equal(x[:, 0], targets)
+    assert np.abs(x[:, 1] - ref[:, 1]).max() <= 1e-5
+    assert np.abs(x[:, 2] - ref[:, 2]).max() <= 1e-4
+
+
 def test_print_images_match_oracle(litho_lib, cuda):
     import torch
     L = litho_lib
