@@ -214,9 +214,17 @@ def stage_models(prec: str, clips: int, n: int, crop: int, n_focus: int, k_eff: 
     }
     if coarse:
         c2 = 2 * crop
-        up = planes * (ne / 2 * fft(ne) + c2 * fft(ne) + c2 * fft(n) + n * fft(n))
-        m["upsample"] = (up, planes * (ne * ne * 4.0 + n * n * 4.0))
-        m["upsample_resist"] = (up + planes * c2 * c2 * 6.0, planes * (ne * ne * 4.0 + n * n * 9.0))
+        # on a 1024-point grid the warp-per-row stage 2 also takes each image row forward and writes
+        # its band spectrum (planes x ne x c2 complex) in place of the coarse image
+        rows_in_stage2 = base == "fft32" and ne == 1024 and crop <= 512
+        row_fft = planes * ne / 2 * fft(ne)  # two real rows per complex transform
+        up_in = planes * ne * c2 * 8.0 if rows_in_stage2 else planes * ne * ne * 4.0
+        up = planes * (c2 * fft(ne) + c2 * fft(n) + n * fft(n)) + (0.0 if rows_in_stage2 else row_fft)
+        if rows_in_stage2:
+            f2, b2 = m["stage2_fft"]
+            m["stage2_fft"] = (f2 + planes * ne * fft(ne), b2 - planes * ne * ne * 4.0 + up_in)
+        m["upsample"] = (up, up_in + planes * n * n * 4.0)
+        m["upsample_resist"] = (up + planes * c2 * c2 * 6.0, up_in + planes * n * n * 9.0)
     return m
 
 
