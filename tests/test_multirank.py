@@ -71,7 +71,9 @@ def test_stage_models_are_consistent():
     assert bench.fft_group(64, 3, 24, 1024, 448) == 8
     phi, t1 = 72 * 448 ** 2 * 8.0, 64 * 72 * 1024 * 448 * 8.0
     assert m3["stage1_fft"][1] == pytest.approx(8 * phi + 64 * 448 ** 2 * 8.0 + t1)
-    assert m3["stage2_fft"][1] == pytest.approx(t1 + 64 * 3 * 1024 ** 2 * 4.0)
+    # on the 1024-point grid stage 2 writes each row's 2C = 896 band spectrum instead of the image
+    assert m3["stage2_fft"][1] == pytest.approx(t1 + 64 * 3 * 1024 * 896 * 8.0)
+    assert m3["upsample_resist"][1] == pytest.approx(64 * 3 * (1024 * 896 * 8.0 + 2048 ** 2 * 9.0))
     # roofline: the binding resource is the one with the longer time at peak
     r = bench.rooflines({"stage1_fft": (10.0, 8), "stage2_fft": (10.0, 8)}, 1, m3, peaks)
     assert r["stage1_fft"]["bound"] == "hbm" and r["stage2_fft"]["bound"] == "alu"
