@@ -15,12 +15,15 @@
 //   k_sigmoid        m from theta
 //   (mask spectrum, stage 1, stage 2, resist blur: shared with the forward path)
 //   k_resist_grad    Z, q and per-block FP64 partial sums of (Z - target)^2
+//                    (coarse grid: k_resist_grad_rows, per row pair, with the
+//                    forward row spectra of q)
 //   k_reduce_loss    fixed-order FP64 sum of the partials (deterministic)
 //   k_adj_rows       per image row: E_fk from the stage-1 field (inverse FFT),
 //                    times G_f, forward FFT, crop columns -> U_fk[y][c]
-//   k_adj_cols       per crop column block: forward FFT over y, crop rows,
-//                    times lam conj(Phi) -> SK_fk[v][c]
-//   k_sum_planes     S = sum over (f, k) of SK in fixed order
+//   k_adj_cols       per crop column block and run of a clip's fields: forward
+//                    FFT over y, crop rows, times lam conj(Phi), summed over
+//                    the run in registers -> one partial S per run
+//   k_sum_planes     S = sum of a clip's runs in fixed order
 //   k_grad_rows      band-to-full inverse of S along x (after stage 1 along y),
 //                    real part, chain factor -> dL/dtheta
 // The fields E are never stored: each backward row recomputes E_fk from the
@@ -293,21 +296,56 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2)
 // loaded once.
 template <int N> struct AdjW { static constexpr int W = Plan<N>::NT <= 64 ? 8 : 4; };
 
+// Where the adjoint columns keep their sums: in registers they cost the
+// 512-point kernel its second CTA per SM (or spills), in shared memory they
+// cost the 1024-point one (twice the slots); so shared memory up to 512.
+template <int N> struct AdjAccInSmem { static constexpr bool value = N <= 512; };
+
+// Runs of fields per clip in the adjoint columns: the largest divisor of the
+// clip's field count that is at most 8 (a function of that count alone, so a
+// clip's sums do not depend on how many clips a launch holds).
+int adj_col_splits(int period) {
+  for (int d = 8; d > 1; --d)
+    if (period % d == 0) return d;
+  return 1;
+}
+
+// Per crop column block and run of fields j in [j0, j1) of one clip (the
+// clip's `period` fields split into `splits` runs of period / splits): the
+// forward transform over y of each field's column, the crop, lam conj(Phi)
+// times it, summed over the run (each thread keeps the same
+// output positions for every field; the sums sit in registers or, up to 512
+// points, in shared memory, one slot per thread and position)
+// and written once, to
+// part[clip splits + split][cv][c].  k_sum_planes then adds a clip's runs in
+// order, so the sum's order depends on the clip's own field count only.
 template <int N>
-__global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const float2* __restrict__ u,
+__global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W, AdjAccInSmem<N>::value ? 2 : 1) k_adj_cols(const float2* __restrict__ u,
                                                                         const float2* __restrict__ phi,
                                                                         const float* __restrict__ lam, int crop,
                                                                         const float2* __restrict__ tw_g,
-                                                                        float2* __restrict__ sk, int period,
-                                                                        int fields, int jb) {
+                                                                        float2* __restrict__ part, int period,
+                                                                        int splits) {
   constexpr int W = AdjW<N>::W, NT = Plan<N>::NT, LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
+  constexpr int RL = Plan<N>::R[Plan<N>::P - 1], PERL = PassShape<N, NT, RL>::PER;
+  constexpr int T = NT * W;
+  constexpr bool kSmem = AdjAccInSmem<N>::value;
   extern __shared__ float2 sm[];
   float2* tw = sm;
   float2* buf = sm + N;
   constexpr int R0 = Plan<N>::R[0], NB0 = N / R0;
   static_assert(PassShape<N, NT, R0>::PER == 1, "one first-pass butterfly per thread");
   const int tid = threadIdx.x, g = tid % W, t = tid / W, c0 = blockIdx.x * W, half = crop / 2;
-  const int j0 = blockIdx.y * jb, j1 = min(fields, j0 + jb);
+  const int clip = blockIdx.y / splits, split = blockIdx.y % splits, jb = period / splits;
+  float2* acc_s = buf + W * LD;  // kSmem: this thread's PERL x RL sums at (pp RL + q) T + tid
+  float2 acc_r[kSmem ? 1 : PERL * RL];
+  auto acc = [&](int i) -> float2& {
+    if constexpr (kSmem)
+      return acc_s[i * T + tid];  // read and written by tid alone
+    else
+      return acc_r[i];
+  };
+  const int j0 = clip * period + split * jb, j1 = j0 + jb;
   load_twiddles<N>(tw, tw_g);
   // this thread's first-pass inputs (rows t + r N/R0) of a field, loaded one field ahead
   float2 nxt[R0];
@@ -316,14 +354,14 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
 #pragma unroll
     for (int r = 0; r < R0; ++r) nxt[r] = t < NB0 ? __ldg(src + (size_t)(t + r * NB0) * crop) : make_float2(0.f, 0.f);
   };
-  if (j0 < j1) prefetch(j0);
+  prefetch(j0);
   __syncthreads();
+#pragma unroll
+  for (int i = 0; i < PERL * RL; ++i) acc(i) = make_float2(0.f, 0.f);
   for (int j = j0; j < j1; ++j) {
     const int jk = j % period;
     const float l = lam[jk];
-    float2* dst = sk + (size_t)j * crop * crop + c0 + g;  // crop row cv at dst[cv crop]
-    if (l == 0.f) {  // uniform across the block
-      for (int cv = t; cv < crop; cv += NT) dst[(size_t)cv * crop] = make_float2(0.f, 0.f);
+    if (l == 0.f) {  // uniform across the block: nothing to add
       if (j + 1 < j1) prefetch(j + 1);
       continue;
     }
@@ -336,15 +374,29 @@ __global__ void __launch_bounds__(Plan<N>::NT * AdjW<N>::W) k_adj_cols(const flo
     auto after_first = [&]() {
       if (j + 1 < j1) prefetch(j + 1);
     };
-    auto use = [&](int, int, int idx, float2 h) {
+    auto use = [&](int pp, int q, int idx, float2 h) {
       const int cv = freq_of_idx(idx, N) + half;
       if (cv >= 0 && cv < crop) {
         const float2 p = __ldg(ph + (size_t)cv * crop);
-        // lam conj(p) h
-        dst[(size_t)cv * crop] = make_float2(l * (p.x * h.x + p.y * h.y), l * (p.x * h.y - p.y * h.x));
+        // += lam conj(p) h
+        float2& a = acc(pp * RL + q);
+        a = make_float2(fmaf(l, p.x * h.x + p.y * h.y, a.x), fmaf(l, p.x * h.y - p.y * h.x, a.y));
       }
     };
     fft_load_use<N, -1, decltype(load), decltype(use), false>(buf + g * LD, tw, t, load, use, after_first);
+  }
+  // the last pass's output positions of this thread: idx = jj + q N/RL, jj = t + pp NT
+  float2* dst = part + (size_t)blockIdx.y * crop * crop + c0 + g;  // crop row cv at dst[cv crop]
+#pragma unroll
+  for (int pp = 0; pp < PERL; ++pp) {
+    const int jj = t + pp * NT;
+    if (jj < N / RL) {
+#pragma unroll
+      for (int q = 0; q < RL; ++q) {
+        const int cv = freq_of_idx(jj + q * (N / RL), N) + half;
+        if (cv >= 0 && cv < crop) dst[(size_t)cv * crop] = acc(pp * RL + q);
+      }
+    }
   }
 }
 
@@ -429,27 +481,18 @@ cudaError_t adj_rows_n(const float2* t1, const float* lam, int nk, int crop, con
 }
 
 template <int N>
-cudaError_t adj_cols_n(const float2* u, const float2* phi, const float* lam, int crop, const float2* tw, float2* sk,
-                       int planes, int period, cudaStream_t st) {
+cudaError_t adj_cols_n(const float2* u, const float2* phi, const float* lam, int crop, const float2* tw, float2* part,
+                       int fields, int period, cudaStream_t st) {
   constexpr int W = AdjW<N>::W;
-  if (crop % W != 0) return cudaErrorInvalidValue;
+  if (crop % W != 0 || period < 1 || fields % period != 0) return cudaErrorInvalidValue;
   constexpr int LD = (PadLen<N>::value + 15) / 16 * 16 + 16 / W;
-  const size_t sm = sizeof(float2) * (N + W * LD);
+  constexpr int RL = Plan<N>::R[Plan<N>::P - 1], PERL = PassShape<N, Plan<N>::NT, RL>::PER;
+  const size_t sm = sizeof(float2) * (N + W * LD + (AdjAccInSmem<N>::value ? size_t(PERL) * RL * Plan<N>::NT * W : 0));
   cudaError_t e = smem_attrs(k_adj_cols<N>, sm);
   if (e != cudaSuccess) return e;
-  // fields per CTA: about four waves of CTAs over the GPU, at least one field each
-  static int sms = 0;  // the same GPU model throughout a process
-  if (!sms) {
-    int dev = 0, v = 0;
-    sms = cudaGetDevice(&dev) == cudaSuccess &&
-                  cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0
-              ? v
-              : 152;
-  }
-  const long long cols = crop / W;
-  const int jb = int(std::max<long long>(1, (long long)planes * cols / (8LL * sms)));
-  k_adj_cols<N><<<dim3(crop / W, (planes + jb - 1) / jb), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, sk,
-                                                                                     period, planes, jb);
+  const int splits = adj_col_splits(period);
+  k_adj_cols<N><<<dim3(crop / W, (fields / period) * splits), Plan<N>::NT * W, sm, st>>>(u, phi, lam, crop, tw, part,
+                                                                                          period, splits);
   return cudaGetLastError();
 }
 
@@ -482,9 +525,10 @@ cudaError_t launch_adj_rows(int n, const float2* t1, const float* lam, int nk, i
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
+// fields = clips x period; part receives clips x adj_col_splits(period) crop x crop sums.
 cudaError_t launch_adj_cols(int n, const float2* u, const float2* phi, const float* lam, int crop, const float2* tw,
-                            float2* sk, int planes, int period, cudaStream_t st) {
-#define CALL(N) adj_cols_n<N>(u, phi, lam, crop, tw, sk, planes, period, st)
+                            float2* part, int fields, int period, cudaStream_t st) {
+#define CALL(N) adj_cols_n<N>(u, phi, lam, crop, tw, part, fields, period, st)
   ILT_DISPATCH(n, CALL)
 #undef CALL
 }
@@ -635,7 +679,7 @@ litho_status ai_channels(const litho_kernels* h, const float* target, int b, dou
       LITHO_TRY_CUDA(cudaGetLastError());
       LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, ones, twe, L.u, g, 1, st, h->d_tw512));
       LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, g * K, K, st));
-      k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, K, size_t(C) * C, L.s, 0);
+      k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, adj_col_splits(K), size_t(C) * C, L.s, 0);
       LITHO_TRY_CUDA(cudaGetLastError());
       LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
       LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, x + (size_t(c0) * 3 + 2) * nn, g,
@@ -783,7 +827,7 @@ litho_status litho_ilt_grad(const litho_kernels* h, const float* theta_dev, cons
         }
         LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, gsrc, twe, L.u, gp, P, st, h->d_tw512));
         LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, gp * K, P * K, st));
-        k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, P * K, size_t(C) * C, L.s, f0 > 0 ? 1 : 0);
+        k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, adj_col_splits(P * K), size_t(C) * C, L.s, f0 > 0 ? 1 : 0);
         LITHO_TRY_CUDA(cudaGetLastError());
       }
     }
@@ -869,7 +913,8 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
           launch_adj_rows(NE, L.t1, h->d_lambda + size_t(f0) * K, K, C, up, twe, L.u, g * p, p, st, h->d_tw512));
       LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, h->d_phi + size_t(f0) * K * C * C, h->d_lambda + size_t(f0) * K, C,
                                      twe, L.sk, g * p * K, p * K, st));
-      k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, p * K, size_t(C) * C, L.s, f0 > f_first ? 1 : 0);
+      k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, adj_col_splits(p * K), size_t(C) * C, L.s,
+                                                 f0 > f_first ? 1 : 0);
       LITHO_TRY_CUDA(cudaGetLastError());
     }
     LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
