@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(Plan<N>::NT * W)
 template <int NC, int N>
 cudaError_t interp_cols_n(const float2* rspec, int planes, int c2, const float2* tw_nc, const float2* tw_n,
                           const float* gain, float2* q, cudaStream_t st) {
-  constexpr int W = 4;
+  constexpr int W = 8;
   if (c2 % W != 0 || c2 > NC) return cudaErrorInvalidValue;
   const size_t sm = sizeof(float2) * (size_t(N) + NC + size_t(W) * InterpShape<N, W>::LD);
   cudaError_t e = smem_attrs(k_interp_cols<NC, N, W>, sm);
