@@ -547,8 +547,9 @@ __device__ __forceinline__ void fft_load_smem(float2* buf, const float2* tw, int
 }
 
 // Columns per CTA for the column-transform kernels (W transforms of
-// Plan<N>::NT threads each): small CTAs so that several share an SM.
-template <int N> struct ColW { static constexpr int W = N >= 512 ? 4 : 8; };
+// Plan<N>::NT threads each): 8, so that a CTA loads its twiddle table for
+// many columns, except at 512 points (4 columns, several CTAs per SM).
+template <int N> struct ColW { static constexpr int W = N == 512 ? 4 : 8; };
 // Column stride in shared memory: the padded length rounded up to 16 complex
 // values plus 16/W, so that a half-warp of the cooperative copies (w fastest,
 // W columns x 16/W rows) touches 16 different 8-byte bank pairs.
