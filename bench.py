@@ -257,7 +257,7 @@ def ai_models(clips: int, n: int, ne: int, crop: int, k: int, coarse: bool, roun
     """stage -> (flops per step, algorithmic DRAM bytes per step) of the AI-input step
     (litho_ai_inputs + litho_print_images), counted as in stage_models: ilt_forward = the image
     channel (mask spectrum, stage 1 and 2 per kernel, interpolation), ilt_backward = the adjoint of
-    ones (adjoint rows and columns per kernel, the band-to-full gradient), ilt_reduce = the two
+    ones (its closed form N^2 sum_k lam_k |Phi_k|^2 mhat, then the band-to-full gradient), ilt_reduce = the two
     channel normalisations (read, then read and write), resist = the print images (blur of the
     targets, two thresholds, the L1 count).  Bytes: targets in, the three channels out."""
     fft = lambda m: 5.0 * m * math.log2(m)  # noqa: E731
@@ -265,9 +265,11 @@ def ai_models(clips: int, n: int, ne: int, crop: int, k: int, coarse: bool, roun
     fwd = clips * (n / 2 * fft(n) + crop * fft(n) +
                    k * (crop * fft(ne) + 6.0 * crop * crop + ne * (fft(ne) + 4.0 * ne)))
     if coarse:
-        fwd += clips * (ne / 2 * fft(ne) + c2 * fft(ne) + c2 * fft(n) + n * fft(n))
-    bwd = clips * (k * (ne * (2 * fft(ne) + 8.0 * ne) + crop * fft(ne) + 6.0 * crop * crop) +
-                   crop * fft(n) + n * fft(n))
+        # the coarse image's row transforms: one per row inside the 1024-point stage 2, else two
+        # real rows per transform
+        rows = ne * fft(ne) if (ne == 1024 and crop <= 512) else ne / 2 * fft(ne)
+        fwd += clips * (rows + c2 * fft(ne) + c2 * fft(n) + n * fft(n))
+    bwd = clips * (k * 4.0 * crop * crop + 4.0 * crop * crop + crop * fft(n) + n * fft(n))
     px = clips * n * n
     return {"ilt_forward": (fwd, px * 4.0 + px * 8.0), "ilt_backward": (bwd, px * 4.0),
             "ilt_reduce": (px * 2 * 3.0, px * 2 * 12.0),

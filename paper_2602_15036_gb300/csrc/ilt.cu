@@ -407,8 +407,31 @@ __global__ void k_to_channel(const float* __restrict__ img, float* __restrict__ 
     x[(i / nn) * 3 * nn + size_t(ch) * nn + i % nn] = img[i];
 }
 
-__global__ void k_fill(float* __restrict__ p, float v, size_t count) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+// The adjoint for dL/dI = 1 on every pixel (the AI input's gradient channel,
+// Eq. (9), and the intensity VJP without an upstream).  By Parseval,
+// sum_x |E_k(x)|^2 = N^2 sum_v |mhat(v) Phi_k(v)|^2, so the sum the adjoint
+// rows and columns form for G = 1 collapses to
+//   S(v,u) = N^2 sum_k lam_k |Phi_k(v,u)|^2 mhat(v,u),
+// exactly (on the coarse grid too: there G is the constant (N/nc)^2 and the
+// transforms are on nc).  No field is transformed.  Clip blockIdx.y; the nk
+// kernels of phi and lam (all planes of the call) are summed in order.
+__global__ void k_ones_adjoint(const float2* __restrict__ mhat, const float2* __restrict__ phi,
+                               const float* __restrict__ lam, int nk, size_t cc, float n2, float2* __restrict__ s,
+                               int accumulate) {
+  mhat += (size_t)blockIdx.y * cc;
+  s += (size_t)blockIdx.y * cc;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cc; i += (size_t)gridDim.x * blockDim.x) {
+    float d = 0.f;
+    for (int k = 0; k < nk; ++k) {
+      const float2 p = __ldg(phi + (size_t)k * cc + i);
+      d = fmaf(__ldg(lam + k), fmaf(p.x, p.x, p.y * p.y), d);
+    }
+    const float2 m = mhat[i];
+    float2 a = accumulate ? s[i] : make_float2(0.f, 0.f);
+    a.x = fmaf(n2 * d, m.x, a.x);
+    a.y = fmaf(n2 * d, m.y, a.y);
+    s[i] = a;
+  }
 }
 
 // s[clip] (+)= sum over the clip's `planes` planes of sk, in order (clip = blockIdx.y).
@@ -671,15 +694,10 @@ litho_status ai_channels(const litho_kernels* h, const float* target, int b, dou
       k_to_channel<<<512, 256, 0, st>>>(L.img, x + size_t(c0) * 3 * nn, g, nn, 1);
       LITHO_TRY_CUDA(cudaGetLastError());
     }
-    {  // channel 2: the adjoint of the same fields applied to dL/dI = 1; on the
-       // coarse grid the low-passed ones are the constant (N/nc)^2 (only the DC term)
-      ProfScope ps(kStageIltBackward, st, 6);
-      float* ones = coarse ? L.ic : L.img;
-      k_fill<<<256, 256, 0, st>>>(ones, float((double(N) / NE) * (double(N) / NE)), size_t(g) * NE * NE);
-      LITHO_TRY_CUDA(cudaGetLastError());
-      LITHO_TRY_CUDA(launch_adj_rows(NE, L.t1, lam, K, C, ones, twe, L.u, g, 1, st, h->d_tw512));
-      LITHO_TRY_CUDA(launch_adj_cols(NE, L.u, phi, lam, C, twe, L.sk, g * K, K, st));
-      k_sum_planes<<<dim3(256, g), 256, 0, st>>>(L.sk, adj_col_splits(K), size_t(C) * C, L.s, 0);
+    {  // channel 2: the adjoint applied to dL/dI = 1, in closed form (k_ones_adjoint)
+      ProfScope ps(kStageIltBackward, st, 3);
+      k_ones_adjoint<<<dim3(128, g), 256, 0, st>>>(L.mhat, phi, lam, K, size_t(C) * C,
+                                                   float(double(N) * double(N)), L.s, 0);
       LITHO_TRY_CUDA(cudaGetLastError());
       LITHO_TRY_CUDA(launch_stage1_fft(L.s, nullptr, g, N, C, h->d_tw, L.qf, st));
       LITHO_TRY_CUDA(launch_grad_rows(N, L.qf, C, scale, nullptr, 0.f, h->d_tw, x + (size_t(c0) * 3 + 2) * nn, g,
@@ -882,31 +900,29 @@ litho_status litho_intensity_vjp(const litho_kernels* h, const float* mask_dev, 
   const size_t nn = size_t(N) * N;
   const float scale = float(2.0 * dose / (double(N) * double(N)));
   // coarse grid as in litho_ilt_grad: the upstream low-passed to the 2C band
-  // and sampled on nc (ones: only the DC term, the constant (N/nc)^2)
+  // and sampled on nc (no upstream: the closed form, on no grid)
   const bool coarse = (int(prec) & LITHO_GRID_COARSE) && h->nc > 0 && interp_cols_supported(h->nc, N);
   const int NE = coarse ? h->nc : N, C2 = 2 * C;
   const float2* twe = coarse ? h->d_twc : h->d_tw;
   const float lp_scale = float((double(N) / NE) * (double(N) / NE));
   ProfScope ps(kStageIltBackward, st, 1);
-  float* ones = coarse ? L.ic : L.img;
-  if (!upstream_dev) {  // dL/dI = 1 on every pixel of the selected planes
-    k_fill<<<256, 256, 0, st>>>(ones, coarse ? lp_scale : 1.0f, size_t(G) * P * NE * NE);
-    LITHO_TRY_CUDA(cudaGetLastError());
-  }
   for (int c0 = 0; c0 < b; c0 += G) {
     const int g = std::min(G, b - c0);
     LITHO_TRY_CUDA(launch_mask_spectrum(mask_dev + c0 * nn, g, N, C, h->d_tw, L.rowbuf, L.mhat, st));
-    for (int f0 = f_first; f0 < f_first + f_count; f0 += P) {
+    if (!upstream_dev) {  // dL/dI = 1 on every pixel of the selected planes: the closed form
+      k_ones_adjoint<<<dim3(128, g), 256, 0, st>>>(L.mhat, h->d_phi + size_t(f_first) * K * C * C,
+                                                   h->d_lambda + size_t(f_first) * K, f_count * K, size_t(C) * C,
+                                                   float(double(N) * double(N)), L.s, 0);
+      LITHO_TRY_CUDA(cudaGetLastError());
+    }
+    for (int f0 = f_first; upstream_dev && f0 < f_first + f_count; f0 += P) {
       const int p = std::min(P, f_first + f_count - f0);
-      const float* up = ones;
-      if (upstream_dev) {
-        up = upstream_dev + (size_t(c0) * F + f0) * nn;
-        if (coarse) {
-          LITHO_TRY_CUDA(launch_mask_spectrum(up, g * p, N, C2, h->d_tw, L.big, L.spec, st));
-          LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, g * p, NE, C2, twe, L.mid, st));
-          LITHO_TRY_CUDA(launch_band_rows_real(L.mid, g * p, NE, C2, lp_scale, twe, L.ic, st));
-          up = L.ic;
-        }
+      const float* up = upstream_dev + (size_t(c0) * F + f0) * nn;
+      if (coarse) {
+        LITHO_TRY_CUDA(launch_mask_spectrum(up, g * p, N, C2, h->d_tw, L.big, L.spec, st));
+        LITHO_TRY_CUDA(launch_stage1_fft(L.spec, nullptr, g * p, NE, C2, twe, L.mid, st));
+        LITHO_TRY_CUDA(launch_band_rows_real(L.mid, g * p, NE, C2, lp_scale, twe, L.ic, st));
+        up = L.ic;
       }
       LITHO_TRY_CUDA(launch_stage1_fft(L.mhat, h->d_phi + size_t(f0) * K * C * C, p * K, NE, C, twe, L.t1, st, g));
       LITHO_TRY_CUDA(

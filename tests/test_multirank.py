@@ -100,15 +100,16 @@ def test_ilt_models_count_the_adjoint_transforms():
 
 def test_ai_models_count_both_channels():
     """The AI-input work model: the image channel (stage 1 and 2 per kernel on the evaluation
-    grid) and the adjoint of ones (two transforms per row, one per crop column); the print images
-    move 14 bytes per pixel (target and blur f32, the image read, two prints)."""
+    grid) and the adjoint of ones in closed form (lam_k |Phi_k|^2 per kernel and band point, then
+    the band-to-full gradient: one transform per crop column and per row, on any grid); the print
+    images move 14 bytes per pixel (target and blur f32, the image read, two prints)."""
     import math
     fft = lambda m: 5.0 * m * math.log2(m)  # noqa: E731
     m = bench.ai_models(16, 2048, 1024, 448, 24, True, 21)
     mf = bench.ai_models(16, 2048, 2048, 448, 24, False, 21)
-    bwd_full = 16 * (24 * (2048 * (2 * fft(2048) + 8.0 * 2048) + 448 * fft(2048) + 6.0 * 448 ** 2) +
-                     448 * fft(2048) + 2048 * fft(2048))
-    assert mf["ilt_backward"][0] == pytest.approx(bwd_full)
-    assert m["ilt_backward"][0] < mf["ilt_backward"][0] / 2
+    bwd = 16 * (24 * 4.0 * 448 ** 2 + 4.0 * 448 ** 2 + 448 * fft(2048) + 2048 * fft(2048))
+    assert mf["ilt_backward"][0] == pytest.approx(bwd)
+    assert m["ilt_backward"][0] == pytest.approx(bwd)
+    assert m["ilt_forward"][0] < mf["ilt_forward"][0] / 2
     assert m["resist"][1] == pytest.approx(16 * 2048 ** 2 * 14.0)
     assert m["ilt_forward"][1] == pytest.approx(16 * 2048 ** 2 * 12.0)

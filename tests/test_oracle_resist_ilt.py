@@ -87,6 +87,27 @@ def test_adjoint_identity_of_the_intensity_map():
     assert abs(lhs - rhs) < 1e-10 * abs(lhs)
 
 
+def test_vjp_of_ones_is_the_parseval_closed_form():
+    """With dL/dI = 1, L = sum_x I(x) = dose N^2 sum_v D(v) |M(v)|^2 (Parseval), D = sum_k lam_k |Phi_k|^2
+    on the band, M = DFT(m)/N^2; so dL/dm = 2 dose Re sum_v D(v) M(v) e^{+2 pi i v.x/N}.  Both sides
+    from plain numpy FFTs, against the oracle's image (for L) and its adjoint (for the gradient)."""
+    kernels, theta, _t, pix = _small_problem()
+    m = L.sigmoid(4 * theta)
+    n = m.shape[0]
+    dose = 1.7
+    mf = np.fft.fft2(m) / (n * n)
+    lam, phi = kernels[1]
+    c = phi.shape[-1]
+    idx = (np.arange(c) - c // 2) % n
+    d = np.zeros((n, n))
+    d[np.ix_(idx, idx)] = np.einsum("k,kvu->vu", lam, np.abs(phi) ** 2)
+    total = dose * n * n * np.sum(d * np.abs(mf) ** 2)
+    assert abs(np.sum(I.socs_image(m, lam, phi, dose)) - total) < 1e-10 * total
+    closed = 2.0 * dose * np.real(np.fft.ifft2(d * mf) * (n * n))
+    got = L.intensity_vjp(m, [(lam, phi)], [np.ones((n, n))], dose)
+    assert np.abs(got - closed).max() < 1e-10 * np.abs(closed).max()
+
+
 def test_gradient_matches_central_finite_differences():
     kernels, theta, target, pix = _small_problem()
     loss, grad = L.loss_and_grad(theta, target, kernels, pixel_nm=pix)
