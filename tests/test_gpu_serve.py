@@ -134,22 +134,32 @@ def _submit_raw(srv, L, kind, optics, n, pixel, k, inp, out):
 
 
 def test_small_requests_overtake_large_ones(litho_lib, cuda):
-    """Head-of-line independence: small images submitted after eight large ILT steps
-    (tens of milliseconds of GPU work) finish before the last of them; small batches run
-    on high-priority streams (kernel sets warmed first so only execution time counts)."""
+    """Head-of-line independence: small images submitted after twelve large ILT steps
+    (three batches of full-grid 2048^2 steps on three of the four slots) finish before
+    the last of them; small batches run on high-priority streams.  Kernel sets are warmed
+    first and the large requests use page-locked buffers (no staging copies on the host),
+    so that only execution time counts."""
+    import torch
     L = litho_lib
     srv = L.Server(16 << 30, max_slots=4, max_queue=64)
+    keep = []
+
+    def pinned(a):
+        t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+        keep.append(t)
+        return t.numpy()
+
     big_in, big_tg = synth.ilt_clip(2048, 8.0, seed=1)
-    big_in = np.ascontiguousarray(big_in)
-    big_tg = np.ascontiguousarray(big_tg)
+    big_in, big_tg = pinned(big_in), pinned(big_tg)
     small = synth.random_rect_mask(256, seed=2)
-    warm = [srv.submit("ilt", L.make_optics(**DUV), 2048, 8.0, 0.0, 24, big_in, np.zeros_like(big_in),
+    warm = [srv.submit("ilt", L.make_optics(**DUV), 2048, 8.0, 0.0, 24, big_in, pinned(np.zeros_like(big_in)),
                        target_host=big_tg)[0],
             srv.submit("image", L.make_optics(**DUV), 256, 8.0, 0.0, 8, small, np.zeros_like(small))[0]]
     st, _ = _wait_all(srv, L, warm)
     assert all(v == L.OK for v in st.values())
-    big = [srv.submit("ilt", L.make_optics(**DUV), 2048, 8.0, 0.0, 24, big_in, np.zeros_like(big_in),
-                      target_host=big_tg)[0] for _ in range(8)]
+    outs = [pinned(np.zeros_like(big_in)) for _ in range(12)]
+    big = [srv.submit("ilt", L.make_optics(**DUV), 2048, 8.0, 0.0, 24, big_in, outs[i],
+                      target_host=big_tg)[0] for i in range(12)]
     ts = [srv.submit("image", L.make_optics(**DUV), 256, 8.0, 0.0, 8, small, np.zeros_like(small))[0]
           for _ in range(6)]
     st, order = _wait_all(srv, L, big + ts)
