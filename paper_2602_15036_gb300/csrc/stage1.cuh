@@ -153,9 +153,12 @@ __global__ void __launch_bounds__(Plan<N>::NT * W, Stage1Pipe<Out>::kMinBlocks)
 template <int N, int W, class Out, bool BANDED>
 cudaError_t launch_stage1_cols_t(const float2* mhat, const float2* phi, int nk, int crop, const float2* tw, Out out,
                                  cudaStream_t st, int clips) {
-  // Kernels per CTA: as many as keep about two waves of CTAs on the GPU
-  // (each CTA loads its twiddles and mask values once and starts its copy
-  // pipeline once, so longer runs of kernels are cheaper), split evenly.
+  // Kernels per CTA: runs of kernels as long as possible (each CTA loads its
+  // twiddles and mask values once and starts its copy pipeline once), split
+  // so that the CTAs fill whole waves: the fewest waves x (kernels per CTA
+  // + half a kernel of set-up).
+  // (One run per CTA block leaves, e.g., 448 CTAs on 304 slots: a second wave
+  // half empty for a whole CTA's time.)
   static int sms = 0;  // the same GPU model throughout a process; a racing first call stores the same value
   if (!sms) {
     int dev = 0, v = 0;
@@ -164,8 +167,18 @@ cudaError_t launch_stage1_cols_t(const float2* mhat, const float2* phi, int nk, 
               ? v
               : 152;
   }
-  const long long ctas = (long long)clips * (crop / W);
-  const int jblocks = int(std::min<long long>(nk, std::max<long long>(1, (2LL * sms + ctas - 1) / ctas)));
+  const long long ctas = (long long)clips * (crop / W), slots = (long long)Stage1Pipe<Out>::kMinBlocks * sms;
+  int jblocks = 1;
+  long long best = -1;
+  for (int jb = 1; jb <= std::min(nk, 32); ++jb) {
+    const long long per = (nk + jb - 1) / jb;
+    const long long waves = (ctas * ((nk + per - 1) / per) + slots - 1) / slots;
+    const long long cost = waves * (2 * per + 1);  // half a kernel's time per CTA for its set-up
+    if (best < 0 || cost < best) {
+      best = cost;
+      jblocks = jb;
+    }
+  }
   const int JB = (nk + jblocks - 1) / jblocks;
   const size_t sm = sizeof(float2) * Stage1Shape<N, W>::smem_elems(crop, Stage1Pipe<Out>::kBuffers);
   cudaError_t e = smem_attrs(k_stage1_cols<N, W, Out, BANDED>, sm);
