@@ -255,9 +255,9 @@ __global__ void __launch_bounds__(Plan<N>::NT) k_band_rows_resist(const float2* 
 // the imaginary part of IDFT(R_y) is the blurred row.  The blurred row's
 // spectrum is (R_y(u) - conj R_y(-u)) / 2i, so one inverse transform of
 // Bl_y0 + i Bl_y1 gives both blurred rows as its real and imaginary parts.
-// The sigmoid resist z = 1 / (1 + e^{-beta (blur - thr)}), the residual
-// d = z - target and dL/dI = 2 d beta z (1 - z) follow on the spot (Eqs. (5)
-// and (10)); the two dL/dI rows go forward as one complex row
+// The sigmoid resist z = 1 / (1 + e^{-beta (blur - thr)}) (a smooth Eq. (5)),
+// the residual d = z - target of the squared-residual ILT loss and
+// dL/dI = 2 d beta z (1 - z) follow on the spot; the two dL/dI rows go forward as one complex row
 // q[y0] + i q[y1] and leave as their two band spectra, as k_mask_rows writes
 // them.  The pair's sum of d^2 goes to partial[plane][pair] in FP64: one
 // partial per row pair, whatever the launch shape, so the loss does not
