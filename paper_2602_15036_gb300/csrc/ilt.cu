@@ -291,9 +291,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps, 2)
 // field j uses kernel j mod period.  W columns per CTA with the lanes of a
 // warp interleaved over them (as in stage 1): the first pass reads U straight
 // from global memory (W adjacent columns of 32/W rows per warp load: whole
-// sectors), the last pass writes the cropped, weighted outputs from
-// registers, and a CTA runs `jb` fields in turn so that its twiddle table is
-// loaded once.
+// sectors), the last pass hands each thread the same output positions for
+// every field, and a CTA runs a run of fields in turn so that its twiddle
+// table is loaded once.
 template <int N> struct AdjW { static constexpr int W = Plan<N>::NT <= 64 ? 8 : 4; };
 
 // Where the adjoint columns keep their sums: in registers they cost the
@@ -313,10 +313,8 @@ int adj_col_splits(int period) {
 // Per crop column block and run of fields j in [j0, j1) of one clip (the
 // clip's `period` fields split into `splits` runs of period / splits): the
 // forward transform over y of each field's column, the crop, lam conj(Phi)
-// times it, summed over the run (each thread keeps the same
-// output positions for every field; the sums sit in registers or, up to 512
-// points, in shared memory, one slot per thread and position)
-// and written once, to
+// times it, summed over the run (in registers, or up to 512 points in shared
+// memory, one slot per thread and output position) and written once, to
 // part[clip splits + split][cv][c].  k_sum_planes then adds a clip's runs in
 // order, so the sum's order depends on the clip's own field count only.
 template <int N>
