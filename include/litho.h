@@ -269,7 +269,10 @@ litho_status litho_resist(const float* intensity_dev, int planes, int n, double 
  * planes outside the range are not read) or, when upstream_dev is NULL, 1 on
  * every pixel (the gradient of the total intensity).  The same adjoint as
  * litho_ilt_grad without the resist and sigmoid factors: 2 D N^-2 Re IDFT of
- * sum_k lam_k conj(Phi_k) DFT_crop(q E_k).  Workspace as litho_ilt_workspace_size
+ * sum_k lam_k conj(Phi_k) DFT_crop(q E_k).  With q = 1 this sum is, by
+ * Parseval, N^2 sum_k lam_k |Phi_k|^2 Mhat (Mhat the mask's crop spectrum), which
+ * is what is evaluated then (no field is transformed; the grid flag has no
+ * effect on the result).  Workspace as litho_ilt_workspace_size
  * (the smaller size evaluates one plane of one clip at a time).  prec:
  * LITHO_PREC_FFT32 (else EUNSUPPORTED), optionally | LITHO_GRID_COARSE (the
  * fields and the adjoint on the coarse grid, q low-passed to the image band
