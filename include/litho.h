@@ -403,10 +403,10 @@ litho_status litho_ilt_workspace_size(const litho_kernels* h, int b, size_t* ful
  * theta_dev, target_dev, grad_dev: float32 [b][n][n] on the device (theta_dev
  * 16-byte aligned, else EINVAL).
  * loss_host (may be NULL): b doubles, reduced in FP64 on the device; when
- * given, the call waits for the stream.  Each clip's loss and gradient are
- * bit-identical whatever the number of clips in the call: the partial sums
- * follow a partition fixed per clip (per row pair of each plane on the coarse
- * grid).  A workspace between min_bytes and
+ * given, the call waits for the stream.  With the full workspace each clip's
+ * loss and gradient are bit-identical whatever the number of clips in the
+ * call: the partial sums follow a partition fixed per clip (per row pair of
+ * each plane on the coarse grid).  A workspace between min_bytes and
  * full_bytes selects recomputation of the forward fields; below min_bytes is
  * ENOMEM.  prec: LITHO_PREC_FFT32 (else EUNSUPPORTED), optionally with
  * LITHO_GRID_COARSE: the fields, the image and the adjoint transforms are
